@@ -1,0 +1,366 @@
+#!/usr/bin/env python
+"""Throughput of one pass of the ptychography hot path: forward model, loss and adjoint.
+
+A step is one pty_loss_grad call over one batch of scan positions of the multislice workload
+(128 x 128 window, 6 probe modes, 8 slices of 512 x 512, 4096 positions, batch 512 positions
+taken as contiguous raster blocks): shifted probes, all transmissions and propagations, the far
+field, the Poisson loss and every gradient (object amplitude and phase, probe, positions, tilts,
+dz).  The metric counts position x mode x slice wavefield updates per second.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the host cores on a
+bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "wavefield updates/s (fwd+adjoint, 1 GB300)"
+UNIT = "position*mode*slice updates/s"
+WORKLOAD = "multislice N=128 M=6 Nz=8, object 8x512x512, 4096 positions, batch 512"
+
+# FP32 CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz max clock.
+ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
+
+
+def fft2_flops(N):
+    """Nominal 5 n log2 n flops of a complex FFT of n = N^2 points."""
+    return 5.0 * N * N * math.log2(N * N)
+
+
+def flops_per_wave(N, Nz, stage):
+    """Algorithmic flops of one (position, mode) wave in the forward or adjoint kernel.
+
+    Forward: 2 Nz 2D FFTs (shift, Nz-1 propagation pairs, far field) + per pixel: shift ramp
+    (2 complex products, 12), Nz transmissions (6 each), Nz-1 propagator products (12 each), far-field
+    scale and |.|^2 (5).  Adjoint: 2 Nz 2D FFTs + per pixel: 2 dL/dI Psi (4), Nz x (conj(psi) g 6,
+    conj(T) g 6), Nz-1 x (propagator 12, dz/tilt term 4), probe ramp and position term (12 + 6 + 4)."""
+    px = N * N
+    if stage == "forward":
+        return 2 * Nz * fft2_flops(N) + px * (12 + 6 * Nz + 12 * (Nz - 1) + 5)
+    return 2 * Nz * fft2_flops(N) + px * (4 + 12 * Nz + 16 * (Nz - 1) + 22)
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("fft_smem.cuh", "pipeline.cuh"):
+        with open(os.path.join(ROOT, "paper_2505_07814_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
+    current kernel source; None otherwise."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch_full_size")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu_id)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is None:
+            return
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            f = [x.strip() for x in l.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": mx, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def gpu_smi_id(torch, dev):
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        return "%08X:%02X:%02X.0" % (p.pci_domain_id, p.pci_bus_id, p.pci_device_id)
+    except Exception:
+        return str(dev.index or 0)
+
+
+def make_inputs(args):
+    import numpy as np
+
+    from paper_2505_07814_gb300 import synth
+
+    w = synth.workload("c2")
+    amp0, phase0 = synth.flat_object(w.Nz, w.H, w.W)  # default start of a reconstruction
+    I_meas = synth.vacuum_patterns(w.probe, w.Ntot)
+    return w, amp0, phase0, I_meas
+
+
+def batch_indices(step, B, Ntot):
+    s = (step * B) % Ntot
+    return [(s + i) % Ntot for i in range(B)]
+
+
+def row_runs(idx):
+    """Maximal runs [lo, hi) of consecutive indices (a contiguous batch that wraps gives two)."""
+    runs, lo = [], idx[0] if idx else 0
+    for a, b in zip(idx, idx[1:] + [None]):
+        if b != a + 1:
+            runs.append((lo, a + 1))
+            lo = b
+    return runs
+
+
+def cpu_oracle_sample(w, amp0, phase0, I_meas, B, seconds):
+    """Time the FP64 oracle's loss and gradient on a bounded sample of one batch."""
+    import numpy as np
+
+    from oracle import ptycho as O
+
+    geom = O.Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, dx=w.dx, lam=w.lam)
+    idx_all = batch_indices(0, B, w.Ntot)
+    t0 = time.perf_counter()
+    O.loss_and_grad(geom, amp0, phase0, w.probe, w.pos, w.tilt, w.dz, I_meas, idx_all[:1])
+    t1 = time.perf_counter() - t0
+    P = max(1, min(B, int(seconds / max(t1, 1e-3))))
+    t0 = time.perf_counter()
+    O.loss_and_grad(geom, amp0, phase0, w.probe, w.pos, w.tilt, w.dz, I_meas, idx_all[:P])
+    dt = time.perf_counter() - t0
+    return P, dt
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    import numpy as np
+
+    w, amp0, phase0, I_meas = make_inputs(args)
+    from oracle import ptycho as O
+
+    geom = O.Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, dx=w.dx, lam=w.lam)
+    P = 2  # positions per step: a bounded sample of one batch (2 x 6 modes x 8 slices = 96 updates)
+    times = []
+    for k in range(args.warmup + args.steps):
+        idx = batch_indices(k, args.batch, w.Ntot)[:P]
+        t0 = time.perf_counter()
+        O.loss_and_grad(geom, amp0, phase0, w.probe, w.pos, w.tilt, w.dz, I_meas, idx)
+        if k >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    upd = P * w.M * w.Nz
+    value = upd * len(times) / sum(times)
+    sample = "%d positions (%d updates) of a %d-position batch per step; FP64 numpy oracle" % (P, upd, args.batch)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": w.N, "M": w.M, "Nz": w.Nz, "positions": w.Ntot,
+                       "batch": args.batch, "sample_positions_per_step": P},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import numpy as np
+    import torch
+
+    from paper_2505_07814_gb300 import _lib, build
+    from paper_2505_07814_gb300.ptycho import Geometry, Params, Ptycho
+
+    if args.warmup < 3:
+        raise SystemExit("at least 3 warm-up steps")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    build.build()
+    _lib.load()
+
+    w, amp0, phase0, I_meas_np = make_inputs(args)
+    B = args.batch
+    geom = Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, Ntot=w.Ntot, dx=w.dx, lam=w.lam, loss="poisson")
+    f32 = dict(dtype=torch.float32, device=dev)
+    params = Params(amp=torch.tensor(amp0, **f32), phase=torch.tensor(phase0, **f32),
+                    probe=torch.tensor(w.probe, dtype=torch.complex64, device=dev), pos=torch.tensor(w.pos, **f32),
+                    tilt=torch.tensor(w.tilt, **f32), dz=torch.tensor([w.dz], **f32))
+    I_meas = torch.tensor(I_meas_np, **f32)
+    pt = Ptycho(geom, B, device=dev)
+    grads = params.zeros_like()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > 129 MB L2
+    # each rank takes its own batches (weak scaling: independent position blocks, no collective)
+    idx_h = [batch_indices(k * world + rank, B, w.Ntot) for k in range(8)]
+    idx_t = [torch.tensor(i, dtype=torch.int32, device=dev) for i in idx_h]
+
+    for k in range(args.warmup):
+        pt.loss_grad(params, idx_t[k % 8], I_meas, grads=grads)
+    torch.cuda.synchronize()
+    assert pt.status() == 0
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    _lib.pty_profile_enable(True)
+    n0 = _lib.pty_launch_count()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(gpu_smi_id(torch, dev)) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record()
+            pt.loss_grad(params, idx_t[k % 8], I_meas, grads=grads)
+            ends[k].record()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = _lib.pty_launch_count() - n0
+    ncalls, stage_ms = _lib.pty_profile_read()
+    _lib.pty_profile_enable(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = t.item()
+    upd_step = B * w.M * w.Nz
+    value = world * upd_step * args.steps / (total_ms / 1e3)
+
+    # dominant kernel and its roofline (FP32 ALU bound: the wave never leaves shared memory)
+    dom = max(("forward", "adjoint"), key=lambda s: stage_ms[s])
+    avg_ms = stage_ms[dom] / max(ncalls, 1)
+    flops = B * w.M * flops_per_wave(w.N, w.Nz, dom)
+    achieved = flops / (avg_ms / 1e3) / 1e12
+    traffic = ncu_traffic("k_" + dom)
+    roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / ALU_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_" + dom,
+                "avg_launch_ms": avg_ms, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"}
+    stages = {k: v / max(ncalls, 1) for k, v in stage_ms.items()}
+
+    # end to end through the public API from pinned host buffers
+    host = {n: getattr(params, n).cpu().pin_memory() for n in ("amp", "phase", "probe", "pos", "tilt", "dz")}
+    h_meas = I_meas.cpu().pin_memory()
+    h_grads = {n: torch.empty_like(getattr(grads, n), device="cpu").pin_memory()
+               for n in ("amp", "phase", "probe", "pos", "tilt", "dz")}
+    h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+    e_steps = min(args.e2e_steps, args.steps)
+    h2d = d2h = 0
+    es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e2e_ms = 0.0
+    for k in range(e_steps):
+        flush.zero_()
+        idx = idx_t[k % 8]
+        es.record()
+        h2d = d2h = 0
+        for n in host:
+            getattr(params, n).copy_(host[n], non_blocking=True)
+            h2d += host[n].numel() * host[n].element_size()
+        for lo, hi in row_runs(idx_h[k % 8]):  # the measured patterns this batch reads
+            I_meas[lo:hi].copy_(h_meas[lo:hi], non_blocking=True)
+            h2d += (hi - lo) * w.N * w.N * 4
+        loss, _ = pt.loss_grad(params, idx, I_meas, grads=grads)
+        for n in h_grads:
+            h_grads[n].copy_(getattr(grads, n), non_blocking=True)
+            d2h += h_grads[n].numel() * h_grads[n].element_size()
+        h_loss.copy_(loss, non_blocking=True)
+        d2h += 8
+        ee.record()
+        ee.synchronize()
+        e2e_ms += es.elapsed_time(ee)
+    e2e_value = world * upd_step * e_steps / (e2e_ms / 1e3)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        P, dt = cpu_oracle_sample(w, amp0, phase0, I_meas_np, B, args.cpu_seconds)
+        cpu = {"value": P * w.M * w.Nz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "FP64 numpy oracle, loss + all gradients for the first %d positions of one %d-position "
+                         "batch (%d updates, %.1f s, single-threaded pocketfft)" % (P, B, P * w.M * w.Nz, dt)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "N": w.N, "M": w.M, "Nz": w.Nz, "positions": w.Ntot, "batch": B,
+                           "object": [w.Nz, w.H, w.W], "loss": "poisson", "grads": "amp,phase,probe,pos,tilt,dz",
+                           "batches": "contiguous raster blocks", "start": "flat object (amp 1, phase U[0,1e-8])",
+                           "l2": "flushed before every step (256 MiB write outside the step events)",
+                           "parallelism": "dp%d" % world},
+                "roofline": roofline, "stage_ms_per_call": stages,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "steps": e_steps},
+                "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * pty.h -- C ABI of the GB300 (sm_103a) multislice ptychography hot path.
+ *
+ * The library evaluates, for a batch of scan positions, the mixed-state multislice forward model
+ * of PtyRAD (arXiv 2505.07814, Sec. "Physical model", Eq. 1-4), the Gaussian or Poisson
+ * negative-log-likelihood loss (Sec. "Optimizers and loss functions", Eq. 5-6) and the exact
+ * gradient of that loss with respect to the six optimisable parameters of Sec. "AD-optimizable
+ * parameters": object amplitude, object phase, probe modes, probe positions, local tilts and slice
+ * spacing dz.  The gradient comes from a hand-written adjoint, not from automatic differentiation.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All array arguments are DEVICE pointers on the current CUDA device, row-major, axis 0 = rows,
+ *    axis 1 = columns.  Complex arrays are interleaved (re, im) float32 pairs and must be 8-byte
+ *    aligned; everything else 4-byte aligned.  The caller owns every buffer; the library allocates
+ *    no device memory and keeps no pointer after a call returns.
+ *  - Calls are asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream).  Results,
+ *    including the device-side status word, are valid once the stream has reached them.
+ *  - Return value: PTY_OK, or an error code with nothing launched (host-side validation).  The
+ *    message of the last failure on the calling thread is available from pty_last_error().
+ *    Conditions that only the device can see (a patch outside the object, a non-finite loss) set
+ *    bits of the status word in the workspace; read them with pty_status().  The kernels clamp an
+ *    out-of-range patch into the object instead of reading out of bounds.
+ *  - Object amp/phase: float [Nz][H][W].  Probe: complex [M][N][N] (real-space modes).
+ *    Positions: float [Ntot][2], (row, col) of the top-left corner of each N x N object patch, in
+ *    pixels; the patch starts at round-half-to-even(pos) and the remainder pos - round(pos) is the
+ *    sub-pixel shift applied to the probe (Sec. "Physical model").  Tilts: float [Ntot][2] radian
+ *    (or [2] with global_tilt), (axis-0, axis-1) components of theta in Eq. 4.  dz: float[1]
+ *    angstrom, the separation between slices (Eq. 3-4).  Measured and modelled patterns: float
+ *    [.][N][N], DC-centred (fftshift of the DFT order), far field taken with the orthonormal DFT.
+ *  - Batches: idx is an int32 [B] array of scan-position indices in [0, Ntot); the batch holds the
+ *    patterns idx[0..B-1].  Repeated indices are allowed (their gradients add).
+ *  - Complex gradients follow dL/dRe + i dL/dIm; amplitude/phase gradients are real.
+ */
+#ifndef PTY_H
+#define PTY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return / status codes.  Device status bits are OR-ed into the workspace status word. */
+enum {
+  PTY_OK = 0,
+  PTY_EINVAL = 1,      /* bad shape, unsupported N, null or misaligned pointer */
+  PTY_EBOUNDS = 2,     /* device bit: a patch round(pos) .. round(pos)+N-1 left the object, or
+                          a batch index was outside [0, Ntot) (then scan position 0 was used) */
+  PTY_EWORKSPACE = 4,  /* workspace smaller than pty_workspace_size() */
+  PTY_ECUDA = 8,       /* a CUDA launch failed; see pty_last_error() */
+  PTY_ETIMEOUT = 16,   /* a bounded device wait gave up (reserved: no kernel here waits) */
+  PTY_ENONFINITE = 32  /* device bit: the loss or its normaliser was not finite */
+};
+
+enum { PTY_LOSS_POISSON = 0, PTY_LOSS_GAUSSIAN = 1 };
+
+/* Which gradients pty_loss_grad / pty_step compute (bit mask). */
+enum {
+  PTY_GRAD_AMP = 1,
+  PTY_GRAD_PHASE = 2,
+  PTY_GRAD_PROBE = 4,
+  PTY_GRAD_POS = 8,
+  PTY_GRAD_TILT = 16,
+  PTY_GRAD_DZ = 32,
+  PTY_GRAD_ALL = 63
+};
+
+/* Problem geometry.  N is the probe window, detector and FFT size: 64 or 128. */
+typedef struct {
+  int N;           /* probe / detector pixels per side */
+  int M;           /* incoherent probe modes, >= 1 (Eq. 2) */
+  int Nz;          /* object slices, >= 1 (Eq. 3) */
+  int H, W;        /* object rows / columns, >= N */
+  int Ntot;        /* scan positions: rows of pos, tilt and I_meas */
+  float dx;        /* real-space pixel size, angstrom (sets the frequency grid of Eq. 4) */
+  float lambda;    /* electron wavelength, angstrom (Eq. 4) */
+  int loss;        /* PTY_LOSS_POISSON (Eq. 6) or PTY_LOSS_GAUSSIAN (Eq. 5) */
+  float p;         /* exponent applied to the patterns in the loss; <= 0 selects the default
+                      (1 for Poisson, 0.5 for Gaussian) */
+  float eps;       /* Poisson stabiliser inside the log (Eq. 6), normally 1e-6 */
+  int grad_mask;   /* PTY_GRAD_* bits */
+  int global_tilt; /* 0: tilt is [Ntot][2] (local); 1: tilt is [2] shared by every position */
+} pty_geom;
+
+/* Adam state and hyper-parameters for pty_step / pty_adam (PyTorch's Adam: bias-corrected first and
+ * second moments; complex tensors are treated as pairs of reals).  m_* and v_* are device float
+ * arrays shaped like the parameter they belong to, zero-initialised by the caller before step 1.
+ * A parameter is updated only if its PTY_GRAD_* bit is set in geom->grad_mask and its lr > 0; this
+ * is the per-parameter learning rate and onset of Sec. "AD-optimizable parameters". */
+typedef struct {
+  float *m_amp, *v_amp, *m_phase, *v_phase, *m_probe, *v_probe;
+  float *m_pos, *v_pos, *m_tilt, *v_tilt, *m_dz, *v_dz;
+  float lr_amp, lr_phase, lr_probe, lr_pos, lr_tilt, lr_dz;
+  float beta1, beta2, eps;
+} pty_adam;
+
+/* Bytes of workspace a call with batch size B needs (forward, loss and adjoint, for the gradients
+ * named in geom->grad_mask).  0 on invalid geometry (see pty_last_error()). */
+size_t pty_workspace_size(const pty_geom* geom, int B);
+
+/* Forward model, Eq. 1-4: I_model[b] = fftshift( sum_m |F_ortho[psi_{idx[b]}^(m)]|^2 ), [B][N][N].
+ * Reads amp, phase, probe, pos, tilt, dz; writes I_model.  ws must hold pty_workspace_size(). */
+int pty_forward(const pty_geom* geom, int B, const int32_t* idx, const float* amp,
+                const float* phase, const float* probe, const float* pos, const float* tilt,
+                const float* dz, float* I_model, void* ws, size_t ws_bytes, void* stream);
+
+/* Loss of the batch (Eq. 5 or 6, means over detector pixels and batch) and its gradients.
+ *  I_meas  float [Ntot][N][N], DC-centred measured patterns (rows idx[b] are used).
+ *  loss    double[1] device scalar (written).
+ *  I_model float [B][N][N] or NULL.
+ *  g_amp, g_phase float [Nz][H][W]; g_probe complex [M][N][N]; g_pos float [Ntot][2];
+ *  g_tilt float [Ntot][2] (or [2] with global_tilt); g_dz float[1].  A gradient whose bit is not
+ *  in geom->grad_mask may be NULL and is left untouched.
+ *  accumulate = 0: every requested gradient array is overwritten in full (zeros where the batch
+ *  does not reach); accumulate = 1: the batch's gradient is added (gradient accumulation over
+ *  sub-batches). */
+int pty_loss_grad(const pty_geom* geom, int B, const int32_t* idx, const float* amp,
+                  const float* phase, const float* probe, const float* pos, const float* tilt,
+                  const float* dz, const float* I_meas, double* loss, float* I_model,
+                  float* g_amp, float* g_phase, float* g_probe, float* g_pos, float* g_tilt,
+                  float* g_dz, int accumulate, void* ws, size_t ws_bytes, void* stream);
+
+/* One Adam step on the parameters in place using the gradients already in g_* (pty_adam state).
+ * step is the 1-based Adam step count used for bias correction. */
+int pty_adam_update(const pty_geom* geom, float* amp, float* phase, float* probe, float* pos,
+                    float* tilt, float* dz, const float* g_amp, const float* g_phase,
+                    const float* g_probe, const float* g_pos, const float* g_tilt,
+                    const float* g_dz, const pty_adam* adam, int step, void* stream);
+
+/* pty_loss_grad (accumulate = 0) followed by pty_adam_update: one gradient-descent iteration on
+ * one batch (Sec. "Optimizers and loss functions", Adam).  Parameters are updated in place. */
+int pty_step(const pty_geom* geom, int B, const int32_t* idx, float* amp, float* phase,
+             float* probe, float* pos, float* tilt, float* dz, const float* I_meas, double* loss,
+             float* g_amp, float* g_phase, float* g_probe, float* g_pos, float* g_tilt,
+             float* g_dz, const pty_adam* adam, int step, void* ws, size_t ws_bytes, void* stream);
+
+/* Synchronises `stream` and returns the OR of the device status bits (PTY_EBOUNDS,
+ * PTY_ENONFINITE) set since the last call that used this workspace began; a negative value if the
+ * status could not be read.  Each pty_forward / pty_loss_grad / pty_step clears the word first. */
+int pty_status(const void* ws, void* stream);
+
+/* Message of the last error returned on the calling thread ("" if none). */
+const char* pty_last_error(void);
+
+/* Bit mask of the FFT sizes N this build supports (bit k set: N = 2^k). */
+int pty_supported_sizes(void);
+
+/* Diagnostics for throughput measurement (not needed to use the library).
+ * pty_launch_count: number of kernels this library has launched in the process so far.
+ * pty_profile_enable(1) resets and starts per-kernel timing: every later pipeline call records a CUDA
+ *   event after each of its kernels on the call's stream (up to 256 calls are kept); (0) stops it.
+ * pty_profile_read fills ms[k] with the summed device time of pipeline stage k over the recorded
+ *   calls, for k < min(n, PTY_PROF_STAGES), synchronising on the recorded events; returns the number
+ *   of calls recorded, or -1 on a CUDA error.  Stages: 0 prepare_object, 1 probe_spectrum, 2 forward,
+ *   3 loss, 4 loss_finalize, 5 adjoint, 6 object_grad, 7 probe_grad, 8 scalar_grad. */
+#define PTY_PROF_STAGES 9
+long long pty_launch_count(void);
+int pty_profile_enable(int on);
+int pty_profile_read(double* ms, int n);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PTY_H */

@@ -1,0 +1,165 @@
+"""ctypes binding of libpty.so (include/pty.h): same names, argument marshalling only.
+
+Every array argument is a raw device address (int) or None; sizes are ints.  Nothing here
+computes any part of the model.  Loading fails loudly if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpty.so")
+
+PTY_OK = 0
+PTY_EINVAL = 1
+PTY_EBOUNDS = 2
+PTY_EWORKSPACE = 4
+PTY_ECUDA = 8
+PTY_ETIMEOUT = 16
+PTY_ENONFINITE = 32
+
+PTY_LOSS_POISSON = 0
+PTY_LOSS_GAUSSIAN = 1
+
+PTY_GRAD_AMP = 1
+PTY_GRAD_PHASE = 2
+PTY_GRAD_PROBE = 4
+PTY_GRAD_POS = 8
+PTY_GRAD_TILT = 16
+PTY_GRAD_DZ = 32
+PTY_GRAD_ALL = 63
+
+# Every symbol include/pty.h declares (checked by the CPU test suite).
+EXPORTS = ("pty_workspace_size", "pty_forward", "pty_loss_grad", "pty_adam_update", "pty_step",
+           "pty_status", "pty_last_error", "pty_supported_sizes", "pty_launch_count", "pty_profile_enable",
+           "pty_profile_read")
+PROF_STAGES = ("prepare_object", "probe_spectrum", "forward", "loss", "loss_finalize", "adjoint", "object_grad",
+               "probe_grad", "scalar_grad")
+
+
+class pty_geom(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("Nz", ctypes.c_int), ("H", ctypes.c_int),
+                ("W", ctypes.c_int), ("Ntot", ctypes.c_int), ("dx", ctypes.c_float),
+                ("lambda_", ctypes.c_float), ("loss", ctypes.c_int), ("p", ctypes.c_float),
+                ("eps", ctypes.c_float), ("grad_mask", ctypes.c_int), ("global_tilt", ctypes.c_int)]
+
+
+class pty_adam(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in ("m_amp", "v_amp", "m_phase", "v_phase", "m_probe", "v_probe",
+                                               "m_pos", "v_pos", "m_tilt", "v_tilt", "m_dz", "v_dz")] + \
+               [(n, ctypes.c_float) for n in ("lr_amp", "lr_phase", "lr_probe", "lr_pos", "lr_tilt", "lr_dz",
+                                              "beta1", "beta2", "eps")]
+
+
+class PtyError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("pty error %d: %s" % (code, msg))
+        self.code = code
+
+
+_lib = None
+P = ctypes.c_void_p
+I = ctypes.c_int
+SZ = ctypes.c_size_t
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libpty.so (once).  Raises if it is missing: there is no fallback path."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError("libpty.so is not built (%s); run paper_2505_07814_gb300.build.build()" % path)
+    lib = ctypes.CDLL(path)
+    G = ctypes.POINTER(pty_geom)
+    A = ctypes.POINTER(pty_adam)
+    lib.pty_workspace_size.argtypes = [G, I]
+    lib.pty_workspace_size.restype = SZ
+    lib.pty_forward.argtypes = [G, I, P, P, P, P, P, P, P, P, P, SZ, P]
+    lib.pty_forward.restype = I
+    lib.pty_loss_grad.argtypes = [G, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, I, P, SZ, P]
+    lib.pty_loss_grad.restype = I
+    lib.pty_adam_update.argtypes = [G, P, P, P, P, P, P, P, P, P, P, P, P, A, I, P]
+    lib.pty_adam_update.restype = I
+    lib.pty_step.argtypes = [G, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, A, I, P, SZ, P]
+    lib.pty_step.restype = I
+    lib.pty_status.argtypes = [P, P]
+    lib.pty_status.restype = I
+    lib.pty_last_error.argtypes = []
+    lib.pty_last_error.restype = ctypes.c_char_p
+    lib.pty_supported_sizes.argtypes = []
+    lib.pty_supported_sizes.restype = I
+    lib.pty_launch_count.argtypes = []
+    lib.pty_launch_count.restype = ctypes.c_longlong
+    lib.pty_profile_enable.argtypes = [I]
+    lib.pty_profile_enable.restype = I
+    lib.pty_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), I]
+    lib.pty_profile_read.restype = I
+    _lib = lib
+    return lib
+
+
+def _check(rc: int):
+    if rc != PTY_OK:
+        raise PtyError(rc, load().pty_last_error().decode())
+
+
+def pty_workspace_size(geom: pty_geom, B: int) -> int:
+    n = load().pty_workspace_size(ctypes.byref(geom), B)
+    if n == 0:
+        raise PtyError(PTY_EINVAL, load().pty_last_error().decode())
+    return n
+
+
+def pty_forward(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_model, ws, ws_bytes, stream):
+    _check(load().pty_forward(ctypes.byref(geom), B, idx, amp, phase, probe, pos, tilt, dz, I_model, ws,
+                              ws_bytes, stream))
+
+
+def pty_loss_grad(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss, I_model, g_amp, g_phase,
+                  g_probe, g_pos, g_tilt, g_dz, accumulate, ws, ws_bytes, stream):
+    _check(load().pty_loss_grad(ctypes.byref(geom), B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss,
+                                I_model, g_amp, g_phase, g_probe, g_pos, g_tilt, g_dz, int(accumulate), ws,
+                                ws_bytes, stream))
+
+
+def pty_adam_update(geom, amp, phase, probe, pos, tilt, dz, g_amp, g_phase, g_probe, g_pos, g_tilt, g_dz,
+                    adam: pty_adam, step, stream):
+    _check(load().pty_adam_update(ctypes.byref(geom), amp, phase, probe, pos, tilt, dz, g_amp, g_phase, g_probe,
+                                  g_pos, g_tilt, g_dz, ctypes.byref(adam), step, stream))
+
+
+def pty_step(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss, g_amp, g_phase, g_probe, g_pos,
+             g_tilt, g_dz, adam: pty_adam, step, ws, ws_bytes, stream):
+    _check(load().pty_step(ctypes.byref(geom), B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss, g_amp,
+                           g_phase, g_probe, g_pos, g_tilt, g_dz, ctypes.byref(adam), step, ws, ws_bytes, stream))
+
+
+def pty_status(ws, stream) -> int:
+    return load().pty_status(ws, stream)
+
+
+def pty_last_error() -> str:
+    return load().pty_last_error().decode()
+
+
+def pty_supported_sizes() -> int:
+    return load().pty_supported_sizes()
+
+
+def pty_launch_count() -> int:
+    return load().pty_launch_count()
+
+
+def pty_profile_enable(on: bool):
+    _check(load().pty_profile_enable(int(on)))
+
+
+def pty_profile_read() -> tuple[int, dict]:
+    """(number of recorded calls, {stage name: summed device milliseconds})."""
+    buf = (ctypes.c_double * len(PROF_STAGES))()
+    n = load().pty_profile_read(buf, len(PROF_STAGES))
+    if n < 0:
+        raise PtyError(PTY_ECUDA, "profile read failed")
+    return n, {name: buf[k] for k, name in enumerate(PROF_STAGES)}

@@ -1,0 +1,807 @@
+// pipeline.cuh -- kernels of the batched multislice forward model, loss and adjoint, templated on
+// the window size N.  One CTA owns one (scan position, probe mode) wavefield for the whole slice
+// loop; the wave never leaves shared memory except as checkpoints for the adjoint.
+//
+// Kernel sequence of one pty_loss_grad call (one stream, no host synchronisation):
+//   k_prepare_object   T = amp exp(i phase) for the whole object; zero dL/dT accumulator
+//   k_probe_spectrum   P^_m = F[P_m]                                              (M CTAs)
+//   k_forward          shift, Nz transmissions, Nz-1 propagations, far field      (B*M CTAs)
+//   k_loss             mode sum, Eq. 5/6 per pixel, dL/dI, per-pattern sums      (B CTAs)
+//   k_loss_finalize    batch loss and dL/dI normaliser (FP64)                      (1 CTA)
+//   k_adjoint          reverse of k_forward, scatter-adds dL/dT, probe-spectrum
+//                      gradient, FP64-reduced position / tilt / dz partials       (B*M CTAs)
+//   k_object_grad      dL/damp, dL/dphase from dL/dT (chain rule of amp exp(i phase))
+//   k_probe_grad       dL/dP_m = F^-1[accumulated spectrum gradient]              (M CTAs)
+//   k_scalar_grad      positions, tilts, dz from the per-wave partials
+#pragma once
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "fft_smem.cuh"
+#include "pty_internal.h"
+
+namespace pty {
+
+template <int N>
+struct Launch;
+template <>
+struct Launch<64> {
+  static constexpr int T = 256;
+};
+template <>
+struct Launch<128> {
+  static constexpr int T = 512;
+};
+
+// exp(i pi x); x is reduced modulo 2 in double precision before the float sincospi.
+__device__ __forceinline__ float2 expipi(double x) {
+  x = x - 2.0 * rint(0.5 * x);
+  float s, c;
+  sincospif((float)x, &s, &c);
+  return make_float2(c, s);
+}
+
+// Signed DFT frequency index of bin k.
+template <int N>
+__device__ __forceinline__ int signed_bin(int k) {
+  return k < N / 2 ? k : k - N;
+}
+
+// Patch corner round(pos) (half to even) and sub-pixel remainder; clamps and flags if outside.
+template <int N>
+__device__ __forceinline__ void patch_corner(const float* pos, int j, int H, int W, int* i0, int* i1,
+                                             float* d0, float* d1, int* status) {
+  const float p0 = pos[2 * j], p1 = pos[2 * j + 1];
+  float r0 = rintf(p0), r1 = rintf(p1);
+  *d0 = p0 - r0;
+  *d1 = p1 - r1;
+  const bool fin = isfinite(p0) && isfinite(p1);
+  const bool ok = fin && r0 >= 0.f && r1 >= 0.f && r0 + N <= (float)H && r1 + N <= (float)W;
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(status, PTY_EBOUNDS);
+    if (!fin) {
+      r0 = 0.f;
+      r1 = 0.f;
+      *d0 = 0.f;
+      *d1 = 0.f;
+    }
+    r0 = fminf(fmaxf(r0, 0.f), (float)(H - N));
+    r1 = fminf(fmaxf(r1, 0.f), (float)(W - N));
+  }
+  *i0 = (int)r0;
+  *i1 = (int)r1;
+}
+
+// Batch entry b's scan index; an index outside [0, Ntot) is flagged and replaced by 0.
+__device__ __forceinline__ int checked_index(const int32_t* idx, int b, int Ntot, int* status) {
+  int j = idx[b];
+  if (j < 0 || j >= Ntot) {
+    if (threadIdx.x == 0) atomicOr(status, PTY_EBOUNDS);
+    j = 0;
+  }
+  return j;
+}
+
+__device__ __forceinline__ void tilt_of(const float* tilt, int global_tilt, int j, float* t0, float* t1) {
+  const float* t = global_tilt ? tilt : tilt + 2 * j;
+  *t0 = t[0];
+  *t1 = t[1];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Object transmission and accumulator reset
+// ---------------------------------------------------------------------------------------------
+static __global__ void k_prepare_object(const float* __restrict__ amp, const float* __restrict__ phase,
+                                 float2* __restrict__ T, float2* __restrict__ gT, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float s, c;
+    sincosf(phase[i], &s, &c);
+    const float a = amp[i];
+    T[i] = make_float2(a * c, a * s);
+    if (gT) gT[i] = make_float2(0.f, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Probe spectra P^_m = F[P_m] (k-space layout); zero the probe-gradient accumulator.
+// ---------------------------------------------------------------------------------------------
+template <int N, int T>
+__global__ void __launch_bounds__(T) k_probe_spectrum(const float2* __restrict__ probe, float2* __restrict__ Phat,
+                                                      float2* __restrict__ gPhat) {
+  using F = Fft2<N, T>;
+  constexpr int RS = F::RS;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* s = sm;
+  float2* tw = s + N * RS;
+  const int m = blockIdx.x, tid = threadIdx.x;
+  build_twiddles<N>(tw);
+  const float2* P = probe + (size_t)m * N * N;
+  for (int e = tid; e < N * N; e += T) s[(e / N) * RS + e % N] = P[e];
+  __syncthreads();
+  F::forward(s, tw);
+  float2* out = Phat + (size_t)m * N * N;
+  float2* g = gPhat ? gPhat + (size_t)m * N * N : nullptr;
+  for (int e = tid; e < N * N; e += T) {
+    out[e] = s[(e / N) * RS + e % N];
+    if (g) g[e] = make_float2(0.f, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Forward: one CTA per (batch entry b, mode m)
+// ---------------------------------------------------------------------------------------------
+struct FwdArgs {
+  int M, Nz, H, W, Ntot, global_tilt;
+  float dx, lam;
+  const int32_t* idx;
+  const float *pos, *tilt, *dz;
+  const float2* T;
+  const float2* Phat;
+  float2* ckpt;
+  float2* vhat;
+  float2* Psi;
+  float* Imode;
+  int* status;
+};
+
+template <int N>
+__host__ __device__ constexpr size_t fwd_smem_bytes() {
+  return sizeof(float2) * ((size_t)N * (N + 1) + 5 * N);
+}
+
+template <int N, int T>
+__global__ void __launch_bounds__(T, 1) k_forward(FwdArgs a) {
+  using F = Fft2<N, T>;
+  constexpr int RS = F::RS;
+  constexpr int NN = N * N;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* s = sm;
+  float2* tw = s + N * RS;
+  float2* ra0 = tw + N;   // shift ramp along axis 0, carries 1/N^2 of the inverse DFT
+  float2* ra1 = ra0 + N;  // shift ramp along axis 1
+  float2* pm0 = ra1 + N;  // propagator factor along axis 0, carries 1/N^2
+  float2* pm1 = pm0 + N;  // propagator factor along axis 1
+  const int tid = threadIdx.x;
+  const int bm = blockIdx.x;
+  const int b = bm / a.M, m = bm % a.M;
+  const int j = checked_index(a.idx, b, a.Ntot, a.status);
+  int i0, i1;
+  float d0, d1, th0, th1;
+  patch_corner<N>(a.pos, j, a.H, a.W, &i0, &i1, &d0, &d1, a.status);
+  tilt_of(a.tilt, a.global_tilt, j, &th0, &th1);
+  const float dz = a.dz[0];
+
+  build_twiddles<N>(tw);
+  if (tid < N) {
+    const int q = signed_bin<N>(kbin<N>(tid));
+    const float inv_nn = 1.0f / (float)NN;
+    ra0[tid] = cscale(expipi(-2.0 * q * (double)d0 / N), inv_nn);
+    ra1[tid] = expipi(-2.0 * q * (double)d1 / N);
+    // Eq. 4 split into its two axes: exp(i pi (-lam dz k_a^2 + 2 dz k_a tan th_a))
+    const double k = q / (N * (double)a.dx);
+    const double base = -(double)a.lam * dz * k * k;
+    pm0[tid] = cscale(expipi(base + 2.0 * dz * k * tan((double)th0)), inv_nn);
+    pm1[tid] = expipi(base + 2.0 * dz * k * tan((double)th1));
+  }
+  __syncthreads();
+
+  // shifted probe P_j = F^-1[P^_m ramp]
+  const float2* Ph = a.Phat + (size_t)m * NN;
+  for (int e = tid; e < NN; e += T) {
+    const int r = e / N, c = e % N;
+    s[r * RS + c] = cmul(cmul(Ph[e], ra1[r]), ra0[c]);
+  }
+  __syncthreads();
+  F::inverse(s, tw);
+
+  for (int sl = 0; sl < a.Nz; ++sl) {
+    const float2* Ts = a.T + (size_t)sl * a.H * a.W + (size_t)i0 * a.W + i1;
+    float2* ck = a.ckpt ? a.ckpt + ((size_t)bm * a.Nz + sl) * NN : nullptr;
+#pragma unroll 4
+    for (int e = tid; e < NN; e += T) {
+      const int r = e / N, c = e % N;
+      float2 v = s[r * RS + c];
+      if (ck) __stcs(ck + e, v);
+      v = cmul(v, __ldg(Ts + (size_t)r * a.W + c));
+      s[r * RS + c] = v;
+    }
+    __syncthreads();
+    if (sl + 1 < a.Nz) {
+      F::forward(s, tw);
+      float2* vh = a.vhat ? a.vhat + ((size_t)bm * (a.Nz - 1) + sl) * NN : nullptr;
+      for (int e = tid; e < NN; e += T) {
+        const int r = e / N, c = e % N;
+        const float2 v = cmul(cmul(s[r * RS + c], pm1[r]), pm0[c]);
+        s[r * RS + c] = v;
+        if (vh) __stcs(vh + e, v);
+      }
+      __syncthreads();
+      F::inverse(s, tw);
+    }
+  }
+  // far field, orthonormal DFT
+  F::forward(s, tw);
+  const float inv_n = 1.0f / (float)N;
+  float2* Psi = a.Psi ? a.Psi + (size_t)bm * NN : nullptr;
+  float* Im = a.Imode + (size_t)bm * NN;
+  for (int e = tid; e < NN; e += T) {
+    const float2 v = cscale(s[(e / N) * RS + e % N], inv_n);
+    if (Psi) __stcs(Psi + e, v);
+    Im[e] = fmaf(v.x, v.x, v.y * v.y);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Loss: one CTA per pattern.  Sums modes, evaluates Eq. 5 or 6 per pixel and dL/dI up to the
+// batch-wide normaliser, and writes FP64 per-pattern sums.
+// ---------------------------------------------------------------------------------------------
+struct LossArgs {
+  int M, Ntot, loss;
+  int* status;
+  float p, eps;
+  const int32_t* idx;
+  const float* Imode;
+  const float* I_meas;
+  float* I_model;
+  float* u;
+  double* lpart;
+};
+
+template <int N>
+__host__ __device__ constexpr size_t loss_smem_bytes() {
+  return sizeof(float) * (size_t)N * (N + 1) + 64 * sizeof(double);
+}
+
+template <int T>
+__device__ __forceinline__ void block_sum2(double& x, double& y, double* red) {
+  for (int o = 16; o > 0; o >>= 1) {
+    x += __shfl_down_sync(0xffffffffu, x, o);
+    y += __shfl_down_sync(0xffffffffu, y, o);
+  }
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  if (l == 0) {
+    red[2 * w] = x;
+    red[2 * w + 1] = y;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sx = 0.0, sy = 0.0;
+    for (int i = 0; i < T / 32; ++i) {
+      sx += red[2 * i];
+      sy += red[2 * i + 1];
+    }
+    x = sx;
+    y = sy;
+  }
+}
+
+template <int N, int T>
+__global__ void __launch_bounds__(T) k_loss(LossArgs a) {
+  constexpr int RS = N + 1;
+  constexpr int NN = N * N;
+  extern __shared__ __align__(16) float lsm[];
+  float* L = lsm;
+  double* red = reinterpret_cast<double*>(lsm + N * RS + ((N * RS) & 1));
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const float* Im = a.Imode + (size_t)b * a.M * NN;
+  for (int e = tid; e < NN; e += T) {
+    float acc = 0.f;
+    for (int m = 0; m < a.M; ++m) acc += Im[(size_t)m * NN + e];
+    L[(e / N) * RS + e % N] = acc;
+  }
+  __syncthreads();
+  const float* Id = a.I_meas ? a.I_meas + (size_t)checked_index(a.idx, b, a.Ntot, a.status) * NN : nullptr;
+  const float p = a.p;
+  float sd = 0.f, st = 0.f;
+  for (int q = tid; q < NN; q += T) {
+    const int k0 = (q / N + N / 2) & (N - 1), k1 = (q % N + N / 2) & (N - 1);
+    const int l = kpos<N>(k1) * RS + kpos<N>(k0);
+    const float I = L[l];
+    if (a.I_model) a.I_model[(size_t)b * NN + q] = I;
+    if (Id) {
+      const float d = Id[q];
+      float Ip, Dp, dpow;
+      if (p == 1.0f) {
+        Ip = I;
+        Dp = d;
+        dpow = 1.0f;
+      } else if (p == 0.5f) {
+        Ip = sqrtf(fmaxf(I, 0.f));
+        Dp = sqrtf(fmaxf(d, 0.f));
+        dpow = I > 0.f ? 0.5f / Ip : 0.f;
+      } else {
+        Ip = powf(fmaxf(I, 0.f), p);
+        Dp = powf(fmaxf(d, 0.f), p);
+        dpow = I > 0.f ? p * powf(I, p - 1.0f) : 0.f;
+      }
+      float term, u;
+      if (a.loss == PTY_LOSS_POISSON) {
+        term = Dp * logf(Ip + a.eps) - Ip;
+        u = -(Dp / (Ip + a.eps) - 1.0f) * dpow;
+      } else {
+        const float df = Ip - Dp;
+        term = df * df;
+        u = df * dpow;
+      }
+      sd += Dp;
+      st += term;
+      L[l] = u;
+    }
+  }
+  __syncthreads();
+  if (a.u) {
+    for (int e = tid; e < NN; e += T) a.u[(size_t)b * NN + e] = L[(e / N) * RS + e % N];
+  }
+  if (a.lpart) {
+    double x = sd, y = st;
+    block_sum2<T>(x, y, red);
+    if (tid == 0) {
+      a.lpart[2 * b] = x;
+      a.lpart[2 * b + 1] = y;
+    }
+  }
+}
+
+// Batch loss (Eq. 5 / 6) and the normaliser of dL/dI, in FP64, fixed summation order.
+static __global__ void k_loss_finalize(const double* __restrict__ lpart, int B, int loss, double DB, double* scal,
+                                double* loss_out, int* status) {
+  __shared__ double red[64];
+  double x = 0.0, y = 0.0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    x += lpart[2 * b];
+    y += lpart[2 * b + 1];
+  }
+  block_sum2<256>(x, y, red);
+  if (threadIdx.x == 0) {
+    double Lv, scale;
+    if (loss == PTY_LOSS_POISSON) {
+      Lv = -y / x;
+      scale = 1.0 / x;
+    } else {
+      Lv = sqrt(DB * y) / x;
+      scale = y > 0.0 ? sqrt(DB) / (sqrt(y) * x) : 0.0;
+    }
+    if (!isfinite(Lv) || !isfinite(scale)) {
+      atomicOr(status, PTY_ENONFINITE);
+      scale = 0.0;
+    }
+    scal[0] = scale;
+    scal[1] = Lv;
+    if (loss_out) *loss_out = Lv;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Adjoint: one CTA per (b, m), slices in reverse.
+// ---------------------------------------------------------------------------------------------
+struct AdjArgs {
+  int M, Nz, H, W, Ntot, global_tilt, grad_mask;
+  float dx, lam;
+  const int32_t* idx;
+  const float *pos, *tilt, *dz;
+  const float2* T;
+  const float2* Phat;
+  const float2* ckpt;
+  const float2* vhat;
+  const float2* Psi;
+  const float* u;
+  const double* scal;
+  float2* gT;
+  float2* gPhat;
+  double* spart;
+  int* status;
+};
+
+template <int N, int T>
+__host__ __device__ constexpr size_t adj_smem_bytes() {
+  return sizeof(float2) * ((size_t)N * (N + 1) + 5 * N) + sizeof(float) * 4 * N + sizeof(double) * 5 * (T / 32);
+}
+
+template <int N, int T>
+__global__ void __launch_bounds__(T, 1) k_adjoint(AdjArgs a) {
+  using F = Fft2<N, T>;
+  constexpr int RS = F::RS;
+  constexpr int NN = N * N;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* s = sm;
+  float2* tw = s + N * RS;
+  float2* cm0 = tw + N;   // conj propagator, axis 0, carries 1/N^2
+  float2* cm1 = cm0 + N;  // conj propagator, axis 1
+  float2* cr0 = cm1 + N;  // conj shift ramp, axis 0 (no scale)
+  float2* cr1 = cr0 + N;  // conj shift ramp, axis 1
+  float* W0 = reinterpret_cast<float*>(cr1 + N);  // per k-space column: sum over rows of w (dz/tilt)
+  float* W1 = W0 + N;                             // per k-space row: sum over columns of w
+  float* X0 = W1 + N;                             // same for the position term
+  float* X1 = X0 + N;
+  double* red = reinterpret_cast<double*>(X1 + N);
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int bm = blockIdx.x;
+  const int b = bm / a.M, m = bm % a.M;
+  const int j = checked_index(a.idx, b, a.Ntot, a.status);
+  int i0, i1;
+  float d0, d1, th0, th1;
+  patch_corner<N>(a.pos, j, a.H, a.W, &i0, &i1, &d0, &d1, a.status);
+  tilt_of(a.tilt, a.global_tilt, j, &th0, &th1);
+  const float dz = a.dz[0];
+  const bool want_obj = (a.grad_mask & (PTY_GRAD_AMP | PTY_GRAD_PHASE)) != 0;
+  const bool want_probe = (a.grad_mask & PTY_GRAD_PROBE) != 0;
+  const bool want_pos = (a.grad_mask & PTY_GRAD_POS) != 0;
+  const bool want_prop = (a.grad_mask & (PTY_GRAD_DZ | PTY_GRAD_TILT)) != 0 && a.vhat != nullptr;
+
+  build_twiddles<N>(tw);
+  if (tid < N) {
+    const int q = signed_bin<N>(kbin<N>(tid));
+    const float inv_nn = 1.0f / (float)NN;
+    const double k = q / (N * (double)a.dx);
+    const double base = -(double)a.lam * dz * k * k;
+    cm0[tid] = cscale(cconj(expipi(base + 2.0 * dz * k * tan((double)th0))), inv_nn);
+    cm1[tid] = cconj(expipi(base + 2.0 * dz * k * tan((double)th1)));
+    cr0[tid] = expipi(2.0 * q * (double)d0 / N);
+    cr1[tid] = expipi(2.0 * q * (double)d1 / N);
+    W0[tid] = 0.f;
+    W1[tid] = 0.f;
+    X0[tid] = 0.f;
+    X1[tid] = 0.f;
+  }
+  __syncthreads();
+
+  // g_Psi = 2 dL/dI Psi ; g_psi = F_ortho^-1[g_Psi] = (1/N) unnormalised inverse
+  const float gs = (float)(2.0 * a.scal[0] / N);
+  {
+    const float* u = a.u + (size_t)b * NN;
+    const float2* Psi = a.Psi + (size_t)bm * NN;
+    for (int e = tid; e < NN; e += T) s[(e / N) * RS + e % N] = cscale(__ldcs(Psi + e), gs * u[e]);
+  }
+  __syncthreads();
+  F::inverse(s, tw);
+
+  float wcol = 0.f;  // this thread's column partial of w (its column is tid % N in every pass)
+  for (int sl = a.Nz - 1; sl >= 0; --sl) {
+    const float2* Ts = a.T + (size_t)sl * a.H * a.W + (size_t)i0 * a.W + i1;
+    float2* gTs = a.gT + (size_t)sl * a.H * a.W + (size_t)i0 * a.W + i1;
+    const float2* ck = a.ckpt + ((size_t)bm * a.Nz + sl) * NN;
+#pragma unroll 4
+    for (int e = tid; e < NN; e += T) {
+      const int r = e / N, c = e % N;
+      const float2 g = s[r * RS + c];
+      if (want_obj) {
+        const float2 psi = __ldcs(ck + e);
+        atomicAdd(gTs + (size_t)r * a.W + c, cmulc(psi, g));
+      }
+      s[r * RS + c] = cmulc(__ldg(Ts + (size_t)r * a.W + c), g);
+    }
+    __syncthreads();
+    if (sl > 0) {
+      F::forward(s, tw);
+      const float2* vh = want_prop ? a.vhat + ((size_t)bm * (a.Nz - 1) + sl - 1) * NN : nullptr;
+      for (int e = tid; e < NN; e += T) {
+        const int r = e / N, c = e % N;
+        const float2 gh = s[r * RS + c];
+        if (vh) {
+          const float2 v = __ldcs(vh + e);
+          float w = gh.x * v.y - gh.y * v.x;  // Im(conj(g^) v)
+          wcol += w;
+          for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+          if (lane == 0) atomicAdd(W1 + r, w);
+        }
+        s[r * RS + c] = cmul(cmul(gh, cm1[r]), cm0[c]);
+      }
+      __syncthreads();
+      F::inverse(s, tw);
+    }
+  }
+  if (want_prop) atomicAdd(W0 + (tid % N), wcol);
+
+  // s = dL/dP_j (natural).  P_j = F^-1[P^ R]  ->  spectrum gradient and position gradient.
+  float xcol = 0.f;
+  if (want_probe || want_pos) {
+    F::forward(s, tw);
+    const float2* Ph = a.Phat + (size_t)m * NN;
+    float2* gP = a.gPhat + (size_t)m * NN;
+    for (int e = tid; e < NN; e += T) {
+      const int r = e / N, c = e % N;
+      const float2 gh = s[r * RS + c];
+      const float2 cr = cmul(cr1[r], cr0[c]);  // conj(R)
+      if (want_probe) atomicAdd(gP + e, cmul(cr, gh));
+      if (want_pos) {
+        const float2 PR = cmulc(cr, Ph[e]);  // R P^
+        float w = gh.x * PR.y - gh.y * PR.x;  // Im(conj(g^) R P^)
+        xcol += w;
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0) atomicAdd(X1 + r, w);
+      }
+    }
+    if (want_pos) atomicAdd(X0 + (tid % N), xcol);
+  }
+  __syncthreads();
+
+  // FP64 dot products of the per-axis sums with the analytic factors.
+  double gp0 = 0.0, gp1 = 0.0, gt0 = 0.0, gt1 = 0.0, gdz = 0.0;
+  if (tid < N) {
+    const int q = signed_bin<N>(kbin<N>(tid));
+    const double k = q / (N * (double)a.dx);
+    const double PI = 3.14159265358979323846;
+    const double t0 = tan((double)th0), t1 = tan((double)th1);
+    const double c0 = cos((double)th0), c1 = cos((double)th1);
+    const double e0 = -PI * a.lam * k * k + 2.0 * PI * k * t0;
+    const double e1 = -PI * a.lam * k * k + 2.0 * PI * k * t1;
+    const double w0 = W0[tid], w1 = W1[tid];
+    gdz = -(e0 * w0 + e1 * w1);
+    gt0 = -(2.0 * PI * dz * k / (c0 * c0)) * w0;
+    gt1 = -(2.0 * PI * dz * k / (c1 * c1)) * w1;
+    const double f = (double)q / N;
+    const double sc = 2.0 * PI / ((double)NN);
+    gp0 = sc * f * X0[tid];
+    gp1 = sc * f * X1[tid];
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    gp0 += __shfl_down_sync(0xffffffffu, gp0, o);
+    gp1 += __shfl_down_sync(0xffffffffu, gp1, o);
+    gt0 += __shfl_down_sync(0xffffffffu, gt0, o);
+    gt1 += __shfl_down_sync(0xffffffffu, gt1, o);
+    gdz += __shfl_down_sync(0xffffffffu, gdz, o);
+  }
+  const int w = tid / 32;
+  if (lane == 0 && w < N / 32) {
+    red[5 * w + 0] = gp0;
+    red[5 * w + 1] = gp1;
+    red[5 * w + 2] = gt0;
+    red[5 * w + 3] = gt1;
+    red[5 * w + 4] = gdz;
+  }
+  __syncthreads();
+  if (tid < 5) {
+    double acc = 0.0;
+    for (int i = 0; i < N / 32; ++i) acc += red[5 * i + tid];
+    a.spart[(size_t)bm * 5 + tid] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Finalisers
+// ---------------------------------------------------------------------------------------------
+// dL/damp = Re(conj(e^{i phase}) dL/dT), dL/dphase = Re(conj(i T) dL/dT) = Im(conj(T) dL/dT)
+static __global__ void k_object_grad(const float* __restrict__ amp, const float* __restrict__ phase,
+                              const float2* __restrict__ gT, float* __restrict__ g_amp, float* __restrict__ g_phase,
+                              int accumulate, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    float s, c;
+    sincosf(phase[i], &s, &c);
+    const float2 g = gT[i];
+    const float a = amp[i];
+    const float ga = fmaf(c, g.x, s * g.y);
+    const float gp = a * fmaf(c, g.y, -s * g.x);
+    if (g_amp) g_amp[i] = accumulate ? g_amp[i] + ga : ga;
+    if (g_phase) g_phase[i] = accumulate ? g_phase[i] + gp : gp;
+  }
+}
+
+// The accumulator holds A = sum_j conj(R_j) F[dL/dP_j] (R_j the shift ramp of position j).  The
+// probe-spectrum gradient is A / N^2 and dL/dP_m = F^H[A / N^2] = (plain inverse sum of A) / N^2.
+template <int N, int T>
+__global__ void __launch_bounds__(T) k_probe_grad(const float2* __restrict__ gPhat, float2* __restrict__ g_probe,
+                                                  int accumulate) {
+  using F = Fft2<N, T>;
+  constexpr int RS = F::RS;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* s = sm;
+  float2* tw = s + N * RS;
+  const int m = blockIdx.x, tid = threadIdx.x;
+  build_twiddles<N>(tw);
+  const float2* G = gPhat + (size_t)m * N * N;
+  for (int e = tid; e < N * N; e += T) s[(e / N) * RS + e % N] = G[e];
+  __syncthreads();
+  F::inverse(s, tw);
+  const float sc = 1.0f / (float)(N * N);
+  float2* out = g_probe + (size_t)m * N * N;
+  for (int e = tid; e < N * N; e += T) {
+    const float2 v = cscale(s[(e / N) * RS + e % N], sc);
+    out[e] = accumulate ? cadd(out[e], v) : v;
+  }
+}
+
+// Positions, tilts (summed over modes; over positions too for a global tilt) and dz.
+static __global__ void k_scalar_grad(const double* __restrict__ spart, const int32_t* __restrict__ idx, int B, int M,
+                              int Ntot, int global_tilt, int grad_mask, float* g_pos, float* g_tilt, float* g_dz,
+                              int accumulate) {
+  __shared__ double red[64];
+  double dzs = 0.0, t0s = 0.0;
+  double t1s = 0.0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    double p0 = 0.0, p1 = 0.0, a0 = 0.0, a1 = 0.0;
+    for (int m = 0; m < M; ++m) {
+      const double* sp = spart + ((size_t)b * M + m) * 5;
+      p0 += sp[0];
+      p1 += sp[1];
+      a0 += sp[2];
+      a1 += sp[3];
+      dzs += sp[4];
+    }
+    const int j = idx[b];
+    if (j < 0 || j >= Ntot) continue;  // flagged by the forward kernel
+    if ((grad_mask & PTY_GRAD_POS) && g_pos) {
+      atomicAdd(g_pos + 2 * j, (float)p0);
+      atomicAdd(g_pos + 2 * j + 1, (float)p1);
+    }
+    if ((grad_mask & PTY_GRAD_TILT) && g_tilt) {
+      if (global_tilt) {
+        t0s += a0;
+        t1s += a1;
+      } else {
+        atomicAdd(g_tilt + 2 * j, (float)a0);
+        atomicAdd(g_tilt + 2 * j + 1, (float)a1);
+      }
+    }
+  }
+  double x = dzs, y = t0s;
+  block_sum2<256>(x, y, red);
+  __syncthreads();
+  double z = t1s, dummy = 0.0;
+  block_sum2<256>(z, dummy, red);
+  if (threadIdx.x == 0) {
+    if ((grad_mask & PTY_GRAD_DZ) && g_dz) g_dz[0] = accumulate ? g_dz[0] + (float)x : (float)x;
+    if ((grad_mask & PTY_GRAD_TILT) && g_tilt && global_tilt) {
+      g_tilt[0] = accumulate ? g_tilt[0] + (float)y : (float)y;
+      g_tilt[1] = accumulate ? g_tilt[1] + (float)z : (float)z;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Host side: one pass of the pipeline for size N
+// ---------------------------------------------------------------------------------------------
+#define PTY_LAUNCH_CHECK(what, stage)                                     \
+  do {                                                                    \
+    cudaError_t e_ = cudaGetLastError();                                  \
+    if (e_ != cudaSuccess) {                                              \
+      set_error("%s launch failed: %s", what, cudaGetErrorString(e_));    \
+      return PTY_ECUDA;                                                   \
+    }                                                                     \
+    if (stage >= 0) {                                                     \
+      note_launch();                                                      \
+      prof_mark(stage, st);                                               \
+    }                                                                     \
+  } while (0)
+
+template <int N>
+int run_pipeline(const Problem& pb) {
+  constexpr int T = Launch<N>::T;
+  constexpr int NN = N * N;
+  const Workspace& ws = pb.ws;
+  cudaStream_t st = pb.stream;
+  const bool grad = pb.mode == MODE_GRAD;
+  const int gm = pb.grad_mask;
+  const bool want_obj = grad && (gm & (PTY_GRAD_AMP | PTY_GRAD_PHASE));
+  const bool want_probe = grad && (gm & PTY_GRAD_PROBE);
+  const bool want_prop = grad && (gm & (PTY_GRAD_DZ | PTY_GRAD_TILT)) && pb.Nz > 1;
+
+  const size_t fsm = fwd_smem_bytes<N>();
+  const size_t asm_ = adj_smem_bytes<N, T>();
+  const size_t lsm = loss_smem_bytes<N>();
+  const size_t psm = sizeof(float2) * ((size_t)N * (N + 1) + N);
+  {  // cheap host calls; repeated every pass so that every device a caller uses gets them
+    if (cudaFuncSetAttribute(k_forward<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_adjoint<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_) != cudaSuccess ||
+        cudaFuncSetAttribute(k_loss<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_probe_spectrum<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_probe_grad<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess) {
+      set_error("cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return PTY_ECUDA;
+    }
+  }
+
+  const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
+  prof_begin(st);
+  k_prepare_object<<<(unsigned)((nobj + 255) / 256 < 152 * 16 ? (nobj + 255) / 256 : 152 * 16), 256, 0, st>>>(
+      pb.amp, pb.phase, ws.T, want_obj ? ws.gT : nullptr, nobj);
+  PTY_LAUNCH_CHECK("k_prepare_object", 0);
+  k_probe_spectrum<N, T><<<pb.M, T, psm, st>>>(pb.probe, ws.Phat, want_probe ? ws.gPhat : nullptr);
+  PTY_LAUNCH_CHECK("k_probe_spectrum", 1);
+
+  if (pb.B > 0) {
+    FwdArgs fa;
+    fa.M = pb.M;
+    fa.Nz = pb.Nz;
+    fa.H = pb.H;
+    fa.W = pb.W;
+    fa.Ntot = pb.Ntot;
+    fa.global_tilt = pb.global_tilt;
+    fa.dx = pb.dx;
+    fa.lam = pb.lam;
+    fa.idx = pb.idx;
+    fa.pos = pb.pos;
+    fa.tilt = pb.tilt;
+    fa.dz = pb.dz;
+    fa.T = ws.T;
+    fa.Phat = ws.Phat;
+    fa.ckpt = want_obj ? ws.ckpt : nullptr;
+    fa.vhat = want_prop ? ws.vhat : nullptr;
+    fa.Psi = grad ? ws.Psi : nullptr;
+    fa.Imode = ws.Imode;
+    fa.status = ws.status;
+    k_forward<N, T><<<pb.B * pb.M, T, fsm, st>>>(fa);
+    PTY_LAUNCH_CHECK("k_forward", 2);
+
+    LossArgs la;
+    la.M = pb.M;
+    la.Ntot = pb.Ntot;
+    la.status = ws.status;
+    la.loss = pb.loss;
+    la.p = pb.p;
+    la.eps = pb.eps;
+    la.idx = pb.idx;
+    la.Imode = ws.Imode;
+    la.I_meas = grad ? pb.I_meas : nullptr;
+    la.I_model = pb.I_model;
+    la.u = grad ? ws.u : nullptr;
+    la.lpart = grad ? ws.lpart : nullptr;
+    k_loss<N, T><<<pb.B, T, lsm, st>>>(la);
+    PTY_LAUNCH_CHECK("k_loss", 3);
+  }
+  if (!grad) return PTY_OK;
+
+  if (pb.B > 0) {
+    k_loss_finalize<<<1, 256, 0, st>>>(ws.lpart, pb.B, pb.loss, (double)pb.B * NN, ws.scal, pb.loss_out, ws.status);
+    PTY_LAUNCH_CHECK("k_loss_finalize", 4);
+    AdjArgs aa;
+    aa.M = pb.M;
+    aa.Nz = pb.Nz;
+    aa.H = pb.H;
+    aa.W = pb.W;
+    aa.Ntot = pb.Ntot;
+    aa.global_tilt = pb.global_tilt;
+    aa.grad_mask = gm;
+    aa.dx = pb.dx;
+    aa.lam = pb.lam;
+    aa.idx = pb.idx;
+    aa.pos = pb.pos;
+    aa.tilt = pb.tilt;
+    aa.dz = pb.dz;
+    aa.T = ws.T;
+    aa.Phat = ws.Phat;
+    aa.ckpt = ws.ckpt;
+    aa.vhat = want_prop ? ws.vhat : nullptr;
+    aa.Psi = ws.Psi;
+    aa.u = ws.u;
+    aa.scal = ws.scal;
+    aa.gT = ws.gT;
+    aa.gPhat = ws.gPhat;
+    aa.spart = ws.spart;
+    aa.status = ws.status;
+    k_adjoint<N, T><<<pb.B * pb.M, T, asm_, st>>>(aa);
+    PTY_LAUNCH_CHECK("k_adjoint", 5);
+  } else if (pb.loss_out) {
+    cudaMemsetAsync(pb.loss_out, 0, sizeof(double), st);
+  }
+
+  if (want_obj) {
+    const unsigned blocks = (unsigned)((nobj + 255) / 256 < 152 * 16 ? (nobj + 255) / 256 : 152 * 16);
+    k_object_grad<<<blocks, 256, 0, st>>>(pb.amp, pb.phase, ws.gT, (gm & PTY_GRAD_AMP) ? pb.g_amp : nullptr,
+                                          (gm & PTY_GRAD_PHASE) ? pb.g_phase : nullptr, pb.accumulate, nobj);
+    PTY_LAUNCH_CHECK("k_object_grad", 6);
+  }
+  if (want_probe) {
+    k_probe_grad<N, T><<<pb.M, T, psm, st>>>(ws.gPhat, pb.g_probe, pb.accumulate);
+    PTY_LAUNCH_CHECK("k_probe_grad", 7);
+  }
+  const bool want_scalar = gm & (PTY_GRAD_POS | PTY_GRAD_TILT | PTY_GRAD_DZ);
+  if (want_scalar) {
+    if (!pb.accumulate) {
+      if ((gm & PTY_GRAD_POS) && pb.g_pos) cudaMemsetAsync(pb.g_pos, 0, sizeof(float) * 2 * pb.Ntot, st);
+      if ((gm & PTY_GRAD_TILT) && pb.g_tilt && !pb.global_tilt)
+        cudaMemsetAsync(pb.g_tilt, 0, sizeof(float) * 2 * pb.Ntot, st);
+    }
+    if (pb.B > 0) {
+      k_scalar_grad<<<1, 256, 0, st>>>(ws.spart, pb.idx, pb.B, pb.M, pb.Ntot, pb.global_tilt, gm, pb.g_pos, pb.g_tilt,
+                                       pb.g_dz, pb.accumulate);
+      PTY_LAUNCH_CHECK("k_scalar_grad", 8);
+    } else if (!pb.accumulate) {
+      if ((gm & PTY_GRAD_DZ) && pb.g_dz) cudaMemsetAsync(pb.g_dz, 0, sizeof(float), st);
+      if ((gm & PTY_GRAD_TILT) && pb.g_tilt && pb.global_tilt) cudaMemsetAsync(pb.g_tilt, 0, 2 * sizeof(float), st);
+    }
+  }
+  PTY_LAUNCH_CHECK("pipeline", -1);
+  return PTY_OK;
+}
+
+}  // namespace pty

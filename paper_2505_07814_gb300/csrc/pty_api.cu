@@ -1,0 +1,387 @@
+// pty_api.cu -- the C ABI declared in include/pty.h: host-side validation, workspace layout,
+// dispatch on the window size N, and the Adam update.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "pty_internal.h"
+
+namespace pty {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Diagnostics
+// ---------------------------------------------------------------------------------------------
+static long long g_launches = 0;
+static const int kProfCalls = 256;
+static bool g_prof_on = false;
+static int g_prof_calls = 0;
+static cudaEvent_t g_prof_ev[kProfCalls][PTY_PROF_STAGES + 1];
+static bool g_prof_have[kProfCalls][PTY_PROF_STAGES + 1];
+static bool g_prof_created = false;
+
+void note_launch() { __atomic_add_fetch(&g_launches, 1, __ATOMIC_RELAXED); }
+
+void prof_begin(cudaStream_t st) {
+  if (!g_prof_on || g_prof_calls >= kProfCalls) return;
+  for (int k = 0; k <= PTY_PROF_STAGES; ++k) g_prof_have[g_prof_calls][k] = false;
+  cudaEventRecord(g_prof_ev[g_prof_calls][0], st);
+  g_prof_have[g_prof_calls][0] = true;
+  ++g_prof_calls;
+}
+
+void prof_mark(int stage, cudaStream_t st) {
+  if (!g_prof_on || g_prof_calls == 0 || g_prof_calls > kProfCalls) return;
+  const int c = g_prof_calls - 1;
+  cudaEventRecord(g_prof_ev[c][stage + 1], st);
+  g_prof_have[c][stage + 1] = true;
+}
+
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspace* out) {
+  const size_t NN = (size_t)g.N * g.N;
+  const size_t nobj = (size_t)g.Nz * g.H * g.W;
+  const bool grad = mode == MODE_GRAD;
+  const bool want_obj = grad && (g.grad_mask & (PTY_GRAD_AMP | PTY_GRAD_PHASE));
+  const bool want_prop = grad && (g.grad_mask & (PTY_GRAD_DZ | PTY_GRAD_TILT)) && g.Nz > 1;
+  const bool want_probe = grad && (g.grad_mask & PTY_GRAD_PROBE);
+  size_t off = 0;
+  Workspace w;
+  memset(&w, 0, sizeof(w));
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += align_up(bytes);
+    return p;
+  };
+  w.status = (int*)take(sizeof(int) * 64);
+  w.scal = (double*)take(sizeof(double) * 4);
+  w.T = (float2*)take(sizeof(float2) * nobj);
+  w.Phat = (float2*)take(sizeof(float2) * g.M * NN);
+  w.Imode = (float*)take(sizeof(float) * (size_t)B * g.M * NN);
+  if (grad) {
+    if (want_obj) w.ckpt = (float2*)take(sizeof(float2) * (size_t)B * g.M * g.Nz * NN);
+    if (want_prop) w.vhat = (float2*)take(sizeof(float2) * (size_t)B * g.M * (g.Nz - 1) * NN);
+    w.Psi = (float2*)take(sizeof(float2) * (size_t)B * g.M * NN);
+    w.u = (float*)take(sizeof(float) * (size_t)B * NN);
+    w.lpart = (double*)take(sizeof(double) * 2 * (size_t)(B > 0 ? B : 1));
+    if (want_obj) w.gT = (float2*)take(sizeof(float2) * nobj);
+    if (want_probe) w.gPhat = (float2*)take(sizeof(float2) * g.M * NN);
+    w.spart = (double*)take(sizeof(double) * 5 * (size_t)(B > 0 ? B : 1) * g.M);
+  }
+  if (out) *out = w;
+  return off;
+}
+
+static bool supported_N(int N) { return N == 64 || N == 128; }
+
+static int validate_geom(const pty_geom* g) {
+  if (!g) {
+    set_error("geometry is NULL");
+    return PTY_EINVAL;
+  }
+  if (!supported_N(g->N)) {
+    set_error("N = %d is not supported (64 or 128)", g->N);
+    return PTY_EINVAL;
+  }
+  if (g->M < 1 || g->Nz < 1 || g->H < g->N || g->W < g->N || g->Ntot < 0) {
+    set_error("bad shape: M=%d Nz=%d H=%d W=%d Ntot=%d (need M,Nz >= 1, H,W >= N)", g->M, g->Nz, g->H, g->W,
+              g->Ntot);
+    return PTY_EINVAL;
+  }
+  if (!(g->dx > 0.f) || !(g->lambda > 0.f) || !isfinite(g->dx) || !isfinite(g->lambda)) {
+    set_error("dx and lambda must be positive and finite");
+    return PTY_EINVAL;
+  }
+  if (g->loss != PTY_LOSS_POISSON && g->loss != PTY_LOSS_GAUSSIAN) {
+    set_error("unknown loss kind %d", g->loss);
+    return PTY_EINVAL;
+  }
+  if ((g->grad_mask & ~PTY_GRAD_ALL) != 0) {
+    set_error("unknown bits in grad_mask 0x%x", g->grad_mask);
+    return PTY_EINVAL;
+  }
+  if ((double)g->Nz * g->H * g->W > 4.0e9) {
+    set_error("object too large");
+    return PTY_EINVAL;
+  }
+  return PTY_OK;
+}
+
+static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+#define REQUIRE(cond, ...)     \
+  do {                         \
+    if (!(cond)) {             \
+      set_error(__VA_ARGS__);  \
+      return PTY_EINVAL;       \
+    }                          \
+  } while (0)
+
+static int prepare(const pty_geom* g, int B, int mode, const int32_t* idx, const float* amp, const float* phase,
+                   const float* probe, const float* pos, const float* tilt, const float* dz, void* ws,
+                   size_t ws_bytes, void* stream, Problem* pb) {
+  int rc = validate_geom(g);
+  if (rc) return rc;
+  REQUIRE(B >= 0, "batch size %d < 0", B);
+  REQUIRE((double)B * g->M < 2.0e9, "batch too large");
+  REQUIRE(amp && phase && probe && pos && tilt && dz, "a parameter pointer is NULL");
+  REQUIRE(B == 0 || idx, "idx is NULL");
+  REQUIRE(B == 0 || g->Ntot >= 1, "a non-empty batch needs Ntot >= 1");
+  REQUIRE(ws, "workspace is NULL");
+  REQUIRE(aligned(probe, 8) && aligned(ws, 256), "probe must be 8-byte and workspace 256-byte aligned");
+  REQUIRE(aligned(amp, 4) && aligned(phase, 4) && aligned(pos, 4) && aligned(tilt, 4) && aligned(dz, 4),
+          "float arrays must be 4-byte aligned");
+  const size_t need = layout_workspace(*g, B, mode, nullptr, nullptr);
+  if (ws_bytes < need) {
+    set_error("workspace has %zu bytes, %zu needed", ws_bytes, need);
+    return PTY_EWORKSPACE;
+  }
+  memset(pb, 0, sizeof(*pb));
+  pb->N = g->N;
+  pb->M = g->M;
+  pb->Nz = g->Nz;
+  pb->H = g->H;
+  pb->W = g->W;
+  pb->Ntot = g->Ntot;
+  pb->B = B;
+  pb->dx = g->dx;
+  pb->lam = g->lambda;
+  pb->loss = g->loss;
+  pb->p = g->p > 0.f ? g->p : (g->loss == PTY_LOSS_POISSON ? 1.0f : 0.5f);
+  pb->eps = g->eps;
+  pb->grad_mask = g->grad_mask;
+  pb->global_tilt = g->global_tilt ? 1 : 0;
+  pb->mode = mode;
+  pb->idx = idx;
+  pb->amp = amp;
+  pb->phase = phase;
+  pb->probe = reinterpret_cast<const float2*>(probe);
+  pb->pos = pos;
+  pb->tilt = tilt;
+  pb->dz = dz;
+  pb->stream = (cudaStream_t)stream;
+  layout_workspace(*g, B, mode, (char*)ws, &pb->ws);
+  return PTY_OK;
+}
+
+// Clears the status word, then runs the pipeline.  First CUDA call of every entry point.
+static int dispatch(const Problem& pb) {
+  if (cudaMemsetAsync(pb.ws.status, 0, sizeof(int), pb.stream) != cudaSuccess) {
+    set_error("cudaMemsetAsync failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return PTY_ECUDA;
+  }
+  switch (pb.N) {
+    case 64: return run_pipeline<64>(pb);
+    case 128: return run_pipeline<128>(pb);
+    default: set_error("N = %d not supported", pb.N); return PTY_EINVAL;
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Adam (PyTorch semantics), one launch over every enabled parameter.
+// ---------------------------------------------------------------------------------------------
+struct AdamSeg {
+  float* p;
+  const float* g;
+  float* m;
+  float* v;
+  size_t n;
+  float lr;
+};
+struct AdamArgs {
+  AdamSeg seg[6];
+  int nseg;
+  float beta1, beta2, eps, bc1, bc2;
+};
+
+__global__ void k_adam(AdamArgs a) {
+  for (int k = 0; k < a.nseg; ++k) {
+    const AdamSeg s = a.seg[k];
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < s.n; i += (size_t)gridDim.x * blockDim.x) {
+      const float g = s.g[i];
+      const float m = a.beta1 * s.m[i] + (1.f - a.beta1) * g;
+      const float v = a.beta2 * s.v[i] + (1.f - a.beta2) * g * g;
+      s.m[i] = m;
+      s.v[i] = v;
+      const float mh = m / a.bc1;
+      const float vh = v / a.bc2;
+      s.p[i] -= s.lr * mh / (sqrtf(vh) + a.eps);
+    }
+  }
+}
+
+}  // namespace pty
+
+using namespace pty;
+
+extern "C" {
+
+size_t pty_workspace_size(const pty_geom* geom, int B) {
+  if (validate_geom(geom) != PTY_OK || B < 0) return 0;
+  return layout_workspace(*geom, B, MODE_GRAD, nullptr, nullptr);
+}
+
+int pty_forward(const pty_geom* geom, int B, const int32_t* idx, const float* amp, const float* phase,
+                const float* probe, const float* pos, const float* tilt, const float* dz, float* I_model, void* ws,
+                size_t ws_bytes, void* stream) {
+  Problem pb;
+  int rc = prepare(geom, B, MODE_FORWARD, idx, amp, phase, probe, pos, tilt, dz, ws, ws_bytes, stream, &pb);
+  if (rc) return rc;
+  REQUIRE(B == 0 || I_model, "I_model is NULL");
+  pb.I_model = I_model;
+  return dispatch(pb);
+}
+
+int pty_loss_grad(const pty_geom* geom, int B, const int32_t* idx, const float* amp, const float* phase,
+                  const float* probe, const float* pos, const float* tilt, const float* dz, const float* I_meas,
+                  double* loss, float* I_model, float* g_amp, float* g_phase, float* g_probe, float* g_pos,
+                  float* g_tilt, float* g_dz, int accumulate, void* ws, size_t ws_bytes, void* stream) {
+  Problem pb;
+  int rc = prepare(geom, B, MODE_GRAD, idx, amp, phase, probe, pos, tilt, dz, ws, ws_bytes, stream, &pb);
+  if (rc) return rc;
+  const int gm = geom->grad_mask;
+  REQUIRE(B == 0 || I_meas, "I_meas is NULL");
+  REQUIRE(!(gm & PTY_GRAD_AMP) || g_amp, "g_amp is NULL but PTY_GRAD_AMP is requested");
+  REQUIRE(!(gm & PTY_GRAD_PHASE) || g_phase, "g_phase is NULL but PTY_GRAD_PHASE is requested");
+  REQUIRE(!(gm & PTY_GRAD_PROBE) || (g_probe && aligned(g_probe, 8)), "g_probe is NULL or misaligned");
+  REQUIRE(!(gm & PTY_GRAD_POS) || g_pos, "g_pos is NULL but PTY_GRAD_POS is requested");
+  REQUIRE(!(gm & PTY_GRAD_TILT) || g_tilt, "g_tilt is NULL but PTY_GRAD_TILT is requested");
+  REQUIRE(!(gm & PTY_GRAD_DZ) || g_dz, "g_dz is NULL but PTY_GRAD_DZ is requested");
+  pb.I_meas = I_meas;
+  pb.loss_out = loss;
+  pb.I_model = I_model;
+  pb.g_amp = g_amp;
+  pb.g_phase = g_phase;
+  pb.g_probe = reinterpret_cast<float2*>(g_probe);
+  pb.g_pos = g_pos;
+  pb.g_tilt = g_tilt;
+  pb.g_dz = g_dz;
+  pb.accumulate = accumulate ? 1 : 0;
+  return dispatch(pb);
+}
+
+int pty_adam_update(const pty_geom* geom, float* amp, float* phase, float* probe, float* pos, float* tilt,
+                    float* dz, const float* g_amp, const float* g_phase, const float* g_probe, const float* g_pos,
+                    const float* g_tilt, const float* g_dz, const pty_adam* adam, int step, void* stream) {
+  int rc = validate_geom(geom);
+  if (rc) return rc;
+  REQUIRE(adam, "adam state is NULL");
+  REQUIRE(step >= 1, "Adam step count must be >= 1");
+  const size_t nobj = (size_t)geom->Nz * geom->H * geom->W;
+  const size_t nprobe = 2 * (size_t)geom->M * geom->N * geom->N;
+  const size_t ntilt = geom->global_tilt ? 2 : 2 * (size_t)geom->Ntot;
+  AdamArgs a;
+  memset(&a, 0, sizeof(a));
+  const int gm = geom->grad_mask;
+  struct {
+    int bit;
+    float* p;
+    const float* g;
+    float *m, *v;
+    size_t n;
+    float lr;
+    const char* name;
+  } c[6] = {
+      {PTY_GRAD_AMP, amp, g_amp, adam->m_amp, adam->v_amp, nobj, adam->lr_amp, "amp"},
+      {PTY_GRAD_PHASE, phase, g_phase, adam->m_phase, adam->v_phase, nobj, adam->lr_phase, "phase"},
+      {PTY_GRAD_PROBE, probe, g_probe, adam->m_probe, adam->v_probe, nprobe, adam->lr_probe, "probe"},
+      {PTY_GRAD_POS, pos, g_pos, adam->m_pos, adam->v_pos, 2 * (size_t)geom->Ntot, adam->lr_pos, "pos"},
+      {PTY_GRAD_TILT, tilt, g_tilt, adam->m_tilt, adam->v_tilt, ntilt, adam->lr_tilt, "tilt"},
+      {PTY_GRAD_DZ, dz, g_dz, adam->m_dz, adam->v_dz, 1, adam->lr_dz, "dz"},
+  };
+  for (int k = 0; k < 6; ++k) {
+    if (!(gm & c[k].bit) || !(c[k].lr > 0.f)) continue;
+    REQUIRE(c[k].p && c[k].g && c[k].m && c[k].v, "Adam for %s needs parameter, gradient and both moments", c[k].name);
+    a.seg[a.nseg++] = AdamSeg{c[k].p, c[k].g, c[k].m, c[k].v, c[k].n, c[k].lr};
+  }
+  if (a.nseg == 0) return PTY_OK;
+  a.beta1 = adam->beta1;
+  a.beta2 = adam->beta2;
+  a.eps = adam->eps;
+  a.bc1 = (float)(1.0 - pow((double)adam->beta1, step));
+  a.bc2 = (float)(1.0 - pow((double)adam->beta2, step));
+  k_adam<<<152 * 8, 256, 0, (cudaStream_t)stream>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("k_adam launch failed: %s", cudaGetErrorString(e));
+    return PTY_ECUDA;
+  }
+  note_launch();
+  return PTY_OK;
+}
+
+int pty_step(const pty_geom* geom, int B, const int32_t* idx, float* amp, float* phase, float* probe, float* pos,
+             float* tilt, float* dz, const float* I_meas, double* loss, float* g_amp, float* g_phase, float* g_probe,
+             float* g_pos, float* g_tilt, float* g_dz, const pty_adam* adam, int step, void* ws, size_t ws_bytes,
+             void* stream) {
+  int rc = pty_loss_grad(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss, nullptr, g_amp, g_phase,
+                         g_probe, g_pos, g_tilt, g_dz, 0, ws, ws_bytes, stream);
+  if (rc) return rc;
+  return pty_adam_update(geom, amp, phase, probe, pos, tilt, dz, g_amp, g_phase, g_probe, g_pos, g_tilt, g_dz, adam,
+                         step, stream);
+}
+
+int pty_status(const void* ws, void* stream) {
+  if (!ws) return -1;
+  if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+    set_error("stream synchronisation failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return -1;
+  }
+  int v = 0;
+  if (cudaMemcpy(&v, ws, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+    set_error("status read failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return -1;
+  }
+  return v;
+}
+
+const char* pty_last_error(void) { return g_err; }
+
+int pty_supported_sizes(void) { return (1 << 6) | (1 << 7); }
+
+long long pty_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+int pty_profile_enable(int on) {
+  if (on && !g_prof_created) {
+    for (int c = 0; c < kProfCalls; ++c)
+      for (int k = 0; k <= PTY_PROF_STAGES; ++k)
+        if (cudaEventCreate(&g_prof_ev[c][k]) != cudaSuccess) {
+          set_error("cudaEventCreate failed");
+          return PTY_ECUDA;
+        }
+    g_prof_created = true;
+  }
+  g_prof_on = on != 0;
+  g_prof_calls = 0;
+  return PTY_OK;
+}
+
+int pty_profile_read(double* ms, int n) {
+  const int m = n < PTY_PROF_STAGES ? n : PTY_PROF_STAGES;
+  for (int k = 0; k < m; ++k) ms[k] = 0.0;
+  for (int c = 0; c < g_prof_calls; ++c) {
+    int prev = 0;  // time from the previous recorded mark to this stage's mark
+    for (int k = 1; k <= PTY_PROF_STAGES; ++k) {
+      if (!g_prof_have[c][k]) continue;
+      if (cudaEventSynchronize(g_prof_ev[c][k]) != cudaSuccess) return -1;
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, g_prof_ev[c][prev], g_prof_ev[c][k]) != cudaSuccess) return -1;
+      if (k - 1 < m) ms[k - 1] += t;
+      prev = k;
+    }
+  }
+  return g_prof_calls;
+}
+
+}  // extern "C"

@@ -1,0 +1,63 @@
+// pty_internal.h -- validated problem description and workspace layout shared by the launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "pty.h"
+
+namespace pty {
+
+// Workspace carve-up (all pieces 256-byte aligned).  k-space arrays use the FFT's digit-ordered
+// layout: element p1 * N + p0 holds frequency (kbin(p0), kbin(p1)) along (axis 0, axis 1).
+struct Workspace {
+  int* status;     // [1]   device status bits
+  float2* T;       // [Nz][H][W]      transmission amp * exp(i phase)
+  float2* Phat;    // [M][N*N]        probe spectra F[P_m] (k-space layout)
+  float2* ckpt;    // [B][M][Nz][N*N] wave entering each slice (natural layout)
+  float2* vhat;    // [B][M][Nz-1][N*N] propagated spectra / N^2 (k-space), for dz/tilt gradients
+  float2* Psi;     // [B][M][N*N]     far-field waves (k-space)
+  float* Imode;    // [B][M][N*N]     per-mode far-field intensity (k-space)
+  float* u;        // [B][N*N]        dL/dI before the batch normaliser (k-space)
+  double* lpart;   // [B][2]          per-pattern loss sums
+  double* scal;    // [4]             {dL/dI normaliser, loss, -, -}
+  float2* gT;      // [Nz][H][W]      dL/dT accumulator
+  float2* gPhat;   // [M][N*N]        probe-spectrum gradient accumulator (k-space)
+  double* spart;   // [B][M][5]       per-wave {pos0, pos1, tilt0, tilt1, dz} gradient partials
+};
+
+enum Mode { MODE_FORWARD = 0, MODE_GRAD = 1 };
+
+struct Problem {
+  int N, M, Nz, H, W, Ntot, B;
+  float dx, lam;
+  int loss;
+  float p, eps;
+  int grad_mask, global_tilt, accumulate, mode;
+  const int32_t* idx;
+  const float *amp, *phase, *pos, *tilt, *dz;
+  const float2* probe;
+  const float* I_meas;
+  double* loss_out;
+  float* I_model;
+  float *g_amp, *g_phase, *g_pos, *g_tilt, *g_dz;
+  float2* g_probe;
+  Workspace ws;
+  cudaStream_t stream;
+};
+
+// Byte offsets of the workspace pieces; returns the total size.  base may be NULL (size query).
+size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspace* out);
+
+// One pass of the hot path for FFT size N (instantiated in pty_n<N>.cu).  Returns a PTY_* code.
+template <int N>
+int run_pipeline(const Problem& pb);
+
+void set_error(const char* fmt, ...);
+
+// Diagnostics: launch counter and optional per-stage event timing (pty_profile_*).
+void note_launch();
+void prof_begin(cudaStream_t st);     // start of a pipeline call
+void prof_mark(int stage, cudaStream_t st);  // after the kernel of `stage`
+
+}  // namespace pty

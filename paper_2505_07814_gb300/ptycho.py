@@ -1,0 +1,179 @@
+"""PyTorch-facing wrapper of the C ABI: tensors in, device pointers out, nothing computed here.
+
+PyTorch supplies device memory and the current stream; every step of the model runs in the CUDA
+kernels of libpty.so.  If the library is missing, constructing `Ptycho` raises.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import torch
+
+from . import _lib
+
+LOSS = {"poisson": _lib.PTY_LOSS_POISSON, "gaussian": _lib.PTY_LOSS_GAUSSIAN}
+GRAD_BITS = {"amp": _lib.PTY_GRAD_AMP, "phase": _lib.PTY_GRAD_PHASE, "probe": _lib.PTY_GRAD_PROBE,
+             "pos": _lib.PTY_GRAD_POS, "tilt": _lib.PTY_GRAD_TILT, "dz": _lib.PTY_GRAD_DZ}
+
+
+@dataclasses.dataclass
+class Geometry:
+    N: int
+    M: int
+    Nz: int
+    H: int
+    W: int
+    Ntot: int
+    dx: float
+    lam: float
+    loss: str = "poisson"
+    p: float = 0.0  # <= 0: default exponent (1 Poisson, 0.5 Gaussian)
+    eps: float = 1e-6
+    grads: tuple = ("amp", "phase", "probe", "pos", "tilt", "dz")
+    global_tilt: bool = False
+
+    @property
+    def grad_mask(self) -> int:
+        m = 0
+        for g in self.grads:
+            m |= GRAD_BITS[g]
+        return m
+
+    def c(self) -> _lib.pty_geom:
+        return _lib.pty_geom(self.N, self.M, self.Nz, self.H, self.W, self.Ntot, self.dx, self.lam,
+                             LOSS[self.loss], self.p, self.eps, self.grad_mask, int(self.global_tilt))
+
+
+@dataclasses.dataclass
+class Params:
+    """Device tensors: amp/phase float32 [Nz,H,W], probe complex64 [M,N,N], pos float32 [Ntot,2],
+    tilt float32 [Ntot,2] (or [2]), dz float32 [1]."""
+    amp: torch.Tensor
+    phase: torch.Tensor
+    probe: torch.Tensor
+    pos: torch.Tensor
+    tilt: torch.Tensor
+    dz: torch.Tensor
+
+    @staticmethod
+    def from_numpy(w, device="cuda", global_tilt=False) -> "Params":
+        f32 = dict(dtype=torch.float32, device=device)
+        tilt = w.tilt[0] if global_tilt else w.tilt
+        return Params(amp=torch.tensor(w.amp, **f32), phase=torch.tensor(w.phase, **f32),
+                      probe=torch.tensor(w.probe, dtype=torch.complex64, device=device),
+                      pos=torch.tensor(w.pos, **f32), tilt=torch.tensor(tilt, **f32),
+                      dz=torch.tensor([w.dz], **f32))
+
+    def zeros_like(self) -> "Params":
+        return Params(*(torch.zeros_like(t) for t in dataclasses.astuple(self)))
+
+
+def _ptr(t, dtype=None, numel=None, name="tensor"):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("%s must be a CUDA tensor" % name)
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if numel is not None and t.numel() != numel:
+        raise ValueError("%s must have %d elements, has %d" % (name, numel, t.numel()))
+    return t.data_ptr()
+
+
+class Ptycho:
+    """One reconstruction problem on one device, with a workspace sized for batches up to max_batch."""
+
+    def __init__(self, geom: Geometry, max_batch: int, device="cuda"):
+        _lib.load()
+        self.geom = geom
+        self.cg = geom.c()
+        self.device = torch.device(device)
+        self.max_batch = max_batch
+        self.ws_bytes = _lib.pty_workspace_size(self.cg, max_batch)
+        self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
+        self.loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+
+    def _stream(self):
+        return torch.cuda.current_stream(self.device).cuda_stream
+
+    def _param_ptrs(self, p: Params):
+        g = self.geom
+        nobj = g.Nz * g.H * g.W
+        ntilt = 2 if g.global_tilt else 2 * g.Ntot
+        return (_ptr(p.amp, torch.float32, nobj, "amp"), _ptr(p.phase, torch.float32, nobj, "phase"),
+                _ptr(p.probe, torch.complex64, g.M * g.N * g.N, "probe"),
+                _ptr(p.pos, torch.float32, 2 * g.Ntot, "pos"), _ptr(p.tilt, torch.float32, ntilt, "tilt"),
+                _ptr(p.dz, torch.float32, 1, "dz"))
+
+    def _idx(self, idx):
+        idx = torch.as_tensor(idx, dtype=torch.int32, device=self.device).contiguous()
+        if idx.numel() > self.max_batch:
+            raise ValueError("batch of %d exceeds max_batch %d" % (idx.numel(), self.max_batch))
+        return idx
+
+    def forward(self, params: Params, idx, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Modelled patterns I[b] for scan positions idx (Eq. 1-4), float32 [B,N,N], DC-centred."""
+        idx = self._idx(idx)
+        B, N = idx.numel(), self.geom.N
+        if out is None:
+            out = torch.empty((B, N, N), dtype=torch.float32, device=self.device)
+        _lib.pty_forward(self.cg, B, _ptr(idx), *self._param_ptrs(params),
+                         _ptr(out, torch.float32, B * N * N, "I_model"), self.ws.data_ptr(), self.ws_bytes,
+                         self._stream())
+        return out
+
+    def loss_grad(self, params: Params, idx, I_meas: torch.Tensor, grads: Params | None = None,
+                  accumulate: bool = False, I_model: torch.Tensor | None = None):
+        """Loss (Eq. 5/6) of the batch and gradients of every parameter named in geom.grads.
+
+        Returns (loss as a float64 device tensor of one element, grads)."""
+        idx = self._idx(idx)
+        g = self.geom
+        B = idx.numel()
+        if grads is None:
+            grads = params.zeros_like()
+        gp = self._param_ptrs(grads)
+        _lib.pty_loss_grad(self.cg, B, _ptr(idx), *self._param_ptrs(params),
+                           _ptr(I_meas, torch.float32, g.Ntot * g.N * g.N, "I_meas"), self.loss.data_ptr(),
+                           _ptr(I_model, torch.float32, B * g.N * g.N, "I_model"), *gp, int(accumulate),
+                           self.ws.data_ptr(), self.ws_bytes, self._stream())
+        return self.loss, grads
+
+    def status(self) -> int:
+        """Device status bits of the last call (synchronises the current stream)."""
+        return _lib.pty_status(self.ws.data_ptr(), self._stream())
+
+
+class Adam:
+    """Adam state (PyTorch semantics) for pty_step / pty_adam_update, one learning rate per parameter.
+    A learning rate of 0 (or a parameter missing from geom.grads) freezes that parameter."""
+
+    def __init__(self, params: Params, lr: dict, betas=(0.9, 0.999), eps=1e-8):
+        self.m = params.zeros_like()
+        self.v = params.zeros_like()
+        self.lr = {k: float(lr.get(k, 0.0)) for k in GRAD_BITS}
+        self.betas, self.eps = betas, eps
+        self.t = 0
+
+    def c(self) -> _lib.pty_adam:
+        a = _lib.pty_adam()
+        for name in GRAD_BITS:
+            setattr(a, "m_" + name, getattr(self.m, name).data_ptr())
+            setattr(a, "v_" + name, getattr(self.v, name).data_ptr())
+            setattr(a, "lr_" + name, self.lr[name])
+        a.beta1, a.beta2 = self.betas
+        a.eps = self.eps
+        return a
+
+
+def step(pt: Ptycho, params: Params, grads: Params, adam: Adam, idx, I_meas: torch.Tensor):
+    """One Adam iteration on one batch through pty_step; returns the batch loss (device tensor)."""
+    idx = pt._idx(idx)
+    g = pt.geom
+    adam.t += 1
+    _lib.pty_step(pt.cg, idx.numel(), _ptr(idx), *pt._param_ptrs(params),
+                  _ptr(I_meas, torch.float32, g.Ntot * g.N * g.N, "I_meas"), pt.loss.data_ptr(),
+                  *pt._param_ptrs(grads), adam.c(), adam.t, pt.ws.data_ptr(), pt.ws_bytes, pt._stream())
+    return pt.loss

@@ -1,0 +1,93 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds for sm_103a, loads, exports
+every function include/pty.h declares, and rejects bad arguments before launching anything."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2505_07814_gb300 import _lib, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _lib.load()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "pty.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(pty_[a-z_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared_functions()
+    assert set(declared) == set(_lib.EXPORTS)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    saved = _lib._lib
+    _lib._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            _lib.load(str(tmp_path / "missing.so"))
+    finally:
+        _lib._lib = saved
+
+
+def _geom(**kw):
+    g = dict(N=64, M=2, Nz=3, H=100, W=110, Ntot=12, dx=0.1, lambda_=0.0251, loss=0, p=0.0, eps=1e-6,
+             grad_mask=63, global_tilt=0)
+    g.update(kw)
+    return _lib.pty_geom(**g)
+
+
+def test_workspace_size_and_validation(lib):
+    n = lib.pty_workspace_size(ctypes.byref(_geom()), 8)
+    # at least the checkpoints: B*M*Nz*N^2 complex64
+    assert n >= 8 * 2 * 3 * 64 * 64 * 8
+    assert lib.pty_workspace_size(ctypes.byref(_geom(grad_mask=_lib.PTY_GRAD_PROBE)), 8) < n
+    for bad in (dict(N=32), dict(N=96), dict(M=0), dict(Nz=0), dict(H=63), dict(loss=7), dict(dx=0.0),
+                dict(grad_mask=64)):
+        assert lib.pty_workspace_size(ctypes.byref(_geom(**bad)), 8) == 0, bad
+        assert lib.pty_last_error()
+    assert lib.pty_supported_sizes() == (1 << 6) | (1 << 7)
+
+
+def test_bad_arguments_rejected_before_launch(lib):
+    g = _geom()
+    fake = ctypes.c_void_p(0x10000)  # never dereferenced: validation fails first
+    null = None
+    # unsupported N
+    rc = lib.pty_forward(ctypes.byref(_geom(N=32)), 1, fake, fake, fake, fake, fake, fake, fake, fake, fake, 1 << 30,
+                         null)
+    assert rc == _lib.PTY_EINVAL and "N = 32" in lib.pty_last_error().decode()
+    # null parameter
+    rc = lib.pty_forward(ctypes.byref(g), 1, fake, null, fake, fake, fake, fake, fake, fake, fake, 1 << 30, null)
+    assert rc == _lib.PTY_EINVAL
+    # workspace too small
+    rc = lib.pty_forward(ctypes.byref(g), 4, fake, fake, fake, fake, fake, fake, fake, fake, fake, 1024, null)
+    assert rc == _lib.PTY_EWORKSPACE and "workspace" in lib.pty_last_error().decode()
+    # negative batch
+    rc = lib.pty_loss_grad(ctypes.byref(g), -1, fake, fake, fake, fake, fake, fake, fake, fake, fake, null, fake,
+                           fake, fake, fake, fake, fake, 0, fake, 1 << 30, null)
+    assert rc == _lib.PTY_EINVAL
+    # requested gradient without an output array
+    ws = ctypes.c_void_p(0x100000)
+    rc = lib.pty_loss_grad(ctypes.byref(g), 2, fake, fake, fake, fake, fake, fake, fake, fake, fake, null, null,
+                           fake, fake, fake, fake, fake, 0, ws, 1 << 40, null)
+    assert rc == _lib.PTY_EINVAL and "g_amp" in lib.pty_last_error().decode()
+    # misaligned probe
+    rc = lib.pty_forward(ctypes.byref(g), 1, fake, fake, fake, ctypes.c_void_p(0x10004), fake, fake, fake, fake,
+                         ws, 1 << 40, null)
+    assert rc == _lib.PTY_EINVAL
+    # Adam with a step count of 0
+    a = _lib.pty_adam()
+    rc = lib.pty_adam_update(ctypes.byref(g), fake, fake, fake, fake, fake, fake, fake, fake, fake, fake, fake, fake,
+                             ctypes.byref(a), 0, null)
+    assert rc == _lib.PTY_EINVAL
