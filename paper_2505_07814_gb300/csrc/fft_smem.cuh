@@ -21,6 +21,8 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 namespace pty {
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -108,6 +110,17 @@ __host__ __device__ constexpr int kbin(int p) {
   return p / Radix<N>::R2 + Radix<N>::R1 * (p % Radix<N>::R2);
 }
 
+// Element hooks fused into the FFT passes.  A hook sees K elements of one task in registers: the
+// elements sit at rows row0 + k * rstride (k < K) of column c of the array being transformed (the
+// first index is the row).  Load hooks run right after the elements are read, store hooks right
+// before they are written.  A hook with kReplaces = true produces the values itself, so the
+// shared-memory read is skipped.
+struct NoHook {
+  static constexpr bool kReplaces = false;
+  template <int K>
+  __device__ __forceinline__ void operator()(int, int, int, float2*) {}
+};
+
 template <int N, int T>
 struct Fft2 {
   static constexpr int R1 = Radix<N>::R1, R2 = Radix<N>::R2, RS = N + 1;
@@ -117,17 +130,28 @@ struct Fft2 {
   static constexpr int NA = N * R2 / T;  // step-A tasks per thread
   static constexpr int NB = N * R1 / T;  // step-B tasks per thread
 
+  template <class H>
+  static constexpr bool kPlain = std::is_same_v<std::decay_t<H>, NoHook>;
+
   // Forward 1D DFT along the first index.  TRANSPOSE: write result to s[c][p] instead of s[p][c].
-  template <bool TRANSPOSE>
-  __device__ static void fwd_pass(float2* s, const float2* tw) {
+  // WRITE = false: the result only goes through the store hook (nothing is written back).  Steps
+  // with a hook run one task at a time (the hook's loads are batched inside the task); steps
+  // without one unroll over the thread's tasks.
+  template <bool TRANSPOSE, bool WRITE = true, class LH = NoHook, class SH = NoHook>
+  __device__ static void fwd_pass(float2* s, const float2* tw, LH&& lh = LH(), SH&& sh = SH()) {
+    static_assert(!(TRANSPOSE && !kPlain<SH>), "store hooks only on non-transposing passes");
     const int tid = threadIdx.x;
-#pragma unroll
+    constexpr int UA = kPlain<LH> ? NA : 1;
+#pragma unroll(UA)
     for (int i = 0; i < NA; ++i) {
       const int t = tid + i * T;
       const int c = t % N, n2 = t / N;
       float2 v[R1];
+      if (!std::remove_reference_t<LH>::kReplaces) {
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) v[n1] = s[(R2 * n1 + n2) * RS + c];
+        for (int n1 = 0; n1 < R1; ++n1) v[n1] = s[(R2 * n1 + n2) * RS + c];
+      }
+      lh.template operator()<R1>(n2, R2, c, v);
       dft<R1, false>(v);
 #pragma unroll
       for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
@@ -135,20 +159,16 @@ struct Fft2 {
       for (int k1 = 0; k1 < R1; ++k1) s[(R2 * k1 + n2) * RS + c] = v[k1];
     }
     __syncthreads();
-    float2 v[NB][R2];
+    if constexpr (TRANSPOSE) {
+      float2 v[NB][R2];
 #pragma unroll
-    for (int i = 0; i < NB; ++i) {
-      const int t = tid + i * T;
-      const int c = t % N, k1 = t / N;
+      for (int i = 0; i < NB; ++i) {
+        const int t = tid + i * T;
+        const int c = t % N, k1 = t / N;
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) v[i][n2] = s[(R2 * k1 + n2) * RS + c];
-      dft<R2, false>(v[i]);
-      if (!TRANSPOSE) {
-#pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) s[(R2 * k1 + k2) * RS + c] = v[i][k2];
+        for (int n2 = 0; n2 < R2; ++n2) v[i][n2] = s[(R2 * k1 + n2) * RS + c];
+        dft<R2, false>(v[i]);
       }
-    }
-    if (TRANSPOSE) {
       __syncthreads();
 #pragma unroll
       for (int i = 0; i < NB; ++i) {
@@ -157,21 +177,41 @@ struct Fft2 {
 #pragma unroll
         for (int k2 = 0; k2 < R2; ++k2) s[c * RS + R2 * k1 + k2] = v[i][k2];
       }
+    } else {
+      constexpr int UB = kPlain<SH> ? NB : 1;
+#pragma unroll(UB)
+      for (int i = 0; i < NB; ++i) {
+        const int t = tid + i * T;
+        const int c = t % N, k1 = t / N;
+        float2 v[R2];
+#pragma unroll
+        for (int n2 = 0; n2 < R2; ++n2) v[n2] = s[(R2 * k1 + n2) * RS + c];
+        dft<R2, false>(v);
+        sh.template operator()<R2>(R2 * k1, 1, c, v);
+        if (WRITE) {
+#pragma unroll
+          for (int k2 = 0; k2 < R2; ++k2) s[(R2 * k1 + k2) * RS + c] = v[k2];
+        }
+      }
     }
     __syncthreads();
   }
 
   // Inverse 1D DFT along the first index (input in k-space digit order, output natural order).
-  template <bool TRANSPOSE>
-  __device__ static void inv_pass(float2* s, const float2* tw) {
+  template <bool TRANSPOSE, class LH = NoHook>
+  __device__ static void inv_pass(float2* s, const float2* tw, LH&& lh = LH()) {
     const int tid = threadIdx.x;
-#pragma unroll
+    constexpr int UB = kPlain<LH> ? NB : 1;
+#pragma unroll(UB)
     for (int i = 0; i < NB; ++i) {
       const int t = tid + i * T;
       const int c = t % N, k1 = t / N;
       float2 v[R2];
+      if (!std::remove_reference_t<LH>::kReplaces) {
 #pragma unroll
-      for (int k2 = 0; k2 < R2; ++k2) v[k2] = s[(R2 * k1 + k2) * RS + c];
+        for (int k2 = 0; k2 < R2; ++k2) v[k2] = s[(R2 * k1 + k2) * RS + c];
+      }
+      lh.template operator()<R2>(R2 * k1, 1, c, v);
       dft<R2, true>(v);
 #pragma unroll
       for (int n2 = 1; n2 < R2; ++n2) v[n2] = cmulc(tw[n2 * k1], v[n2]);
@@ -179,20 +219,16 @@ struct Fft2 {
       for (int n2 = 0; n2 < R2; ++n2) s[(R2 * k1 + n2) * RS + c] = v[n2];
     }
     __syncthreads();
-    float2 v[NA][R1];
+    if constexpr (TRANSPOSE) {
+      float2 v[NA][R1];
 #pragma unroll
-    for (int i = 0; i < NA; ++i) {
-      const int t = tid + i * T;
-      const int c = t % N, n2 = t / N;
+      for (int i = 0; i < NA; ++i) {
+        const int t = tid + i * T;
+        const int c = t % N, n2 = t / N;
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) v[i][k1] = s[(R2 * k1 + n2) * RS + c];
-      dft<R1, true>(v[i]);
-      if (!TRANSPOSE) {
-#pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) s[(R2 * n1 + n2) * RS + c] = v[i][n1];
+        for (int k1 = 0; k1 < R1; ++k1) v[i][k1] = s[(R2 * k1 + n2) * RS + c];
+        dft<R1, true>(v[i]);
       }
-    }
-    if (TRANSPOSE) {
       __syncthreads();
 #pragma unroll
       for (int i = 0; i < NA; ++i) {
@@ -201,19 +237,52 @@ struct Fft2 {
 #pragma unroll
         for (int n1 = 0; n1 < R1; ++n1) s[c * RS + R2 * n1 + n2] = v[i][n1];
       }
+    } else {
+#pragma unroll
+      for (int i = 0; i < NA; ++i) {
+        const int t = tid + i * T;
+        const int c = t % N, n2 = t / N;
+        float2 v[R1];
+#pragma unroll
+        for (int k1 = 0; k1 < R1; ++k1) v[k1] = s[(R2 * k1 + n2) * RS + c];
+        dft<R1, true>(v);
+#pragma unroll
+        for (int n1 = 0; n1 < R1; ++n1) s[(R2 * n1 + n2) * RS + c] = v[n1];
+      }
     }
     __syncthreads();
   }
 
-  // natural s[r][c] -> k-space s[p1][p0]  (unnormalised forward DFT)
-  __device__ static void forward(float2* s, const float2* tw) {
-    fwd_pass<true>(s, tw);
-    fwd_pass<false>(s, tw);
+  // natural s[r][c] -> k-space s[p1][p0] (unnormalised forward DFT).  `load` sees natural (r, c);
+  // `store` sees k-space (p1, p0).  WRITE = false leaves the result only to `store`.
+  template <bool WRITE = true, class LH = NoHook, class SH = NoHook>
+  __device__ static void forward(float2* s, const float2* tw, LH&& load = LH(), SH&& store = SH()) {
+    fwd_pass<true>(s, tw, load);
+    fwd_pass<false, WRITE>(s, tw, NoHook(), store);
   }
-  // k-space s[p1][p0] -> natural s[r][c]  (unnormalised inverse DFT)
-  __device__ static void inverse(float2* s, const float2* tw) {
-    inv_pass<true>(s, tw);
+  // k-space s[p1][p0] -> natural s[r][c] (unnormalised inverse DFT); `load` sees k-space (p1, p0).
+  template <class LH = NoHook>
+  __device__ static void inverse(float2* s, const float2* tw, LH&& load = LH()) {
+    inv_pass<true>(s, tw, load);
     inv_pass<false>(s, tw);
+  }
+
+  // Apply a hook to every element of the natural-layout array (same task shape as step A).
+  template <class H>
+  __device__ static void elementwise(float2* s, H&& h) {
+    const int tid = threadIdx.x;
+#pragma unroll 1
+    for (int i = 0; i < NA; ++i) {
+      const int t = tid + i * T;
+      const int c = t % N, n2 = t / N;
+      float2 v[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) v[n1] = s[(R2 * n1 + n2) * RS + c];
+      h.template operator()<R1>(n2, R2, c, v);
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) s[(R2 * n1 + n2) * RS + c] = v[n1];
+    }
+    __syncthreads();
   }
 };
 

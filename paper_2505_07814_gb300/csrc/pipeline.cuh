@@ -26,11 +26,11 @@ template <int N>
 struct Launch;
 template <>
 struct Launch<64> {
-  static constexpr int T = 256;
+  static constexpr int T = 256, MIN_BLOCKS = 2;
 };
 template <>
 struct Launch<128> {
-  static constexpr int T = 512;
+  static constexpr int T = 512, MIN_BLOCKS = 1;
 };
 
 // exp(i pi x); x is reduced modulo 2 in double precision before the float sincospi.
@@ -149,8 +149,98 @@ __host__ __device__ constexpr size_t fwd_smem_bytes() {
   return sizeof(float2) * ((size_t)N * (N + 1) + 5 * N);
 }
 
+// L2 prefetch of a byte range (rounded out to 16-byte boundaries).
+__device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
+  const uintptr_t a = (uintptr_t)p & ~(uintptr_t)15;
+  const uintptr_t e = ((uintptr_t)p + bytes + 15) & ~(uintptr_t)15;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
+}
+// Rows [0, N) of an N-wide patch with row stride W (elements), one row per thread tid < N.
+template <int N>
+__device__ __forceinline__ void prefetch_patch(const float2* base, int W) {
+  if (threadIdx.x < N) prefetch_l2(base + (size_t)threadIdx.x * W, sizeof(float2) * N);
+}
+// A contiguous N*N block, split over the first 8 threads.
+template <int N>
+__device__ __forceinline__ void prefetch_block(const float2* base) {
+  constexpr size_t chunk = sizeof(float2) * N * N / 8;
+  if (threadIdx.x < 8) prefetch_l2(reinterpret_cast<const char*>(base) + threadIdx.x * chunk, chunk);
+}
+
+// ---- forward hooks (see NoHook for the calling convention) ----
+// shifted-probe spectrum P^_m R_j (k-space), replaces the shared-memory contents
+template <int N>
+struct ShiftLoad {
+  static constexpr bool kReplaces = true;
+  const float2* Ph;
+  const float2 *ra0, *ra1;
+  template <int K>
+  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+    float2 p[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) p[k] = Ph[(row0 + k * rs) * N + c];
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = cmul(cmul(p[k], ra1[row0 + k * rs]), ra0[c]);
+  }
+};
+// transmission of slice s: checkpoint the entering wave, then multiply by T (natural layout)
+template <int N>
+struct TransLoad {
+  static constexpr bool kReplaces = false;
+  const float2* Ts;  // patch corner in T
+  int W;
+  float2* ck;  // checkpoint block or nullptr
+  template <int K>
+  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+    float2 t[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) t[k] = __ldg(Ts + (size_t)(row0 + k * rs) * W + c);
+    if (ck) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) __stcs(ck + (row0 + k * rs) * N + c, v[k]);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = cmul(v[k], t[k]);
+  }
+};
+// propagator of Eq. 4 (with 1/N^2 of the following inverse DFT), k-space; optionally stored
+template <int N>
+struct PropStore {
+  static constexpr bool kReplaces = false;
+  const float2 *m0, *m1;
+  float2* vh;
+  template <int K>
+  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+    const float2 mc = m0[c];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int r = row0 + k * rs;
+      v[k] = cmul(cmul(v[k], m1[r]), mc);
+      if (vh) __stcs(vh + r * N + c, v[k]);
+    }
+  }
+};
+// far field: orthonormal scale, store Psi (for the adjoint) and the mode's intensity
+template <int N>
+struct FarStore {
+  static constexpr bool kReplaces = false;
+  float2* Psi;
+  float* Im;
+  template <int K>
+  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+    const float inv_n = 1.0f / (float)N;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int e = (row0 + k * rs) * N + c;
+      const float2 x = cscale(v[k], inv_n);
+      if (Psi) __stcs(Psi + e, x);
+      Im[e] = fmaf(x.x, x.x, x.y * x.y);
+    }
+  }
+};
+
 template <int N, int T>
-__global__ void __launch_bounds__(T, 1) k_forward(FwdArgs a) {
+__global__ void __launch_bounds__(T, Launch<N>::MIN_BLOCKS) k_forward(FwdArgs a) {
   using F = Fft2<N, T>;
   constexpr int RS = F::RS;
   constexpr int NN = N * N;
@@ -170,6 +260,9 @@ __global__ void __launch_bounds__(T, 1) k_forward(FwdArgs a) {
   patch_corner<N>(a.pos, j, a.H, a.W, &i0, &i1, &d0, &d1, a.status);
   tilt_of(a.tilt, a.global_tilt, j, &th0, &th1);
   const float dz = a.dz[0];
+  const size_t plane = (size_t)a.H * a.W;
+  const float2* Tpatch = a.T + (size_t)i0 * a.W + i1;
+  prefetch_patch<N>(Tpatch, a.W);
 
   build_twiddles<N>(tw);
   if (tid < N) {
@@ -186,48 +279,19 @@ __global__ void __launch_bounds__(T, 1) k_forward(FwdArgs a) {
   __syncthreads();
 
   // shifted probe P_j = F^-1[P^_m ramp]
-  const float2* Ph = a.Phat + (size_t)m * NN;
-  for (int e = tid; e < NN; e += T) {
-    const int r = e / N, c = e % N;
-    s[r * RS + c] = cmul(cmul(Ph[e], ra1[r]), ra0[c]);
-  }
-  __syncthreads();
-  F::inverse(s, tw);
+  F::inverse(s, tw, ShiftLoad<N>{a.Phat + (size_t)m * NN, ra0, ra1});
 
   for (int sl = 0; sl < a.Nz; ++sl) {
-    const float2* Ts = a.T + (size_t)sl * a.H * a.W + (size_t)i0 * a.W + i1;
-    float2* ck = a.ckpt ? a.ckpt + ((size_t)bm * a.Nz + sl) * NN : nullptr;
-#pragma unroll 4
-    for (int e = tid; e < NN; e += T) {
-      const int r = e / N, c = e % N;
-      float2 v = s[r * RS + c];
-      if (ck) __stcs(ck + e, v);
-      v = cmul(v, __ldg(Ts + (size_t)r * a.W + c));
-      s[r * RS + c] = v;
-    }
-    __syncthreads();
+    if (sl + 1 < a.Nz) prefetch_patch<N>(Tpatch + (sl + 1) * plane, a.W);
+    TransLoad<N> trans{Tpatch + sl * plane, a.W, a.ckpt ? a.ckpt + ((size_t)bm * a.Nz + sl) * NN : nullptr};
     if (sl + 1 < a.Nz) {
-      F::forward(s, tw);
       float2* vh = a.vhat ? a.vhat + ((size_t)bm * (a.Nz - 1) + sl) * NN : nullptr;
-      for (int e = tid; e < NN; e += T) {
-        const int r = e / N, c = e % N;
-        const float2 v = cmul(cmul(s[r * RS + c], pm1[r]), pm0[c]);
-        s[r * RS + c] = v;
-        if (vh) __stcs(vh + e, v);
-      }
-      __syncthreads();
+      F::forward(s, tw, trans, PropStore<N>{pm0, pm1, vh});
       F::inverse(s, tw);
+    } else {
+      F::template forward<false>(s, tw, trans,
+                                 FarStore<N>{a.Psi ? a.Psi + (size_t)bm * NN : nullptr, a.Imode + (size_t)bm * NN});
     }
-  }
-  // far field, orthonormal DFT
-  F::forward(s, tw);
-  const float inv_n = 1.0f / (float)N;
-  float2* Psi = a.Psi ? a.Psi + (size_t)bm * NN : nullptr;
-  float* Im = a.Imode + (size_t)bm * NN;
-  for (int e = tid; e < NN; e += T) {
-    const float2 v = cscale(s[(e / N) * RS + e % N], inv_n);
-    if (Psi) __stcs(Psi + e, v);
-    Im[e] = fmaf(v.x, v.x, v.y * v.y);
   }
 }
 
@@ -394,11 +458,121 @@ struct AdjArgs {
 
 template <int N, int T>
 __host__ __device__ constexpr size_t adj_smem_bytes() {
-  return sizeof(float2) * ((size_t)N * (N + 1) + 5 * N) + sizeof(float) * 4 * N + sizeof(double) * 5 * (T / 32);
+  return sizeof(float2) * ((size_t)N * (N + 1) + 5 * N) + sizeof(float) * 6 * N + sizeof(double) * 5 * (T / 32);
 }
 
+// ---- adjoint hooks ----
+// g_psi at the far field = F_ortho^-1[2 dL/dI Psi]: forms 2 dL/dI Psi / N (k-space), replaces
+template <int N>
+struct FarGradLoad {
+  static constexpr bool kReplaces = true;
+  const float* u;
+  const float2* Psi;
+  float gs;
+  template <int K>
+  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+    float2 p[K];
+    float w[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int e = (row0 + k * rs) * N + c;
+      p[k] = __ldcs(Psi + e);
+      w[k] = u[e];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = cscale(p[k], gs * w[k]);
+  }
+};
+// transmission of slice s backwards: dL/dT += conj(psi_in) g (scatter-add), g <- conj(T) g
+template <int N>
+struct AdjTransLoad {
+  static constexpr bool kReplaces = false;
+  const float2* Ts;  // patch corner in T
+  float2* gTs;       // patch corner in the dL/dT accumulator
+  const float2* ck;  // checkpoint of the wave entering slice s, or nullptr (no object gradient)
+  int W;
+  template <int K>
+  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+    float2 t[K], ps[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int r = row0 + k * rs;
+      t[k] = __ldg(Ts + (size_t)r * W + c);
+      if (ck) ps[k] = __ldcs(ck + r * N + c);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      if (ck) atomicAdd(gTs + (size_t)(row0 + k * rs) * W + c, cmulc(ps[k], v[k]));
+      v[k] = cmulc(t[k], v[k]);
+    }
+  }
+};
+// propagation backwards in k-space: dz / tilt terms against the stored forward spectrum, then
+// g^ <- conj(M) g^ / N^2.  Accumulates -sum w (e0 + e1), -sum w c0, -sum w c1 with w = Im(conj(g^) v^).
+template <int N>
+struct AdjPropStore {
+  static constexpr bool kReplaces = false;
+  const float2 *cm0, *cm1;
+  const float2* vh;  // stored v^/N^2 of this propagation, or nullptr
+  const float *e0, *e1, *c0, *c1;
+  float &dz, &t0, &t1;
+  template <int K>
+  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+    const float2 mc = cm0[c];
+    if (vh) {
+      float2 x[K];
+#pragma unroll
+      for (int k = 0; k < K; ++k) x[k] = __ldcs(vh + (row0 + k * rs) * N + c);
+      const float ec = e0[c], cc = c0[c];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int r = row0 + k * rs;
+        const float w = v[k].x * x[k].y - v[k].y * x[k].x;
+        dz = fmaf(w, ec + e1[r], dz);
+        t0 = fmaf(w, cc, t0);
+        t1 = fmaf(w, c1[r], t1);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = cmul(cmul(v[k], cm1[row0 + k * rs]), mc);
+  }
+};
+// dL/dP_j in k-space: probe-spectrum gradient conj(R) g^ (scatter-add) and the position terms
+// sum f_a Im(conj(g^) R P^) (f_a carries 2 pi / N^2).
+template <int N>
+struct ProbeStore {
+  static constexpr bool kReplaces = false;
+  float2* gP;  // or nullptr
+  const float2* Ph;
+  const float2 *cr0, *cr1;
+  const float *f0, *f1;
+  bool pos;
+  float &p0, &p1;
+  template <int K>
+  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+    const float2 crc = cr0[c];
+    float2 ph[K];
+    if (pos) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) ph[k] = Ph[(row0 + k * rs) * N + c];
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int r = row0 + k * rs;
+      const float2 cr = cmul(cr1[r], crc);  // conj(R)
+      if (gP) atomicAdd(gP + r * N + c, cmul(cr, v[k]));
+      if (pos) {
+        const float2 PR = cmulc(cr, ph[k]);  // R P^
+        const float w = v[k].x * PR.y - v[k].y * PR.x;
+        p0 = fmaf(w, f0[c], p0);
+        p1 = fmaf(w, f1[r], p1);
+      }
+    }
+  }
+};
+
 template <int N, int T>
-__global__ void __launch_bounds__(T, 1) k_adjoint(AdjArgs a) {
+__global__ void __launch_bounds__(T, Launch<N>::MIN_BLOCKS) k_adjoint(AdjArgs a) {
   using F = Fft2<N, T>;
   constexpr int RS = F::RS;
   constexpr int NN = N * N;
@@ -407,13 +581,15 @@ __global__ void __launch_bounds__(T, 1) k_adjoint(AdjArgs a) {
   float2* tw = s + N * RS;
   float2* cm0 = tw + N;   // conj propagator, axis 0, carries 1/N^2
   float2* cm1 = cm0 + N;  // conj propagator, axis 1
-  float2* cr0 = cm1 + N;  // conj shift ramp, axis 0 (no scale)
+  float2* cr0 = cm1 + N;  // conj shift ramp, axis 0
   float2* cr1 = cr0 + N;  // conj shift ramp, axis 1
-  float* W0 = reinterpret_cast<float*>(cr1 + N);  // per k-space column: sum over rows of w (dz/tilt)
-  float* W1 = W0 + N;                             // per k-space row: sum over columns of w
-  float* X0 = W1 + N;                             // same for the position term
-  float* X1 = X0 + N;
-  double* red = reinterpret_cast<double*>(X1 + N);
+  float* e0 = reinterpret_cast<float*>(cr1 + N);  // -(dM/d dz)/(i M) per axis
+  float* e1 = e0 + N;
+  float* c0 = e1 + N;  // -(dM/d theta_a)/(i M)
+  float* c1 = c0 + N;
+  float* f0 = c1 + N;  // 2 pi f_a / N^2 (position term)
+  float* f1 = f0 + N;
+  double* red = reinterpret_cast<double*>(f1 + N);
   const int tid = threadIdx.x, lane = tid & 31;
   const int bm = blockIdx.x;
   const int b = bm / a.M, m = bm % a.M;
@@ -427,6 +603,12 @@ __global__ void __launch_bounds__(T, 1) k_adjoint(AdjArgs a) {
   const bool want_probe = (a.grad_mask & PTY_GRAD_PROBE) != 0;
   const bool want_pos = (a.grad_mask & PTY_GRAD_POS) != 0;
   const bool want_prop = (a.grad_mask & (PTY_GRAD_DZ | PTY_GRAD_TILT)) != 0 && a.vhat != nullptr;
+  const size_t plane = (size_t)a.H * a.W;
+  const size_t patch = (size_t)i0 * a.W + i1;
+  const float2* ck_base = a.ckpt + (size_t)bm * a.Nz * NN;
+  const float2* vh_base = want_prop ? a.vhat + (size_t)bm * (a.Nz - 1) * NN : nullptr;
+  if (want_obj) prefetch_block<N>(ck_base + (size_t)(a.Nz - 1) * NN);
+  if (want_prop && a.Nz > 1) prefetch_block<N>(vh_base + (size_t)(a.Nz - 2) * NN);
 
   build_twiddles<N>(tw);
   if (tid < N) {
@@ -434,125 +616,60 @@ __global__ void __launch_bounds__(T, 1) k_adjoint(AdjArgs a) {
     const float inv_nn = 1.0f / (float)NN;
     const double k = q / (N * (double)a.dx);
     const double base = -(double)a.lam * dz * k * k;
-    cm0[tid] = cscale(cconj(expipi(base + 2.0 * dz * k * tan((double)th0))), inv_nn);
-    cm1[tid] = cconj(expipi(base + 2.0 * dz * k * tan((double)th1)));
+    const double tn0 = tan((double)th0), tn1 = tan((double)th1);
+    cm0[tid] = cscale(cconj(expipi(base + 2.0 * dz * k * tn0)), inv_nn);
+    cm1[tid] = cconj(expipi(base + 2.0 * dz * k * tn1));
     cr0[tid] = expipi(2.0 * q * (double)d0 / N);
     cr1[tid] = expipi(2.0 * q * (double)d1 / N);
-    W0[tid] = 0.f;
-    W1[tid] = 0.f;
-    X0[tid] = 0.f;
-    X1[tid] = 0.f;
-  }
-  __syncthreads();
-
-  // g_Psi = 2 dL/dI Psi ; g_psi = F_ortho^-1[g_Psi] = (1/N) unnormalised inverse
-  const float gs = (float)(2.0 * a.scal[0] / N);
-  {
-    const float* u = a.u + (size_t)b * NN;
-    const float2* Psi = a.Psi + (size_t)bm * NN;
-    for (int e = tid; e < NN; e += T) s[(e / N) * RS + e % N] = cscale(__ldcs(Psi + e), gs * u[e]);
-  }
-  __syncthreads();
-  F::inverse(s, tw);
-
-  float wcol = 0.f;  // this thread's column partial of w (its column is tid % N in every pass)
-  for (int sl = a.Nz - 1; sl >= 0; --sl) {
-    const float2* Ts = a.T + (size_t)sl * a.H * a.W + (size_t)i0 * a.W + i1;
-    float2* gTs = a.gT + (size_t)sl * a.H * a.W + (size_t)i0 * a.W + i1;
-    const float2* ck = a.ckpt + ((size_t)bm * a.Nz + sl) * NN;
-#pragma unroll 4
-    for (int e = tid; e < NN; e += T) {
-      const int r = e / N, c = e % N;
-      const float2 g = s[r * RS + c];
-      if (want_obj) {
-        const float2 psi = __ldcs(ck + e);
-        atomicAdd(gTs + (size_t)r * a.W + c, cmulc(psi, g));
-      }
-      s[r * RS + c] = cmulc(__ldg(Ts + (size_t)r * a.W + c), g);
-    }
-    __syncthreads();
-    if (sl > 0) {
-      F::forward(s, tw);
-      const float2* vh = want_prop ? a.vhat + ((size_t)bm * (a.Nz - 1) + sl - 1) * NN : nullptr;
-      for (int e = tid; e < NN; e += T) {
-        const int r = e / N, c = e % N;
-        const float2 gh = s[r * RS + c];
-        if (vh) {
-          const float2 v = __ldcs(vh + e);
-          float w = gh.x * v.y - gh.y * v.x;  // Im(conj(g^) v)
-          wcol += w;
-          for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-          if (lane == 0) atomicAdd(W1 + r, w);
-        }
-        s[r * RS + c] = cmul(cmul(gh, cm1[r]), cm0[c]);
-      }
-      __syncthreads();
-      F::inverse(s, tw);
-    }
-  }
-  if (want_prop) atomicAdd(W0 + (tid % N), wcol);
-
-  // s = dL/dP_j (natural).  P_j = F^-1[P^ R]  ->  spectrum gradient and position gradient.
-  float xcol = 0.f;
-  if (want_probe || want_pos) {
-    F::forward(s, tw);
-    const float2* Ph = a.Phat + (size_t)m * NN;
-    float2* gP = a.gPhat + (size_t)m * NN;
-    for (int e = tid; e < NN; e += T) {
-      const int r = e / N, c = e % N;
-      const float2 gh = s[r * RS + c];
-      const float2 cr = cmul(cr1[r], cr0[c]);  // conj(R)
-      if (want_probe) atomicAdd(gP + e, cmul(cr, gh));
-      if (want_pos) {
-        const float2 PR = cmulc(cr, Ph[e]);  // R P^
-        float w = gh.x * PR.y - gh.y * PR.x;  // Im(conj(g^) R P^)
-        xcol += w;
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        if (lane == 0) atomicAdd(X1 + r, w);
-      }
-    }
-    if (want_pos) atomicAdd(X0 + (tid % N), xcol);
-  }
-  __syncthreads();
-
-  // FP64 dot products of the per-axis sums with the analytic factors.
-  double gp0 = 0.0, gp1 = 0.0, gt0 = 0.0, gt1 = 0.0, gdz = 0.0;
-  if (tid < N) {
-    const int q = signed_bin<N>(kbin<N>(tid));
-    const double k = q / (N * (double)a.dx);
     const double PI = 3.14159265358979323846;
-    const double t0 = tan((double)th0), t1 = tan((double)th1);
-    const double c0 = cos((double)th0), c1 = cos((double)th1);
-    const double e0 = -PI * a.lam * k * k + 2.0 * PI * k * t0;
-    const double e1 = -PI * a.lam * k * k + 2.0 * PI * k * t1;
-    const double w0 = W0[tid], w1 = W1[tid];
-    gdz = -(e0 * w0 + e1 * w1);
-    gt0 = -(2.0 * PI * dz * k / (c0 * c0)) * w0;
-    gt1 = -(2.0 * PI * dz * k / (c1 * c1)) * w1;
-    const double f = (double)q / N;
-    const double sc = 2.0 * PI / ((double)NN);
-    gp0 = sc * f * X0[tid];
-    gp1 = sc * f * X1[tid];
+    const double cs0 = cos((double)th0), cs1 = cos((double)th1);
+    e0[tid] = (float)(PI * a.lam * k * k - 2.0 * PI * k * tn0);
+    e1[tid] = (float)(PI * a.lam * k * k - 2.0 * PI * k * tn1);
+    c0[tid] = (float)(-2.0 * PI * dz * k / (cs0 * cs0));
+    c1[tid] = (float)(-2.0 * PI * dz * k / (cs1 * cs1));
+    f0[tid] = (float)(2.0 * PI * q / ((double)N * NN));
+    f1[tid] = f0[tid];
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    gp0 += __shfl_down_sync(0xffffffffu, gp0, o);
-    gp1 += __shfl_down_sync(0xffffffffu, gp1, o);
-    gt0 += __shfl_down_sync(0xffffffffu, gt0, o);
-    gt1 += __shfl_down_sync(0xffffffffu, gt1, o);
-    gdz += __shfl_down_sync(0xffffffffu, gdz, o);
+  __syncthreads();
+
+  // g_psi = F_ortho^-1[2 dL/dI Psi] = (1/N) unnormalised inverse of 2 dL/dI Psi
+  F::inverse(s, tw, FarGradLoad<N>{a.u + (size_t)b * NN, a.Psi + (size_t)bm * NN, (float)(2.0 * a.scal[0] / N)});
+
+  float gdz = 0.f, gt0 = 0.f, gt1 = 0.f, gp0 = 0.f, gp1 = 0.f;
+  for (int sl = a.Nz - 1; sl >= 0; --sl) {
+    if (sl >= 1 && want_obj) prefetch_block<N>(ck_base + (size_t)(sl - 1) * NN);
+    if (sl >= 2 && want_prop) prefetch_block<N>(vh_base + (size_t)(sl - 2) * NN);
+    AdjTransLoad<N> trans{a.T + sl * plane + patch, a.gT + sl * plane + patch,
+                          want_obj ? ck_base + (size_t)sl * NN : nullptr, a.W};
+    if (sl > 0) {
+      F::forward(s, tw, trans,
+                 AdjPropStore<N>{cm0, cm1, want_prop ? vh_base + (size_t)(sl - 1) * NN : nullptr, e0, e1, c0, c1, gdz,
+                                 gt0, gt1});
+      F::inverse(s, tw);
+    } else if (want_probe || want_pos) {
+      F::template forward<false>(
+          s, tw, trans,
+          ProbeStore<N>{want_probe ? a.gPhat + (size_t)m * NN : nullptr, a.Phat + (size_t)m * NN, cr0, cr1, f0, f1,
+                        want_pos, gp0, gp1});
+    } else if (want_obj) {
+      F::elementwise(s, trans);
+    }
   }
+
+  // FP64 reduction of the five scalar partials over the CTA
+  double v5[5] = {gp0, gp1, gt0, gt1, gdz};
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+    for (int o = 16; o > 0; o >>= 1) v5[q] += __shfl_down_sync(0xffffffffu, v5[q], o);
   const int w = tid / 32;
-  if (lane == 0 && w < N / 32) {
-    red[5 * w + 0] = gp0;
-    red[5 * w + 1] = gp1;
-    red[5 * w + 2] = gt0;
-    red[5 * w + 3] = gt1;
-    red[5 * w + 4] = gdz;
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) red[5 * w + q] = v5[q];
   }
   __syncthreads();
   if (tid < 5) {
     double acc = 0.0;
-    for (int i = 0; i < N / 32; ++i) acc += red[5 * i + tid];
+    for (int i = 0; i < T / 32; ++i) acc += red[5 * i + tid];
     a.spart[(size_t)bm * 5 + tid] = acc;
   }
 }
