@@ -30,6 +30,8 @@ def nvcc() -> str:
 
 def flags(verbose: bool = False):
     f = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC, *ARCH]
+    # PTY_NVCC_FLAGS: extra -D tuning switches (thread counts, hook batch sizes) for sweeps
+    f += os.environ.get("PTY_NVCC_FLAGS", "").split()
     if verbose:
         f += ["-Xptxas", "-v"]
     return f

@@ -1,21 +1,25 @@
 // fft_smem.cuh -- 2D complex FFT of one N x N wavefield held in shared memory by one CTA.
 //
-// Layout.  The wave is float2 s[N][N + 1]: one complex pad per row makes the row stride odd, so
-// both a warp walking along a row (32 consecutive columns) and a warp walking down 32 rows of one
-// column touch 32 distinct bank pairs.
+// Layout.  The wave is float2 s[N][N + 1]: one complex pad per row makes the row stride odd, so a
+// warp walking along a row (32 consecutive columns) and a warp walking down 32 rows of one column
+// both touch 32 distinct bank pairs.
 //
-// Algorithm.  Every 1D pass transforms along the FIRST index with a two-factor Cooley-Tukey split
-// N = R1 * R2 (n = R2 n1 + n2, k = k1 + R1 k2):
-//   step A   R1-point DFT over n1 for every (column, n2), times W_N^{n2 k1}, written back in place;
-//   step B   R2-point DFT over n2 for every (column, k1), written back in place.
-// Lanes of a warp always own consecutive columns, so every shared-memory access is conflict-free;
-// the small DFTs run in registers.  The forward output is left in the digit order the split
-// produces (position p = R2 k1 + k2 holds frequency k1 + R1 k2): pointwise k-space work is done in
-// that order and the inverse pass (the same steps mirrored, decimation in time) consumes it, so no
-// reordering pass is ever needed.  A 2D transform is two 1D passes; the first one writes its
-// result transposed (s[c][p] instead of s[p][c]) so that the second pass again runs along the
-// first index.  Forward: natural s[r][c] -> k-space s[p1][p0]; inverse: k-space -> natural.
+// Algorithm.  N = A * 4.  Along axis 0 (columns) the split is n = 4 n1 + n2, k = k1 + A k2; along
+// axis 1 (rows) it is n = A n1 + n2, k = k1 + 4 k2.  A forward 2D transform is three steps, each
+// one read and one write of shared memory, with one barrier after each:
+//   col    for every (column, n2): A-point DFT over n1, times W_N^{n2 k1};
+//   block  for every 4 x 4 block {rows 4 k1 + q} x {cols A p + n2}: the 4-point column DFTs
+//          (q -> k2), then the 4-point row DFTs (p -> k1) times W_N^{n2 k1};
+//   row    for every (row, k1): A-point DFT over n2.
+// The small DFTs run in registers.  The output stays in the digit order the split produces
+// (k-space layout below): pointwise k-space work is done in that order and the inverse (the same
+// steps mirrored) consumes it, so no reordering pass is ever needed.  Lanes of a warp always own
+// consecutive columns (col, block) or consecutive rows (row), so shared memory is conflict-free.
 // Neither direction normalises (the inverse is the plain conjugate-sign sum).
+//
+// k-space layout: s[p0][p1]; axis-0 position p0 = 4 k1 + k2 holds bin k1 + A k2, axis-1 position
+// p1 = A k1 + k2 holds bin k1 + 4 k2.  Global k-space buffers are stored transposed, element
+// (p0, p1) at p1 * N + p0, so that the row step's lanes (consecutive p0) access them coalesced.
 //
 // Twiddles come from a per-CTA table tw[t] = exp(-2 pi i t / N) built with sincospif().
 #pragma once
@@ -37,31 +41,34 @@ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
 
-// z * W_R^k with W_R = exp(-2 pi i / R) (forward) or its conjugate (INV); k is a compile-time
-// constant once the calling loops are unrolled, so the branches fold away.
+// cos(2 pi e / 32) for e = 0..8 (the rest follow by symmetry).
+__device__ __forceinline__ constexpr float cos32(int e) {
+  return e == 0 ? 1.0f
+       : e == 1 ? 0.98078528040323043f
+       : e == 2 ? 0.92387953251128676f
+       : e == 3 ? 0.83146961230254524f
+       : e == 4 ? 0.70710678118654752f
+       : e == 5 ? 0.55557023301960222f
+       : e == 6 ? 0.38268343236508977f
+       : e == 7 ? 0.19509032201612826f
+                : 0.0f;
+}
+
+// z * W_R^k with W_R = exp(-2 pi i / R) (forward) or its conjugate (INV), for R | 32; k is a
+// compile-time constant once the calling loops are unrolled, so everything folds to constants.
 template <int R, bool INV>
 __device__ __forceinline__ float2 twmul(int k, float2 z) {
-  constexpr float H = 0.70710678118654752f;  // cos(pi/4)
-  constexpr float C8 = 0.92387953251128676f;  // cos(pi/8)
-  constexpr float S8 = 0.38268343236508977f;  // sin(pi/8)
-  const int e = k * (16 / R);                 // angle in units of 2 pi / 16
-  float c, s;                                 // W = c - i s (forward)
-  switch (e) {
-    case 0: return z;
-    case 4: return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
-    case 2: c = H; s = H; break;
-    case 6: c = -H; s = H; break;
-    case 1: c = C8; s = S8; break;
-    case 3: c = S8; s = C8; break;
-    case 5: c = -S8; s = C8; break;
-    case 7: c = -C8; s = S8; break;
-    default: c = 1.f; s = 0.f; break;
-  }
+  const int e = k * (32 / R);  // angle in units of 2 pi / 32, 0 <= e < 16
+  if (e == 0) return z;
+  if (e == 8) return INV ? make_float2(-z.y, z.x) : make_float2(z.y, -z.x);
+  // W = c - i s with c = cos(2 pi e / 32), s = sin(2 pi e / 32) = cos(2 pi (8 - e) / 32)
+  const float c = e < 8 ? cos32(e) : -cos32(16 - e);
+  float s = e < 8 ? cos32(8 - e) : cos32(e - 8);
   if (INV) s = -s;
   return make_float2(fmaf(z.x, c, z.y * s), fmaf(z.y, c, -z.x * s));
 }
 
-// In-register R-point DFT (R = 2, 4, 8, 16), natural order in and out, radix-2 decimation in time.
+// In-register R-point DFT (R = 2 ... 32), natural order in and out, radix-2 decimation in time.
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2* x) {
   if constexpr (R == 1) {
@@ -88,199 +95,269 @@ __device__ __forceinline__ void dft(float2* x) {
   }
 }
 
+// Position of frequency bin k along axis 0 / axis 1 of the k-space layout, and the inverse maps.
 template <int N>
-struct Radix;
-template <>
-struct Radix<64> {
-  static constexpr int R1 = 8, R2 = 8;
-};
-template <>
-struct Radix<128> {
-  static constexpr int R1 = 8, R2 = 16;
-};
-
-// Position of frequency bin k (0..N-1, DFT order) along one axis of the k-space layout.
-template <int N>
-__host__ __device__ constexpr int kpos(int k) {
-  return Radix<N>::R2 * (k % Radix<N>::R1) + k / Radix<N>::R1;
+__host__ __device__ constexpr int kpos0(int k) {
+  return 4 * (k % (N / 4)) + k / (N / 4);
 }
-// Frequency bin held at k-space position p.
 template <int N>
-__host__ __device__ constexpr int kbin(int p) {
-  return p / Radix<N>::R2 + Radix<N>::R1 * (p % Radix<N>::R2);
+__host__ __device__ constexpr int kbin0(int p) {
+  return p / 4 + (N / 4) * (p % 4);
+}
+template <int N>
+__host__ __device__ constexpr int kpos1(int k) {
+  return (N / 4) * (k % 4) + k / 4;
+}
+template <int N>
+__host__ __device__ constexpr int kbin1(int p) {
+  return p / (N / 4) + 4 * (p % (N / 4));
 }
 
-// Element hooks fused into the FFT passes.  A hook sees K elements of one task in registers: the
-// elements sit at rows row0 + k * rstride (k < K) of column c of the array being transformed (the
-// first index is the row).  Load hooks run right after the elements are read, store hooks right
-// before they are written.  A hook with kReplaces = true produces the values itself, so the
-// shared-memory read is skipped.
+// Element hooks fused into the FFT steps.  A hook sees K elements of one task in registers: element
+// k sits at (row0 + k * rs, col0 + k * cs) of the array being transformed.  Load hooks run right
+// after the elements are read (natural layout in a forward transform, k-space in an inverse), store
+// hooks right before they are written (k-space).  A hook with kReplaces = true produces the values
+// itself, so the shared-memory read is skipped.  Hooks are called on chunks of kChunk elements so
+// that their global loads can be batched without holding a whole task's worth of registers.
 struct NoHook {
   static constexpr bool kReplaces = false;
+  static constexpr int kChunk = 1;
   template <int K>
-  __device__ __forceinline__ void operator()(int, int, int, float2*) {}
+  __device__ __forceinline__ void operator()(int, int, int, int, float2*) {}
 };
 
 template <int N, int T>
 struct Fft2 {
-  static constexpr int R1 = Radix<N>::R1, R2 = Radix<N>::R2, RS = N + 1;
-  static_assert(R1 * R2 == N, "radix split");
-  static_assert((N * R1) % T == 0 && (N * R2) % T == 0, "tasks must divide the CTA");
-  static_assert(T % N == 0, "each thread keeps one column");
-  static constexpr int NA = N * R2 / T;  // step-A tasks per thread
-  static constexpr int NB = N * R1 / T;  // step-B tasks per thread
-
+  static constexpr int A = N / 4, RS = N + 1;
+  static_assert(A == 16 || A == 32, "N = 64 or 128");
+  static constexpr int NCOL = 4 * N / T;    // col-step tasks per thread: (c, n2)
+  static constexpr int NBLK = A * A / T;    // block-step tasks per thread: (k1, n2)
+  static constexpr int NROW = 4 * N / T;    // row-step tasks per thread: (r, k1)
+  static_assert(NCOL * T == 4 * N && NBLK * T == A * A, "tasks must divide the CTA");
   template <class H>
   static constexpr bool kPlain = std::is_same_v<std::decay_t<H>, NoHook>;
 
-  // Forward 1D DFT along the first index.  TRANSPOSE: write result to s[c][p] instead of s[p][c].
-  // WRITE = false: the result only goes through the store hook (nothing is written back).  Steps
-  // with a hook run one task at a time (the hook's loads are batched inside the task); steps
-  // without one unroll over the thread's tasks.
-  template <bool TRANSPOSE, bool WRITE = true, class LH = NoHook, class SH = NoHook>
-  __device__ static void fwd_pass(float2* s, const float2* tw, LH&& lh = LH(), SH&& sh = SH()) {
-    static_assert(!(TRANSPOSE && !kPlain<SH>), "store hooks only on non-transposing passes");
-    const int tid = threadIdx.x;
-    constexpr int UA = kPlain<LH> ? NA : 1;
-#pragma unroll(UA)
-    for (int i = 0; i < NA; ++i) {
-      const int t = tid + i * T;
+  template <class H>
+  __device__ static __forceinline__ void hook(H& h, int row0, int rs, int col0, int cs, float2* v) {
+    if constexpr (!kPlain<H>) {
+      constexpr int KC = std::decay_t<H>::kChunk;
+#pragma unroll
+      for (int q = 0; q < A; q += KC) h.template operator()<KC>(row0 + q * rs, rs, col0 + q * cs, cs, v + q);
+    }
+  }
+
+  // ---- forward steps ----
+  template <class LH>
+  __device__ static void col_fwd(float2* s, const float2* tw, LH& lh) {
+#pragma unroll 1
+    for (int i = 0; i < NCOL; ++i) {
+      const int t = threadIdx.x + i * T;
       const int c = t % N, n2 = t / N;
-      float2 v[R1];
+      float2 v[A];
       if (!std::remove_reference_t<LH>::kReplaces) {
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) v[n1] = s[(R2 * n1 + n2) * RS + c];
+        for (int n1 = 0; n1 < A; ++n1) v[n1] = s[(4 * n1 + n2) * RS + c];
       }
-      lh.template operator()<R1>(n2, R2, c, v);
-      dft<R1, false>(v);
+      hook(lh, n2, 4, c, 0, v);
+      dft<A, false>(v);
 #pragma unroll
-      for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
+      for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
 #pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) s[(R2 * k1 + n2) * RS + c] = v[k1];
+      for (int k1 = 0; k1 < A; ++k1) s[(4 * k1 + n2) * RS + c] = v[k1];
     }
     __syncthreads();
-    if constexpr (TRANSPOSE) {
-      float2 v[NB][R2];
+  }
+  __device__ static void block_fwd(float2* s, const float2* tw) {
 #pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        const int t = tid + i * T;
-        const int c = t % N, k1 = t / N;
+    for (int i = 0; i < NBLK; ++i) {
+      const int t = threadIdx.x + i * T;
+      const int n2 = t % A, k1 = t / A;
+      float2 b[4][4];  // [q: row digit][p: column digit]
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) v[i][n2] = s[(R2 * k1 + n2) * RS + c];
-        dft<R2, false>(v[i]);
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) b[q][p] = s[(4 * k1 + q) * RS + A * p + n2];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        float2 col[4] = {b[0][p], b[1][p], b[2][p], b[3][p]};
+        dft<4, false>(col);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q][p] = col[q];
       }
-      __syncthreads();
+      const float2 w1 = tw[n2], w2 = tw[2 * n2], w3 = tw[3 * n2];
 #pragma unroll
-      for (int i = 0; i < NB; ++i) {
-        const int t = tid + i * T;
-        const int c = t % N, k1 = t / N;
-#pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) s[c * RS + R2 * k1 + k2] = v[i][k2];
+      for (int q = 0; q < 4; ++q) {
+        dft<4, false>(b[q]);
+        b[q][1] = cmul(b[q][1], w1);
+        b[q][2] = cmul(b[q][2], w2);
+        b[q][3] = cmul(b[q][3], w3);
       }
-    } else {
-      constexpr int UB = kPlain<SH> ? NB : 1;
-#pragma unroll(UB)
-      for (int i = 0; i < NB; ++i) {
-        const int t = tid + i * T;
-        const int c = t % N, k1 = t / N;
-        float2 v[R2];
 #pragma unroll
-        for (int n2 = 0; n2 < R2; ++n2) v[n2] = s[(R2 * k1 + n2) * RS + c];
-        dft<R2, false>(v);
-        sh.template operator()<R2>(R2 * k1, 1, c, v);
-        if (WRITE) {
+      for (int q = 0; q < 4; ++q)
 #pragma unroll
-          for (int k2 = 0; k2 < R2; ++k2) s[(R2 * k1 + k2) * RS + c] = v[k2];
-        }
+        for (int p = 0; p < 4; ++p) s[(4 * k1 + q) * RS + A * p + n2] = b[q][p];
+    }
+    __syncthreads();
+  }
+  template <bool WRITE, class SH>
+  __device__ static void row_fwd(float2* s, SH& sh) {
+#pragma unroll 1
+    for (int i = 0; i < NROW; ++i) {
+      const int t = threadIdx.x + i * T;
+      const int r = t % N, k1 = t / N;
+      float2 v[A];
+#pragma unroll
+      for (int n2 = 0; n2 < A; ++n2) v[n2] = s[r * RS + A * k1 + n2];
+      dft<A, false>(v);
+      hook(sh, r, 0, A * k1, 1, v);
+      if (WRITE) {
+#pragma unroll
+        for (int k2 = 0; k2 < A; ++k2) s[r * RS + A * k1 + k2] = v[k2];
       }
     }
     __syncthreads();
   }
 
-  // Inverse 1D DFT along the first index (input in k-space digit order, output natural order).
-  template <bool TRANSPOSE, class LH = NoHook>
-  __device__ static void inv_pass(float2* s, const float2* tw, LH&& lh = LH()) {
-    const int tid = threadIdx.x;
-    constexpr int UB = kPlain<LH> ? NB : 1;
-#pragma unroll(UB)
-    for (int i = 0; i < NB; ++i) {
-      const int t = tid + i * T;
-      const int c = t % N, k1 = t / N;
-      float2 v[R2];
+  // ---- inverse steps (mirror images) ----
+  template <class LH>
+  __device__ static void row_inv(float2* s, const float2* tw, LH& lh) {
+#pragma unroll 1
+    for (int i = 0; i < NROW; ++i) {
+      const int t = threadIdx.x + i * T;
+      const int r = t % N, k1 = t / N;
+      float2 v[A];
       if (!std::remove_reference_t<LH>::kReplaces) {
 #pragma unroll
-        for (int k2 = 0; k2 < R2; ++k2) v[k2] = s[(R2 * k1 + k2) * RS + c];
+        for (int k2 = 0; k2 < A; ++k2) v[k2] = s[r * RS + A * k1 + k2];
       }
-      lh.template operator()<R2>(R2 * k1, 1, c, v);
-      dft<R2, true>(v);
+      hook(lh, r, 0, A * k1, 1, v);
+      dft<A, true>(v);
 #pragma unroll
-      for (int n2 = 1; n2 < R2; ++n2) v[n2] = cmulc(tw[n2 * k1], v[n2]);
+      for (int n2 = 1; n2 < A; ++n2) v[n2] = cmulc(tw[n2 * k1], v[n2]);
 #pragma unroll
-      for (int n2 = 0; n2 < R2; ++n2) s[(R2 * k1 + n2) * RS + c] = v[n2];
+      for (int n2 = 0; n2 < A; ++n2) s[r * RS + A * k1 + n2] = v[n2];
     }
     __syncthreads();
-    if constexpr (TRANSPOSE) {
-      float2 v[NA][R1];
+  }
+  __device__ static void block_inv(float2* s) {
 #pragma unroll
-      for (int i = 0; i < NA; ++i) {
-        const int t = tid + i * T;
-        const int c = t % N, n2 = t / N;
+    for (int i = 0; i < NBLK; ++i) {
+      const int t = threadIdx.x + i * T;
+      const int n2 = t % A, k1 = t / A;
+      float2 b[4][4];
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) v[i][k1] = s[(R2 * k1 + n2) * RS + c];
-        dft<R1, true>(v[i]);
+      for (int q = 0; q < 4; ++q)
+#pragma unroll
+        for (int p = 0; p < 4; ++p) b[q][p] = s[(4 * k1 + q) * RS + A * p + n2];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) dft<4, true>(b[q]);
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        float2 col[4] = {b[0][p], b[1][p], b[2][p], b[3][p]};
+        dft<4, true>(col);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q][p] = col[q];
       }
-      __syncthreads();
 #pragma unroll
-      for (int i = 0; i < NA; ++i) {
-        const int t = tid + i * T;
-        const int c = t % N, n2 = t / N;
+      for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) s[c * RS + R2 * n1 + n2] = v[i][n1];
-      }
-    } else {
+        for (int p = 0; p < 4; ++p) s[(4 * k1 + q) * RS + A * p + n2] = b[q][p];
+    }
+    __syncthreads();
+  }
+  __device__ static void col_inv(float2* s, const float2* tw) {
+#pragma unroll 1
+    for (int i = 0; i < NCOL; ++i) {
+      const int t = threadIdx.x + i * T;
+      const int c = t % N, n2 = t / N;
+      float2 v[A];
 #pragma unroll
-      for (int i = 0; i < NA; ++i) {
-        const int t = tid + i * T;
-        const int c = t % N, n2 = t / N;
-        float2 v[R1];
+      for (int k1 = 0; k1 < A; ++k1) v[k1] = s[(4 * k1 + n2) * RS + c];
 #pragma unroll
-        for (int k1 = 0; k1 < R1; ++k1) v[k1] = s[(R2 * k1 + n2) * RS + c];
-        dft<R1, true>(v);
+      for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(tw[n2 * k1], v[k1]);
+      dft<A, true>(v);
 #pragma unroll
-        for (int n1 = 0; n1 < R1; ++n1) s[(R2 * n1 + n2) * RS + c] = v[n1];
-      }
+      for (int n1 = 0; n1 < A; ++n1) s[(4 * n1 + n2) * RS + c] = v[n1];
     }
     __syncthreads();
   }
 
-  // natural s[r][c] -> k-space s[p1][p0] (unnormalised forward DFT).  `load` sees natural (r, c);
-  // `store` sees k-space (p1, p0).  WRITE = false leaves the result only to `store`.
+  // ---- fused steps: the end of one transform and the start of the next share a task ----
+  // col_inv (finishing an inverse FFT, natural output) -> hook (natural (r, c)) -> col_fwd
+  // (starting the next forward FFT).  FWD = false: stop after the hook (nothing written back).
+  template <bool FWD, class H>
+  __device__ static void col_inv_fwd(float2* s, const float2* tw, H& h) {
+#pragma unroll 1
+    for (int i = 0; i < NCOL; ++i) {
+      const int t = threadIdx.x + i * T;
+      const int c = t % N, n2 = t / N;
+      float2 v[A];
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1) v[k1] = s[(4 * k1 + n2) * RS + c];
+#pragma unroll
+      for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(tw[n2 * k1], v[k1]);
+      dft<A, true>(v);
+      hook(h, n2, 4, c, 0, v);
+      if (FWD) {
+        dft<A, false>(v);
+#pragma unroll
+        for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
+#pragma unroll
+        for (int k1 = 0; k1 < A; ++k1) s[(4 * k1 + n2) * RS + c] = v[k1];
+      }
+    }
+    __syncthreads();
+  }
+  // row_fwd (finishing a forward FFT) -> hook (k-space (p0, p1)) -> row_inv (starting an inverse)
+  template <class H>
+  __device__ static void row_fwd_inv(float2* s, const float2* tw, H& h) {
+#pragma unroll 1
+    for (int i = 0; i < NROW; ++i) {
+      const int t = threadIdx.x + i * T;
+      const int r = t % N, k1 = t / N;
+      float2 v[A];
+#pragma unroll
+      for (int n2 = 0; n2 < A; ++n2) v[n2] = s[r * RS + A * k1 + n2];
+      dft<A, false>(v);
+      hook(h, r, 0, A * k1, 1, v);
+      dft<A, true>(v);
+#pragma unroll
+      for (int n2 = 1; n2 < A; ++n2) v[n2] = cmulc(tw[n2 * k1], v[n2]);
+#pragma unroll
+      for (int n2 = 0; n2 < A; ++n2) s[r * RS + A * k1 + n2] = v[n2];
+    }
+    __syncthreads();
+  }
+
+  // natural s[r][c] -> k-space s[p0][p1] (unnormalised forward DFT).  `load` sees natural (r, c);
+  // `store` sees k-space (p0, p1).  WRITE = false leaves the result only to `store`.
   template <bool WRITE = true, class LH = NoHook, class SH = NoHook>
   __device__ static void forward(float2* s, const float2* tw, LH&& load = LH(), SH&& store = SH()) {
-    fwd_pass<true>(s, tw, load);
-    fwd_pass<false, WRITE>(s, tw, NoHook(), store);
+    col_fwd(s, tw, load);
+    block_fwd(s, tw);
+    row_fwd<WRITE>(s, store);
   }
-  // k-space s[p1][p0] -> natural s[r][c] (unnormalised inverse DFT); `load` sees k-space (p1, p0).
+  // k-space s[p0][p1] -> natural s[r][c] (unnormalised inverse DFT); `load` sees k-space (p0, p1).
   template <class LH = NoHook>
   __device__ static void inverse(float2* s, const float2* tw, LH&& load = LH()) {
-    inv_pass<true>(s, tw, load);
-    inv_pass<false>(s, tw);
+    row_inv(s, tw, load);
+    block_inv(s);
+    col_inv(s, tw);
   }
 
-  // Apply a hook to every element of the natural-layout array (same task shape as step A).
+  // Apply a hook to every element of the natural-layout array (same task shape as the col step).
   template <class H>
   __device__ static void elementwise(float2* s, H&& h) {
-    const int tid = threadIdx.x;
 #pragma unroll 1
-    for (int i = 0; i < NA; ++i) {
-      const int t = tid + i * T;
+    for (int i = 0; i < NCOL; ++i) {
+      const int t = threadIdx.x + i * T;
       const int c = t % N, n2 = t / N;
-      float2 v[R1];
+      float2 v[A];
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) v[n1] = s[(R2 * n1 + n2) * RS + c];
-      h.template operator()<R1>(n2, R2, c, v);
+      for (int n1 = 0; n1 < A; ++n1) v[n1] = s[(4 * n1 + n2) * RS + c];
+      hook(h, n2, 4, c, 0, v);
 #pragma unroll
-      for (int n1 = 0; n1 < R1; ++n1) s[(R2 * n1 + n2) * RS + c] = v[n1];
+      for (int n1 = 0; n1 < A; ++n1) s[(4 * n1 + n2) * RS + c] = v[n1];
     }
     __syncthreads();
   }

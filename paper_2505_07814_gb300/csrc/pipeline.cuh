@@ -20,17 +20,52 @@
 #include "fft_smem.cuh"
 #include "pty_internal.h"
 
+#ifndef PTY_TF128
+#define PTY_TF128 256
+#endif
+#ifndef PTY_TA128
+#define PTY_TA128 512
+#endif
+#ifndef PTY_KS
+#define PTY_KS 4
+#endif
+#ifndef PTY_KT
+#define PTY_KT 4
+#endif
+#ifndef PTY_KP
+#define PTY_KP 4
+#endif
+#ifndef PTY_KF
+#define PTY_KF 4
+#endif
+#ifndef PTY_KG
+#define PTY_KG 4
+#endif
+#ifndef PTY_KA
+#define PTY_KA 4
+#endif
+#ifndef PTY_KQ
+#define PTY_KQ 4
+#endif
+#ifndef PTY_KR
+#define PTY_KR 4
+#endif
+
 namespace pty {
 
 template <int N>
 struct Launch;
+// Threads per CTA of the forward (TF) and adjoint (TA) kernels and of the small kernels (T), with the
+// CTAs per SM the register budget is sized for.  At N = 128 one wave (132 KB) fills the SM's shared
+// memory: the forward runs 256 threads with up to 255 registers each, the adjoint 512 threads so
+// that more of its checkpoint / transmission loads are in flight.
 template <>
 struct Launch<64> {
-  static constexpr int T = 256, MIN_BLOCKS = 2;
+  static constexpr int T = 256, TF = 128, TA = 128, MINB_F = 4, MINB_A = 4;
 };
 template <>
 struct Launch<128> {
-  static constexpr int T = 512, MIN_BLOCKS = 1;
+  static constexpr int T = 512, TF = PTY_TF128, TA = PTY_TA128, MINB_F = 1, MINB_A = 1;
 };
 
 // exp(i pi x); x is reduced modulo 2 in double precision before the float sincospi.
@@ -121,8 +156,8 @@ __global__ void __launch_bounds__(T) k_probe_spectrum(const float2* __restrict__
   F::forward(s, tw);
   float2* out = Phat + (size_t)m * N * N;
   float2* g = gPhat ? gPhat + (size_t)m * N * N : nullptr;
-  for (int e = tid; e < N * N; e += T) {
-    out[e] = s[(e / N) * RS + e % N];
+  for (int e = tid; e < N * N; e += T) {  // e = p1 * N + p0
+    out[e] = s[(e % N) * RS + e / N];
     if (g) g[e] = make_float2(0.f, 0.f);
   }
 }
@@ -149,6 +184,19 @@ __host__ __device__ constexpr size_t fwd_smem_bytes() {
   return sizeof(float2) * ((size_t)N * (N + 1) + 5 * N);
 }
 
+// Loads of data written by earlier kernels and read-only here (checkpoints, spectra, transmission):
+// non-coherent and not volatile, so the compiler may batch them ahead of this thread's atomics.
+__device__ __forceinline__ float2 ld_ro(const float2* p) {
+  float2 v;
+  asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float ld_ro(const float* p) {
+  float v;
+  asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+  return v;
+}
+
 // L2 prefetch of a byte range (rounded out to 16-byte boundaries).
 __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
   const uintptr_t a = (uintptr_t)p & ~(uintptr_t)15;
@@ -167,37 +215,41 @@ __device__ __forceinline__ void prefetch_block(const float2* base) {
   if (threadIdx.x < 8) prefetch_l2(reinterpret_cast<const char*>(base) + threadIdx.x * chunk, chunk);
 }
 
-// ---- forward hooks (see NoHook for the calling convention) ----
+// ---- forward hooks (see NoHook for the calling convention).  Natural-layout hooks run in the
+// col step (lanes own consecutive columns); k-space hooks run in the row step (lanes own
+// consecutive k-space rows p0, so global k-space buffers are indexed p1 * N + p0). ----
 // shifted-probe spectrum P^_m R_j (k-space), replaces the shared-memory contents
 template <int N>
 struct ShiftLoad {
   static constexpr bool kReplaces = true;
+  static constexpr int kChunk = PTY_KS;
   const float2* Ph;
   const float2 *ra0, *ra1;
   template <int K>
-  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+  __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     float2 p[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) p[k] = Ph[(row0 + k * rs) * N + c];
+    for (int k = 0; k < K; ++k) p[k] = ld_ro(Ph + (c0 + k * cs) * N + r0 + k * rs);
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = cmul(cmul(p[k], ra1[row0 + k * rs]), ra0[c]);
+    for (int k = 0; k < K; ++k) v[k] = cmul(cmul(p[k], ra0[r0 + k * rs]), ra1[c0 + k * cs]);
   }
 };
 // transmission of slice s: checkpoint the entering wave, then multiply by T (natural layout)
 template <int N>
 struct TransLoad {
   static constexpr bool kReplaces = false;
+  static constexpr int kChunk = PTY_KT;
   const float2* Ts;  // patch corner in T
   int W;
   float2* ck;  // checkpoint block or nullptr
   template <int K>
-  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+  __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     float2 t[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) t[k] = __ldg(Ts + (size_t)(row0 + k * rs) * W + c);
+    for (int k = 0; k < K; ++k) t[k] = ld_ro(Ts + (size_t)(r0 + k * rs) * W + c0 + k * cs);
     if (ck) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) __stcs(ck + (row0 + k * rs) * N + c, v[k]);
+      for (int k = 0; k < K; ++k) __stcs(ck + (r0 + k * rs) * N + c0 + k * cs, v[k]);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = cmul(v[k], t[k]);
@@ -207,16 +259,16 @@ struct TransLoad {
 template <int N>
 struct PropStore {
   static constexpr bool kReplaces = false;
+  static constexpr int kChunk = PTY_KP;
   const float2 *m0, *m1;
   float2* vh;
   template <int K>
-  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
-    const float2 mc = m0[c];
+  __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int r = row0 + k * rs;
-      v[k] = cmul(cmul(v[k], m1[r]), mc);
-      if (vh) __stcs(vh + r * N + c, v[k]);
+      const int r = r0 + k * rs, c = c0 + k * cs;
+      v[k] = cmul(cmul(v[k], m0[r]), m1[c]);
+      if (vh) __stcs(vh + c * N + r, v[k]);
     }
   }
 };
@@ -224,14 +276,15 @@ struct PropStore {
 template <int N>
 struct FarStore {
   static constexpr bool kReplaces = false;
+  static constexpr int kChunk = PTY_KF;
   float2* Psi;
   float* Im;
   template <int K>
-  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+  __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     const float inv_n = 1.0f / (float)N;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int e = (row0 + k * rs) * N + c;
+      const int e = (c0 + k * cs) * N + r0 + k * rs;
       const float2 x = cscale(v[k], inv_n);
       if (Psi) __stcs(Psi + e, x);
       Im[e] = fmaf(x.x, x.x, x.y * x.y);
@@ -240,7 +293,7 @@ struct FarStore {
 };
 
 template <int N, int T>
-__global__ void __launch_bounds__(T, Launch<N>::MIN_BLOCKS) k_forward(FwdArgs a) {
+__global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   using F = Fft2<N, T>;
   constexpr int RS = F::RS;
   constexpr int NN = N * N;
@@ -266,31 +319,37 @@ __global__ void __launch_bounds__(T, Launch<N>::MIN_BLOCKS) k_forward(FwdArgs a)
 
   build_twiddles<N>(tw);
   if (tid < N) {
-    const int q = signed_bin<N>(kbin<N>(tid));
+    // axis-0 tables are indexed by k-space row p0, axis-1 tables by k-space column p1
+    const int q0 = signed_bin<N>(kbin0<N>(tid)), q1 = signed_bin<N>(kbin1<N>(tid));
     const float inv_nn = 1.0f / (float)NN;
-    ra0[tid] = cscale(expipi(-2.0 * q * (double)d0 / N), inv_nn);
-    ra1[tid] = expipi(-2.0 * q * (double)d1 / N);
+    ra0[tid] = cscale(expipi(-2.0 * q0 * (double)d0 / N), inv_nn);
+    ra1[tid] = expipi(-2.0 * q1 * (double)d1 / N);
     // Eq. 4 split into its two axes: exp(i pi (-lam dz k_a^2 + 2 dz k_a tan th_a))
-    const double k = q / (N * (double)a.dx);
-    const double base = -(double)a.lam * dz * k * k;
-    pm0[tid] = cscale(expipi(base + 2.0 * dz * k * tan((double)th0)), inv_nn);
-    pm1[tid] = expipi(base + 2.0 * dz * k * tan((double)th1));
+    const double k0 = q0 / (N * (double)a.dx), k1 = q1 / (N * (double)a.dx);
+    pm0[tid] = cscale(expipi(-(double)a.lam * dz * k0 * k0 + 2.0 * dz * k0 * tan((double)th0)), inv_nn);
+    pm1[tid] = expipi(-(double)a.lam * dz * k1 * k1 + 2.0 * dz * k1 * tan((double)th1));
   }
   __syncthreads();
 
-  // shifted probe P_j = F^-1[P^_m ramp]
-  F::inverse(s, tw, ShiftLoad<N>{a.Phat + (size_t)m * NN, ra0, ra1});
-
+  // Shifted probe P_j = F^-1[P^_m R]: the row and block steps of the inverse here; its column step
+  // is fused with the first transmission below.  Every propagation F^-1[M F[T psi]] likewise runs
+  // as: fused column step (inverse end, T, checkpoint, forward start), block step, fused row step
+  // (forward end, M, inverse start), block step.
+  ShiftLoad<N> shift{a.Phat + (size_t)m * NN, ra0, ra1};
+  F::row_inv(s, tw, shift);
+  F::block_inv(s);
   for (int sl = 0; sl < a.Nz; ++sl) {
     if (sl + 1 < a.Nz) prefetch_patch<N>(Tpatch + (sl + 1) * plane, a.W);
     TransLoad<N> trans{Tpatch + sl * plane, a.W, a.ckpt ? a.ckpt + ((size_t)bm * a.Nz + sl) * NN : nullptr};
+    F::template col_inv_fwd<true>(s, tw, trans);
+    F::block_fwd(s, tw);
     if (sl + 1 < a.Nz) {
-      float2* vh = a.vhat ? a.vhat + ((size_t)bm * (a.Nz - 1) + sl) * NN : nullptr;
-      F::forward(s, tw, trans, PropStore<N>{pm0, pm1, vh});
-      F::inverse(s, tw);
+      PropStore<N> prop{pm0, pm1, a.vhat ? a.vhat + ((size_t)bm * (a.Nz - 1) + sl) * NN : nullptr};
+      F::row_fwd_inv(s, tw, prop);
+      F::block_inv(s);
     } else {
-      F::template forward<false>(s, tw, trans,
-                                 FarStore<N>{a.Psi ? a.Psi + (size_t)bm * NN : nullptr, a.Imode + (size_t)bm * NN});
+      FarStore<N> far{a.Psi ? a.Psi + (size_t)bm * NN : nullptr, a.Imode + (size_t)bm * NN};
+      F::template row_fwd<false>(s, far);
     }
   }
 }
@@ -359,7 +418,7 @@ __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
   float sd = 0.f, st = 0.f;
   for (int q = tid; q < NN; q += T) {
     const int k0 = (q / N + N / 2) & (N - 1), k1 = (q % N + N / 2) & (N - 1);
-    const int l = kpos<N>(k1) * RS + kpos<N>(k0);
+    const int l = kpos1<N>(k1) * RS + kpos0<N>(k0);  // staging row p1, column p0 (global p1 * N + p0)
     const float I = L[l];
     if (a.I_model) a.I_model[(size_t)b * NN + q] = I;
     if (Id) {
@@ -466,18 +525,19 @@ __host__ __device__ constexpr size_t adj_smem_bytes() {
 template <int N>
 struct FarGradLoad {
   static constexpr bool kReplaces = true;
+  static constexpr int kChunk = PTY_KG;
   const float* u;
   const float2* Psi;
   float gs;
   template <int K>
-  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+  __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     float2 p[K];
     float w[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int e = (row0 + k * rs) * N + c;
-      p[k] = __ldcs(Psi + e);
-      w[k] = u[e];
+      const int e = (c0 + k * cs) * N + r0 + k * rs;
+      p[k] = ld_ro(Psi + e);
+      w[k] = ld_ro(u + e);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = cscale(p[k], gs * w[k]);
@@ -487,22 +547,23 @@ struct FarGradLoad {
 template <int N>
 struct AdjTransLoad {
   static constexpr bool kReplaces = false;
+  static constexpr int kChunk = PTY_KA;
   const float2* Ts;  // patch corner in T
   float2* gTs;       // patch corner in the dL/dT accumulator
   const float2* ck;  // checkpoint of the wave entering slice s, or nullptr (no object gradient)
   int W;
   template <int K>
-  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
+  __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     float2 t[K], ps[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int r = row0 + k * rs;
-      t[k] = __ldg(Ts + (size_t)r * W + c);
-      if (ck) ps[k] = __ldcs(ck + r * N + c);
+      const int r = r0 + k * rs, c = c0 + k * cs;
+      t[k] = ld_ro(Ts + (size_t)r * W + c);
+      if (ck) ps[k] = ld_ro(ck + r * N + c);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      if (ck) atomicAdd(gTs + (size_t)(row0 + k * rs) * W + c, cmulc(ps[k], v[k]));
+      if (ck) atomicAdd(gTs + (size_t)(r0 + k * rs) * W + c0 + k * cs, cmulc(ps[k], v[k]));
       v[k] = cmulc(t[k], v[k]);
     }
   }
@@ -512,29 +573,28 @@ struct AdjTransLoad {
 template <int N>
 struct AdjPropStore {
   static constexpr bool kReplaces = false;
+  static constexpr int kChunk = PTY_KQ;
   const float2 *cm0, *cm1;
   const float2* vh;  // stored v^/N^2 of this propagation, or nullptr
-  const float *e0, *e1, *c0, *c1;
+  const float *e0, *e1, *c0t, *c1t;
   float &dz, &t0, &t1;
   template <int K>
-  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
-    const float2 mc = cm0[c];
+  __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     if (vh) {
       float2 x[K];
 #pragma unroll
-      for (int k = 0; k < K; ++k) x[k] = __ldcs(vh + (row0 + k * rs) * N + c);
-      const float ec = e0[c], cc = c0[c];
+      for (int k = 0; k < K; ++k) x[k] = ld_ro(vh + (c0 + k * cs) * N + r0 + k * rs);
 #pragma unroll
       for (int k = 0; k < K; ++k) {
-        const int r = row0 + k * rs;
+        const int r = r0 + k * rs, c = c0 + k * cs;
         const float w = v[k].x * x[k].y - v[k].y * x[k].x;
-        dz = fmaf(w, ec + e1[r], dz);
-        t0 = fmaf(w, cc, t0);
-        t1 = fmaf(w, c1[r], t1);
+        dz = fmaf(w, e0[r] + e1[c], dz);
+        t0 = fmaf(w, c0t[r], t0);
+        t1 = fmaf(w, c1t[c], t1);
       }
     }
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = cmul(cmul(v[k], cm1[row0 + k * rs]), mc);
+    for (int k = 0; k < K; ++k) v[k] = cmul(cmul(v[k], cm0[r0 + k * rs]), cm1[c0 + k * cs]);
   }
 };
 // dL/dP_j in k-space: probe-spectrum gradient conj(R) g^ (scatter-add) and the position terms
@@ -542,6 +602,7 @@ struct AdjPropStore {
 template <int N>
 struct ProbeStore {
   static constexpr bool kReplaces = false;
+  static constexpr int kChunk = PTY_KR;
   float2* gP;  // or nullptr
   const float2* Ph;
   const float2 *cr0, *cr1;
@@ -549,30 +610,29 @@ struct ProbeStore {
   bool pos;
   float &p0, &p1;
   template <int K>
-  __device__ __forceinline__ void operator()(int row0, int rs, int c, float2* v) {
-    const float2 crc = cr0[c];
+  __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     float2 ph[K];
     if (pos) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) ph[k] = Ph[(row0 + k * rs) * N + c];
+      for (int k = 0; k < K; ++k) ph[k] = ld_ro(Ph + (c0 + k * cs) * N + r0 + k * rs);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int r = row0 + k * rs;
-      const float2 cr = cmul(cr1[r], crc);  // conj(R)
-      if (gP) atomicAdd(gP + r * N + c, cmul(cr, v[k]));
+      const int r = r0 + k * rs, c = c0 + k * cs;
+      const float2 cr = cmul(cr0[r], cr1[c]);  // conj(R)
+      if (gP) atomicAdd(gP + c * N + r, cmul(cr, v[k]));
       if (pos) {
         const float2 PR = cmulc(cr, ph[k]);  // R P^
         const float w = v[k].x * PR.y - v[k].y * PR.x;
-        p0 = fmaf(w, f0[c], p0);
-        p1 = fmaf(w, f1[r], p1);
+        p0 = fmaf(w, f0[r], p0);
+        p1 = fmaf(w, f1[c], p1);
       }
     }
   }
 };
 
 template <int N, int T>
-__global__ void __launch_bounds__(T, Launch<N>::MIN_BLOCKS) k_adjoint(AdjArgs a) {
+__global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   using F = Fft2<N, T>;
   constexpr int RS = F::RS;
   constexpr int NN = N * N;
@@ -612,28 +672,31 @@ __global__ void __launch_bounds__(T, Launch<N>::MIN_BLOCKS) k_adjoint(AdjArgs a)
 
   build_twiddles<N>(tw);
   if (tid < N) {
-    const int q = signed_bin<N>(kbin<N>(tid));
+    // axis-0 tables are indexed by k-space row p0, axis-1 tables by k-space column p1
+    const int q0 = signed_bin<N>(kbin0<N>(tid)), q1 = signed_bin<N>(kbin1<N>(tid));
     const float inv_nn = 1.0f / (float)NN;
-    const double k = q / (N * (double)a.dx);
-    const double base = -(double)a.lam * dz * k * k;
+    const double k0 = q0 / (N * (double)a.dx), k1 = q1 / (N * (double)a.dx);
     const double tn0 = tan((double)th0), tn1 = tan((double)th1);
-    cm0[tid] = cscale(cconj(expipi(base + 2.0 * dz * k * tn0)), inv_nn);
-    cm1[tid] = cconj(expipi(base + 2.0 * dz * k * tn1));
-    cr0[tid] = expipi(2.0 * q * (double)d0 / N);
-    cr1[tid] = expipi(2.0 * q * (double)d1 / N);
+    cm0[tid] = cscale(cconj(expipi(-(double)a.lam * dz * k0 * k0 + 2.0 * dz * k0 * tn0)), inv_nn);
+    cm1[tid] = cconj(expipi(-(double)a.lam * dz * k1 * k1 + 2.0 * dz * k1 * tn1));
+    cr0[tid] = expipi(2.0 * q0 * (double)d0 / N);
+    cr1[tid] = expipi(2.0 * q1 * (double)d1 / N);
     const double PI = 3.14159265358979323846;
     const double cs0 = cos((double)th0), cs1 = cos((double)th1);
-    e0[tid] = (float)(PI * a.lam * k * k - 2.0 * PI * k * tn0);
-    e1[tid] = (float)(PI * a.lam * k * k - 2.0 * PI * k * tn1);
-    c0[tid] = (float)(-2.0 * PI * dz * k / (cs0 * cs0));
-    c1[tid] = (float)(-2.0 * PI * dz * k / (cs1 * cs1));
-    f0[tid] = (float)(2.0 * PI * q / ((double)N * NN));
-    f1[tid] = f0[tid];
+    e0[tid] = (float)(PI * a.lam * k0 * k0 - 2.0 * PI * k0 * tn0);
+    e1[tid] = (float)(PI * a.lam * k1 * k1 - 2.0 * PI * k1 * tn1);
+    c0[tid] = (float)(-2.0 * PI * dz * k0 / (cs0 * cs0));
+    c1[tid] = (float)(-2.0 * PI * dz * k1 / (cs1 * cs1));
+    f0[tid] = (float)(2.0 * PI * q0 / ((double)N * NN));
+    f1[tid] = (float)(2.0 * PI * q1 / ((double)N * NN));
   }
   __syncthreads();
 
-  // g_psi = F_ortho^-1[2 dL/dI Psi] = (1/N) unnormalised inverse of 2 dL/dI Psi
-  F::inverse(s, tw, FarGradLoad<N>{a.u + (size_t)b * NN, a.Psi + (size_t)bm * NN, (float)(2.0 * a.scal[0] / N)});
+  // g_psi = F_ortho^-1[2 dL/dI Psi] = (1/N) unnormalised inverse of 2 dL/dI Psi; its column step is
+  // fused with the last slice's transmission below (same step structure as the forward kernel).
+  FarGradLoad<N> farg{a.u + (size_t)b * NN, a.Psi + (size_t)bm * NN, (float)(2.0 * a.scal[0] / N)};
+  F::row_inv(s, tw, farg);
+  F::block_inv(s);
 
   float gdz = 0.f, gt0 = 0.f, gt1 = 0.f, gp0 = 0.f, gp1 = 0.f;
   for (int sl = a.Nz - 1; sl >= 0; --sl) {
@@ -641,18 +704,21 @@ __global__ void __launch_bounds__(T, Launch<N>::MIN_BLOCKS) k_adjoint(AdjArgs a)
     if (sl >= 2 && want_prop) prefetch_block<N>(vh_base + (size_t)(sl - 2) * NN);
     AdjTransLoad<N> trans{a.T + sl * plane + patch, a.gT + sl * plane + patch,
                           want_obj ? ck_base + (size_t)sl * NN : nullptr, a.W};
-    if (sl > 0) {
-      F::forward(s, tw, trans,
-                 AdjPropStore<N>{cm0, cm1, want_prop ? vh_base + (size_t)(sl - 1) * NN : nullptr, e0, e1, c0, c1, gdz,
-                                 gt0, gt1});
-      F::inverse(s, tw);
-    } else if (want_probe || want_pos) {
-      F::template forward<false>(
-          s, tw, trans,
-          ProbeStore<N>{want_probe ? a.gPhat + (size_t)m * NN : nullptr, a.Phat + (size_t)m * NN, cr0, cr1, f0, f1,
-                        want_pos, gp0, gp1});
+    if (sl > 0 || want_probe || want_pos) {
+      F::template col_inv_fwd<true>(s, tw, trans);
+      F::block_fwd(s, tw);
+      if (sl > 0) {
+        AdjPropStore<N> prop{cm0, cm1, want_prop ? vh_base + (size_t)(sl - 1) * NN : nullptr, e0, e1, c0, c1,
+                             gdz, gt0, gt1};
+        F::row_fwd_inv(s, tw, prop);
+        F::block_inv(s);
+      } else {
+        ProbeStore<N> probe{want_probe ? a.gPhat + (size_t)m * NN : nullptr, a.Phat + (size_t)m * NN, cr0, cr1, f0,
+                            f1, want_pos, gp0, gp1};
+        F::template row_fwd<false>(s, probe);
+      }
     } else if (want_obj) {
-      F::elementwise(s, trans);
+      F::template col_inv_fwd<false>(s, tw, trans);
     }
   }
 
@@ -706,7 +772,7 @@ __global__ void __launch_bounds__(T) k_probe_grad(const float2* __restrict__ gPh
   const int m = blockIdx.x, tid = threadIdx.x;
   build_twiddles<N>(tw);
   const float2* G = gPhat + (size_t)m * N * N;
-  for (int e = tid; e < N * N; e += T) s[(e / N) * RS + e % N] = G[e];
+  for (int e = tid; e < N * N; e += T) s[(e % N) * RS + e / N] = G[e];  // e = p1 * N + p0
   __syncthreads();
   F::inverse(s, tw);
   const float sc = 1.0f / (float)(N * N);
@@ -792,13 +858,14 @@ int run_pipeline(const Problem& pb) {
   const bool want_probe = grad && (gm & PTY_GRAD_PROBE);
   const bool want_prop = grad && (gm & (PTY_GRAD_DZ | PTY_GRAD_TILT)) && pb.Nz > 1;
 
+  constexpr int TF = Launch<N>::TF, TA = Launch<N>::TA;
   const size_t fsm = fwd_smem_bytes<N>();
-  const size_t asm_ = adj_smem_bytes<N, T>();
+  const size_t asm_ = adj_smem_bytes<N, TA>();
   const size_t lsm = loss_smem_bytes<N>();
   const size_t psm = sizeof(float2) * ((size_t)N * (N + 1) + N);
   {  // cheap host calls; repeated every pass so that every device a caller uses gets them
-    if (cudaFuncSetAttribute(k_forward<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_adjoint<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_) != cudaSuccess ||
+    if (cudaFuncSetAttribute(k_forward<N, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) != cudaSuccess ||
+        cudaFuncSetAttribute(k_adjoint<N, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_) != cudaSuccess ||
         cudaFuncSetAttribute(k_loss<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm) != cudaSuccess ||
         cudaFuncSetAttribute(k_probe_spectrum<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess ||
         cudaFuncSetAttribute(k_probe_grad<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess) {
@@ -836,7 +903,7 @@ int run_pipeline(const Problem& pb) {
     fa.Psi = grad ? ws.Psi : nullptr;
     fa.Imode = ws.Imode;
     fa.status = ws.status;
-    k_forward<N, T><<<pb.B * pb.M, T, fsm, st>>>(fa);
+    k_forward<N, TF><<<pb.B * pb.M, TF, fsm, st>>>(fa);
     PTY_LAUNCH_CHECK("k_forward", 2);
 
     LossArgs la;
@@ -885,7 +952,7 @@ int run_pipeline(const Problem& pb) {
     aa.gPhat = ws.gPhat;
     aa.spart = ws.spart;
     aa.status = ws.status;
-    k_adjoint<N, T><<<pb.B * pb.M, T, asm_, st>>>(aa);
+    k_adjoint<N, TA><<<pb.B * pb.M, TA, asm_, st>>>(aa);
     PTY_LAUNCH_CHECK("k_adjoint", 5);
   } else if (pb.loss_out) {
     cudaMemsetAsync(pb.loss_out, 0, sizeof(double), st);
