@@ -147,6 +147,30 @@ const char* pty_last_error(void);
 /* Bit mask of the FFT sizes N this build supports (bit k set: N = 2^k). */
 int pty_supported_sizes(void);
 
+/* pty_loss_grad without a caller-supplied workspace, for callers that cannot allocate device memory:
+ * code running inside a host framework that owns every device allocation through its own pool, or
+ * a real-time loop that cannot afford the device-wide synchronisation of cudaMalloc / cudaFree.
+ * There is no counterpart in the paper; the computation is exactly pty_loss_grad's.
+ *  - Scratch is a fixed array of PTY_NOALLOC_SCRATCH_BYTES (32 MiB) inside this library's device
+ *    code.  Every GPU that loads the library holds it until the process exits.  A batch whose
+ *    pty_workspace_size() exceeds it is rejected with PTY_EWORKSPACE before anything is launched.
+ *  - The call allocates nothing.  Its first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ *    capture on the device.
+ *  - All calls share the one array, which keeps the last call's contents (the pass clears what it
+ *    accumulates into).  Calls whose work overlaps on the GPU (other streams, other host threads)
+ *    race on it: serialise them.
+ *  - status: optional device int that receives the call's device status bits (as pty_status would
+ *    report them) once the stream reaches the end of the call; may be NULL.
+ *  Other arguments, layouts and error codes as pty_loss_grad. */
+#define PTY_NOALLOC_SCRATCH_BYTES (32u << 20)
+int pty_loss_grad_noalloc(const pty_geom* geom, int B, const int32_t* idx, const float* amp,
+                          const float* phase, const float* probe, const float* pos,
+                          const float* tilt, const float* dz, const float* I_meas, double* loss,
+                          float* I_model, float* g_amp, float* g_phase, float* g_probe,
+                          float* g_pos, float* g_tilt, float* g_dz, int accumulate, int* status,
+                          void* stream);
+
 /* Diagnostics for throughput measurement (not needed to use the library).
  * pty_launch_count: number of kernels this library has launched in the process so far.
  * pty_profile_enable(1) resets and starts per-kernel timing: every later pipeline call records a CUDA

@@ -33,7 +33,7 @@ PTY_GRAD_ALL = 63
 # Every symbol include/pty.h declares (checked by the CPU test suite).
 EXPORTS = ("pty_workspace_size", "pty_forward", "pty_loss_grad", "pty_adam_update", "pty_step",
            "pty_status", "pty_last_error", "pty_supported_sizes", "pty_launch_count", "pty_profile_enable",
-           "pty_profile_read")
+           "pty_profile_read", "pty_loss_grad_noalloc")
 PROF_STAGES = ("prepare_object", "probe_spectrum", "forward", "loss", "loss_finalize", "adjoint", "object_grad",
                "probe_grad", "scalar_grad")
 
@@ -90,6 +90,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pty_last_error.restype = ctypes.c_char_p
     lib.pty_supported_sizes.argtypes = []
     lib.pty_supported_sizes.restype = I
+    lib.pty_loss_grad_noalloc.argtypes = [G, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, I, P, P]
+    lib.pty_loss_grad_noalloc.restype = I
     lib.pty_launch_count.argtypes = []
     lib.pty_launch_count.restype = ctypes.c_longlong
     lib.pty_profile_enable.argtypes = [I]
@@ -163,3 +165,10 @@ def pty_profile_read() -> tuple[int, dict]:
     if n < 0:
         raise PtyError(PTY_ECUDA, "profile read failed")
     return n, {name: buf[k] for k, name in enumerate(PROF_STAGES)}
+
+
+def pty_loss_grad_noalloc(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss, I_model, g_amp, g_phase,
+                          g_probe, g_pos, g_tilt, g_dz, accumulate, status, stream):
+    _check(load().pty_loss_grad_noalloc(ctypes.byref(geom), B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss,
+                                        I_model, g_amp, g_phase, g_probe, g_pos, g_tilt, g_dz, int(accumulate),
+                                        status, stream))

@@ -350,6 +350,61 @@ const char* pty_last_error(void) { return g_err; }
 
 int pty_supported_sizes(void) { return (1 << 6) | (1 << 7); }
 
+// ---------------------------------------------------------------------------------------------
+// pty_loss_grad_noalloc: the same pass, with its scratch in a fixed device array of this library.
+// ---------------------------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+constexpr size_t kNoallocBytes = (size_t)PTY_NOALLOC_SCRATCH_BYTES;
+// Loaded with the library's device code on every GPU that uses it and held until the process exits.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
+// Device address of g_noalloc_scratch per device ordinal (host code may not use the symbol itself).
+void* g_noalloc_addr[256] = {nullptr};
+}  // namespace
+
+extern "C" {
+
+int pty_loss_grad_noalloc(const pty_geom* geom, int B, const int32_t* idx, const float* amp, const float* phase,
+                          const float* probe, const float* pos, const float* tilt, const float* dz,
+                          const float* I_meas, double* loss, float* I_model, float* g_amp, float* g_phase,
+                          float* g_probe, float* g_pos, float* g_tilt, float* g_dz, int accumulate, int* status,
+                          void* stream) {
+  int rc = validate_geom(geom);
+  if (rc) return rc;
+  REQUIRE(B >= 0, "batch size %d < 0", B);
+  const size_t need = layout_workspace(*geom, B, MODE_GRAD, nullptr, nullptr);
+  if (need > kNoallocBytes) {
+    set_error("pty_loss_grad_noalloc: this batch needs %zu bytes of scratch but the fixed area holds %zu; "
+              "use a smaller batch or pty_loss_grad with a caller-owned workspace", need, kNoallocBytes);
+    return PTY_EWORKSPACE;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    set_error("pty_loss_grad_noalloc: no current CUDA device");
+    return PTY_ECUDA;
+  }
+  if (!g_noalloc_addr[dev]) {  // first call on this device: look up the array's device address
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      set_error("pty_loss_grad_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return PTY_ECUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  void* ws = g_noalloc_addr[dev];
+  rc = pty_loss_grad(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss, I_model, g_amp, g_phase, g_probe,
+                     g_pos, g_tilt, g_dz, accumulate, ws, kNoallocBytes, stream);
+  if (rc == PTY_OK && status) {
+    if (cudaMemcpyAsync(status, ws, sizeof(int), cudaMemcpyDeviceToDevice, (cudaStream_t)stream) != cudaSuccess) {
+      set_error("pty_loss_grad_noalloc: status copy failed: %s", cudaGetErrorString(cudaGetLastError()));
+      return PTY_ECUDA;
+    }
+  }
+  return rc;
+}
+
 long long pty_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
 
 int pty_profile_enable(int on) {
