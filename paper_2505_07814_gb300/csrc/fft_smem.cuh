@@ -345,6 +345,46 @@ struct Fft2 {
     col_inv(s, tw);
   }
 
+  // Apply a hook to every element of the natural-layout array in batches of U elements per thread:
+  // thread t owns column t % N and rows t / N + i * (T / N), so a batch is U rows of one column.  The
+  // hook sees the whole batch at once and can keep U of its global loads in flight.
+  template <int U, class H>
+  __device__ static void pointwise(float2* s, H& h) {
+    constexpr int NE = N * N / T, RPI = T / N;
+    static_assert(NE % U == 0, "batch must divide the elements per thread");
+    const int c = threadIdx.x % N, r0 = threadIdx.x / N;
+#pragma unroll 1
+    for (int i0 = 0; i0 < NE; i0 += U) {
+      float2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = s[(r0 + (i0 + u) * RPI) * RS + c];
+      h.template operator()<U>(r0 + i0 * RPI, RPI, c, 0, v);
+#pragma unroll
+      for (int u = 0; u < U; ++u) s[(r0 + (i0 + u) * RPI) * RS + c] = v[u];
+    }
+    __syncthreads();
+  }
+
+  // The same for the k-space array with lanes owning consecutive rows p0 (thread t: row t % N,
+  // columns t / N + i * (T / N)), so that transposed global k-space buffers (p1 * N + p0) are read
+  // coalesced and shared memory is walked with the odd row stride.
+  template <int U, class H>
+  __device__ static void pointwise_rows(float2* s, H& h) {
+    constexpr int NE = N * N / T, CPI = T / N;
+    static_assert(NE % U == 0, "batch must divide the elements per thread");
+    const int r = threadIdx.x % N, c0 = threadIdx.x / N;
+#pragma unroll 1
+    for (int i0 = 0; i0 < NE; i0 += U) {
+      float2 v[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) v[u] = s[r * RS + c0 + (i0 + u) * CPI];
+      h.template operator()<U>(r, 0, c0 + i0 * CPI, CPI, v);
+#pragma unroll
+      for (int u = 0; u < U; ++u) s[r * RS + c0 + (i0 + u) * CPI] = v[u];
+    }
+    __syncthreads();
+  }
+
   // Apply a hook to every element of the natural-layout array (same task shape as the col step).
   template <class H>
   __device__ static void elementwise(float2* s, H&& h) {

@@ -26,6 +26,18 @@
 #ifndef PTY_TA128
 #define PTY_TA128 512
 #endif
+#ifndef PTY_ADJ_SPLIT_COL
+#define PTY_ADJ_SPLIT_COL 1
+#endif
+#ifndef PTY_ADJ_BATCH
+#define PTY_ADJ_BATCH 8
+#endif
+#ifndef PTY_ADJ_SPLIT_ROW
+#define PTY_ADJ_SPLIT_ROW 1
+#endif
+#ifndef PTY_FWD_SPLIT_COL
+#define PTY_FWD_SPLIT_COL 0
+#endif
 #ifndef PTY_KS
 #define PTY_KS 4
 #endif
@@ -341,7 +353,14 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   for (int sl = 0; sl < a.Nz; ++sl) {
     if (sl + 1 < a.Nz) prefetch_patch<N>(Tpatch + (sl + 1) * plane, a.W);
     TransLoad<N> trans{Tpatch + sl * plane, a.W, a.ckpt ? a.ckpt + ((size_t)bm * a.Nz + sl) * NN : nullptr};
+#if PTY_FWD_SPLIT_COL
+    NoHook none;
+    F::col_inv(s, tw);
+    F::template pointwise<PTY_ADJ_BATCH>(s, trans);
+    F::col_fwd(s, tw, none);
+#else
     F::template col_inv_fwd<true>(s, tw, trans);
+#endif
     F::block_fwd(s, tw);
     if (sl + 1 < a.Nz) {
       PropStore<N> prop{pm0, pm1, a.vhat ? a.vhat + ((size_t)bm * (a.Nz - 1) + sl) * NN : nullptr};
@@ -699,18 +718,34 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   F::block_inv(s);
 
   float gdz = 0.f, gt0 = 0.f, gt1 = 0.f, gp0 = 0.f, gp1 = 0.f;
+  NoHook none;
   for (int sl = a.Nz - 1; sl >= 0; --sl) {
     if (sl >= 1 && want_obj) prefetch_block<N>(ck_base + (size_t)(sl - 1) * NN);
     if (sl >= 2 && want_prop) prefetch_block<N>(vh_base + (size_t)(sl - 2) * NN);
     AdjTransLoad<N> trans{a.T + sl * plane + patch, a.gT + sl * plane + patch,
                           want_obj ? ck_base + (size_t)sl * NN : nullptr, a.W};
     if (sl > 0 || want_probe || want_pos) {
+#if PTY_ADJ_SPLIT_COL
+      // column inverse, then the transmission step as its own pass with deep load batches, then
+      // the column forward: one more shared-memory round trip, but no DFT registers are live
+      // while the checkpoint and transmission loads are in flight
+      F::col_inv(s, tw);
+      F::template pointwise<PTY_ADJ_BATCH>(s, trans);
+      F::col_fwd(s, tw, none);
+#else
       F::template col_inv_fwd<true>(s, tw, trans);
+#endif
       F::block_fwd(s, tw);
       if (sl > 0) {
         AdjPropStore<N> prop{cm0, cm1, want_prop ? vh_base + (size_t)(sl - 1) * NN : nullptr, e0, e1, c0, c1,
                              gdz, gt0, gt1};
+#if PTY_ADJ_SPLIT_ROW
+        F::template row_fwd<true>(s, none);
+        F::template pointwise_rows<PTY_ADJ_BATCH>(s, prop);
+        F::row_inv(s, tw, none);
+#else
         F::row_fwd_inv(s, tw, prop);
+#endif
         F::block_inv(s);
       } else {
         ProbeStore<N> probe{want_probe ? a.gPhat + (size_t)m * NN : nullptr, a.Phat + (size_t)m * NN, cr0, cr1, f0,
