@@ -82,6 +82,12 @@ typedef struct {
   float eps;       /* Poisson stabiliser inside the log (Eq. 6), normally 1e-6 */
   int grad_mask;   /* PTY_GRAD_* bits */
   int global_tilt; /* 0: tilt is [Ntot][2] (local); 1: tilt is [2] shared by every position */
+  int ckpt_stride; /* adjoint memory plan.  0 or 1: the forward keeps the wave entering every slice
+                      (and every propagated spectrum) for the adjoint: B*M*(2 Nz - 1)*N^2*8 bytes.
+                      K > 1: it keeps only the spectrum entering slices K, 2K, ... and the adjoint
+                      re-runs each K-slice segment from there before differentiating it:
+                      B*M*(ceil(Nz/K) - 1 + 2K + 1)*N^2*8 bytes and about one more forward pass of
+                      work.  K >= Nz re-runs the whole forward. */
 } pty_geom;
 
 /* Adam state and hyper-parameters for pty_step / pty_adam (PyTorch's Adam: bias-corrected first and
@@ -121,6 +127,23 @@ int pty_loss_grad(const pty_geom* geom, int B, const int32_t* idx, const float* 
                   const float* dz, const float* I_meas, double* loss, float* I_model,
                   float* g_amp, float* g_phase, float* g_probe, float* g_pos, float* g_tilt,
                   float* g_dz, int accumulate, void* ws, size_t ws_bytes, void* stream);
+
+/* Forward model as pty_forward, keeping in ws what pty_backward needs (checkpoints per
+ * geom->ckpt_stride, far-field waves, transmission, probe spectra).  The parameters and ws must not
+ * change between this call and the matching pty_backward. */
+int pty_forward_save(const pty_geom* geom, int B, const int32_t* idx, const float* amp,
+                     const float* phase, const float* probe, const float* pos, const float* tilt,
+                     const float* dz, float* I_model, void* ws, size_t ws_bytes, void* stream);
+
+/* Adjoint of the forward model of the preceding pty_forward_save on the same ws and arguments: the
+ * gradients of a caller-defined loss whose derivative with respect to the modelled patterns is
+ * dL_dI (float [B][N][N], DC-centred).  Gradient arrays, mask and accumulate as pty_loss_grad.
+ * This is the backward of an autograd function wrapping the forward model. */
+int pty_backward(const pty_geom* geom, int B, const int32_t* idx, const float* amp,
+                 const float* phase, const float* probe, const float* pos, const float* tilt,
+                 const float* dz, const float* dL_dI, float* g_amp, float* g_phase, float* g_probe,
+                 float* g_pos, float* g_tilt, float* g_dz, int accumulate, void* ws, size_t ws_bytes,
+                 void* stream);
 
 /* One Adam step on the parameters in place using the gradients already in g_* (pty_adam state).
  * step is the 1-based Adam step count used for bias correction. */

@@ -33,7 +33,7 @@ PTY_GRAD_ALL = 63
 # Every symbol include/pty.h declares (checked by the CPU test suite).
 EXPORTS = ("pty_workspace_size", "pty_forward", "pty_loss_grad", "pty_adam_update", "pty_step",
            "pty_status", "pty_last_error", "pty_supported_sizes", "pty_launch_count", "pty_profile_enable",
-           "pty_profile_read", "pty_loss_grad_noalloc")
+           "pty_profile_read", "pty_loss_grad_noalloc", "pty_forward_save", "pty_backward")
 PROF_STAGES = ("prepare_object", "probe_spectrum", "forward", "loss", "loss_finalize", "adjoint", "object_grad",
                "probe_grad", "scalar_grad")
 
@@ -42,7 +42,8 @@ class pty_geom(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int), ("M", ctypes.c_int), ("Nz", ctypes.c_int), ("H", ctypes.c_int),
                 ("W", ctypes.c_int), ("Ntot", ctypes.c_int), ("dx", ctypes.c_float),
                 ("lambda_", ctypes.c_float), ("loss", ctypes.c_int), ("p", ctypes.c_float),
-                ("eps", ctypes.c_float), ("grad_mask", ctypes.c_int), ("global_tilt", ctypes.c_int)]
+                ("eps", ctypes.c_float), ("grad_mask", ctypes.c_int), ("global_tilt", ctypes.c_int),
+                ("ckpt_stride", ctypes.c_int)]
 
 
 class pty_adam(ctypes.Structure):
@@ -80,6 +81,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pty_forward.restype = I
     lib.pty_loss_grad.argtypes = [G, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, I, P, SZ, P]
     lib.pty_loss_grad.restype = I
+    lib.pty_forward_save.argtypes = [G, I, P, P, P, P, P, P, P, P, P, SZ, P]
+    lib.pty_forward_save.restype = I
+    lib.pty_backward.argtypes = [G, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, I, P, SZ, P]
+    lib.pty_backward.restype = I
     lib.pty_adam_update.argtypes = [G, P, P, P, P, P, P, P, P, P, P, P, P, A, I, P]
     lib.pty_adam_update.restype = I
     lib.pty_step.argtypes = [G, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, A, I, P, SZ, P]
@@ -124,6 +129,17 @@ def pty_loss_grad(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss, 
     _check(load().pty_loss_grad(ctypes.byref(geom), B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss,
                                 I_model, g_amp, g_phase, g_probe, g_pos, g_tilt, g_dz, int(accumulate), ws,
                                 ws_bytes, stream))
+
+
+def pty_forward_save(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_model, ws, ws_bytes, stream):
+    _check(load().pty_forward_save(ctypes.byref(geom), B, idx, amp, phase, probe, pos, tilt, dz, I_model, ws,
+                                   ws_bytes, stream))
+
+
+def pty_backward(geom, B, idx, amp, phase, probe, pos, tilt, dz, dL_dI, g_amp, g_phase, g_probe, g_pos, g_tilt,
+                 g_dz, accumulate, ws, ws_bytes, stream):
+    _check(load().pty_backward(ctypes.byref(geom), B, idx, amp, phase, probe, pos, tilt, dz, dL_dI, g_amp, g_phase,
+                               g_probe, g_pos, g_tilt, g_dz, int(accumulate), ws, ws_bytes, stream))
 
 
 def pty_adam_update(geom, amp, phase, probe, pos, tilt, dz, g_amp, g_phase, g_probe, g_pos, g_tilt, g_dz,

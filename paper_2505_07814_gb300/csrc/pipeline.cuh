@@ -184,11 +184,15 @@ struct FwdArgs {
   const float *pos, *tilt, *dz;
   const float2* T;
   const float2* Phat;
-  float2* ckpt;
-  float2* vhat;
+  float2* ckpt;     // every slice's entering wave [wave][Nz][N*N], or nullptr
+  float2* vhat;     // every propagated spectrum [wave][Nz-1][N*N], or nullptr
+  float2* anchors;  // recompute mode: spectrum entering slice q*K, [wave][nseg-1][N*N], or nullptr
+  int kstride;      // recompute mode: slices per segment K (anchors at slices K, 2K, ...)
   float2* Psi;
   float* Imode;
   int* status;
+  // segment replay (k_recompute): slices [s0, s1) from the anchor of s0, into per-segment buffers
+  int s0, s1;
 };
 
 template <int N>
@@ -363,7 +367,14 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
 #endif
     F::block_fwd(s, tw);
     if (sl + 1 < a.Nz) {
-      PropStore<N> prop{pm0, pm1, a.vhat ? a.vhat + ((size_t)bm * (a.Nz - 1) + sl) * NN : nullptr};
+      float2* vh = nullptr;
+      if (a.vhat) {
+        vh = a.vhat + ((size_t)bm * (a.Nz - 1) + sl) * NN;
+      } else if (a.anchors && (sl + 1) % a.kstride == 0) {
+        const int nanch = (a.Nz + a.kstride - 1) / a.kstride - 1;
+        vh = a.anchors + ((size_t)bm * nanch + (sl + 1) / a.kstride - 1) * NN;
+      }
+      PropStore<N> prop{pm0, pm1, vh};
       F::row_fwd_inv(s, tw, prop);
       F::block_inv(s);
     } else {
@@ -371,6 +382,117 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
       F::template row_fwd<false>(s, far);
     }
   }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Segment replay for the recompute mode: one CTA per wave re-runs slices [s0, s1) from the stored
+// spectrum entering slice s0 (or from the shifted probe when s0 = 0) and writes the entering waves
+// (slot sl - s0) and propagated spectra (slot j holds the spectrum entering slice s0 + j) that the
+// adjoint of that segment reads.  The spectrum entering slice s is F[psi_in,s] / N^2, exactly what
+// the forward kernel stores as an anchor, so the replay reproduces the forward's values.
+// ---------------------------------------------------------------------------------------------
+// entering spectrum of the segment (k-space), replaces; also copied into segment slot 0
+template <int N>
+struct AnchorLoad {
+  static constexpr bool kReplaces = true;
+  static constexpr int kChunk = PTY_KS;
+  const float2* an;
+  float2* slot0;  // or nullptr
+  template <int K>
+  __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) v[k] = ld_ro(an + (c0 + k * cs) * N + r0 + k * rs);
+    if (slot0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) __stcs(slot0 + (c0 + k * cs) * N + r0 + k * rs, v[k]);
+    }
+  }
+};
+// entering wave of the last slice of a segment (natural layout), stored only
+template <int N>
+struct CkptStore {
+  static constexpr bool kReplaces = false;
+  static constexpr int kChunk = 4;
+  float2* ck;
+  template <int K>
+  __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) __stcs(ck + (r0 + k * rs) * N + c0 + k * cs, v[k]);
+  }
+};
+
+template <int N, int T>
+__global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_recompute(FwdArgs a) {
+  using F = Fft2<N, T>;
+  constexpr int RS = F::RS;
+  constexpr int NN = N * N;
+  extern __shared__ __align__(16) float2 sm[];
+  float2* s = sm;
+  float2* tw = s + N * RS;
+  float2* ra0 = tw + N;
+  float2* ra1 = ra0 + N;
+  float2* pm0 = ra1 + N;
+  float2* pm1 = pm0 + N;
+  const int tid = threadIdx.x;
+  const int bm = blockIdx.x;
+  const int b = bm / a.M, m = bm % a.M;
+  const int j = checked_index(a.idx, b, a.Ntot, a.status);
+  int i0, i1;
+  float d0, d1, th0, th1;
+  patch_corner<N>(a.pos, j, a.H, a.W, &i0, &i1, &d0, &d1, a.status);
+  tilt_of(a.tilt, a.global_tilt, j, &th0, &th1);
+  const float dz = a.dz[0];
+  const size_t plane = (size_t)a.H * a.W;
+  const float2* Tpatch = a.T + (size_t)i0 * a.W + i1;
+  const int K = a.kstride;
+  build_twiddles<N>(tw);
+  if (tid < N) {
+    const int q0 = signed_bin<N>(kbin0<N>(tid)), q1 = signed_bin<N>(kbin1<N>(tid));
+    const float inv_nn = 1.0f / (float)NN;
+    ra0[tid] = cscale(expipi(-2.0 * q0 * (double)d0 / N), inv_nn);
+    ra1[tid] = expipi(-2.0 * q1 * (double)d1 / N);
+    const double k0 = q0 / (N * (double)a.dx), k1 = q1 / (N * (double)a.dx);
+    pm0[tid] = cscale(expipi(-(double)a.lam * dz * k0 * k0 + 2.0 * dz * k0 * tan((double)th0)), inv_nn);
+    pm1[tid] = expipi(-(double)a.lam * dz * k1 * k1 + 2.0 * dz * k1 * tan((double)th1));
+  }
+  __syncthreads();
+  float2* ck_seg = a.ckpt ? a.ckpt + (size_t)bm * K * NN : nullptr;
+  float2* vh_seg = a.vhat ? a.vhat + (size_t)bm * K * NN : nullptr;
+  if (a.s0 == 0) {
+    ShiftLoad<N> shift{a.Phat + (size_t)m * NN, ra0, ra1};
+    F::row_inv(s, tw, shift);
+  } else {
+    const int nanch = (a.Nz + K - 1) / K - 1;
+    AnchorLoad<N> anc{a.anchors + ((size_t)bm * nanch + a.s0 / K - 1) * NN, vh_seg};
+    F::row_inv(s, tw, anc);
+  }
+  F::block_inv(s);
+  for (int sl = a.s0; sl < a.s1; ++sl) {
+    float2* ck = ck_seg ? ck_seg + (size_t)(sl - a.s0) * NN : nullptr;
+    if (sl + 1 < a.s1) {
+      TransLoad<N> trans{Tpatch + sl * plane, a.W, ck};
+      F::template col_inv_fwd<true>(s, tw, trans);
+      F::block_fwd(s, tw);
+      PropStore<N> prop{pm0, pm1, vh_seg ? vh_seg + (size_t)(sl + 1 - a.s0) * NN : nullptr};
+      F::row_fwd_inv(s, tw, prop);
+      F::block_inv(s);
+    } else if (ck) {
+      CkptStore<N> store{ck};
+      F::template col_inv_fwd<false>(s, tw, store);
+    }
+  }
+}
+
+// External dL/dI (DC-centred [B][N][N]) into the adjoint's k-space layout; the normaliser becomes 1.
+template <int N>
+__global__ void k_dldi_to_kspace(const float* __restrict__ dldi, float* __restrict__ u, double* scal, int B) {
+  const size_t n = (size_t)B * N * N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / (N * N)), q = (int)(i % (N * N));
+    const int k0 = (q / N + N / 2) & (N - 1), k1 = (q % N + N / 2) & (N - 1);
+    u[(size_t)b * N * N + kpos1<N>(k1) * N + kpos0<N>(k0)] = dldi[i];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) scal[0] = 1.0;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -523,15 +645,21 @@ struct AdjArgs {
   const float *pos, *tilt, *dz;
   const float2* T;
   const float2* Phat;
+  // entering wave of slice s at ckpt[wave][s - ck_first], spectrum entering slice s at
+  // vhat[wave][s - 1 - vh_first]; ck_per_wave / vh_per_wave slots per wave
   const float2* ckpt;
   const float2* vhat;
+  int ck_first, ck_per_wave, vh_first, vh_per_wave;
   const float2* Psi;
   const float* u;
   const double* scal;
   float2* gT;
   float2* gPhat;
-  double* spart;
+  double* spart;  // [wave][5], accumulated over the segments of one pass
   int* status;
+  // slices [s0, s1) of this launch; the adjoint wave is carried between launches in gstate
+  int s0, s1;
+  float2* gstate;
 };
 
 template <int N, int T>
@@ -684,10 +812,12 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   const bool want_prop = (a.grad_mask & (PTY_GRAD_DZ | PTY_GRAD_TILT)) != 0 && a.vhat != nullptr;
   const size_t plane = (size_t)a.H * a.W;
   const size_t patch = (size_t)i0 * a.W + i1;
-  const float2* ck_base = a.ckpt + (size_t)bm * a.Nz * NN;
-  const float2* vh_base = want_prop ? a.vhat + (size_t)bm * (a.Nz - 1) * NN : nullptr;
-  if (want_obj) prefetch_block<N>(ck_base + (size_t)(a.Nz - 1) * NN);
-  if (want_prop && a.Nz > 1) prefetch_block<N>(vh_base + (size_t)(a.Nz - 2) * NN);
+  // slot pointers relative to slice numbers (ck_base + s * NN is slice s's entering wave, vh_base +
+  // (s - 1) * NN the spectrum entering slice s)
+  const float2* ck_base = want_obj ? a.ckpt + ((ptrdiff_t)bm * a.ck_per_wave - a.ck_first) * NN : nullptr;
+  const float2* vh_base = want_prop ? a.vhat + ((ptrdiff_t)bm * a.vh_per_wave - a.vh_first) * NN : nullptr;
+  if (want_obj) prefetch_block<N>(ck_base + (size_t)(a.s1 - 1) * NN);
+  if (want_prop && a.s1 - 1 > a.s0 - 1 && a.s1 >= 2) prefetch_block<N>(vh_base + (size_t)(a.s1 - 2) * NN);
 
   build_twiddles<N>(tw);
   if (tid < N) {
@@ -711,20 +841,26 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   }
   __syncthreads();
 
-  // g_psi = F_ortho^-1[2 dL/dI Psi] = (1/N) unnormalised inverse of 2 dL/dI Psi; its column step is
-  // fused with the last slice's transmission below (same step structure as the forward kernel).
-  FarGradLoad<N> farg{a.u + (size_t)b * NN, a.Psi + (size_t)bm * NN, (float)(2.0 * a.scal[0] / N)};
-  F::row_inv(s, tw, farg);
-  F::block_inv(s);
+  if (a.s1 == a.Nz) {
+    // g_psi = F_ortho^-1[2 dL/dI Psi] = (1/N) unnormalised inverse of 2 dL/dI Psi; its column step
+    // is fused with the last slice's transmission below (same step structure as the forward kernel).
+    FarGradLoad<N> farg{a.u + (size_t)b * NN, a.Psi + (size_t)bm * NN, (float)(2.0 * a.scal[0] / N)};
+    F::row_inv(s, tw, farg);
+    F::block_inv(s);
+  } else {
+    const float2* g = a.gstate + (size_t)bm * NN;
+    for (int e = tid; e < NN; e += T) s[(e / N) * RS + e % N] = ld_ro(g + e);
+    __syncthreads();
+  }
 
   float gdz = 0.f, gt0 = 0.f, gt1 = 0.f, gp0 = 0.f, gp1 = 0.f;
   NoHook none;
-  for (int sl = a.Nz - 1; sl >= 0; --sl) {
-    if (sl >= 1 && want_obj) prefetch_block<N>(ck_base + (size_t)(sl - 1) * NN);
-    if (sl >= 2 && want_prop) prefetch_block<N>(vh_base + (size_t)(sl - 2) * NN);
+  for (int sl = a.s1 - 1; sl >= a.s0; --sl) {
+    if (sl - 1 >= a.s0 && want_obj) prefetch_block<N>(ck_base + (size_t)(sl - 1) * NN);
+    if (sl - 2 >= a.s0 - 1 && sl >= 2 && want_prop) prefetch_block<N>(vh_base + (size_t)(sl - 2) * NN);
     AdjTransLoad<N> trans{a.T + sl * plane + patch, a.gT + sl * plane + patch,
                           want_obj ? ck_base + (size_t)sl * NN : nullptr, a.W};
-    if (sl > 0 || want_probe || want_pos) {
+    if (sl > 0 || want_probe || want_pos) {  // (sl > 0: propagate back into slice sl - 1)
 #if PTY_ADJ_SPLIT_COL
       // column inverse, then the transmission step as its own pass with deep load batches, then
       // the column forward: one more shared-memory round trip, but no DFT registers are live
@@ -771,7 +907,11 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   if (tid < 5) {
     double acc = 0.0;
     for (int i = 0; i < T / 32; ++i) acc += red[5 * i + tid];
-    a.spart[(size_t)bm * 5 + tid] = acc;
+    a.spart[(size_t)bm * 5 + tid] += acc;
+  }
+  if (a.s0 > 0) {  // hand the adjoint wave to the launch of the previous segment
+    float2* g = a.gstate + (size_t)bm * NN;
+    for (int e = tid; e < NN; e += T) g[e] = s[(e / N) * RS + e % N];
   }
 }
 
@@ -875,49 +1015,50 @@ static __global__ void k_scalar_grad(const double* __restrict__ spart, const int
       set_error("%s launch failed: %s", what, cudaGetErrorString(e_));    \
       return PTY_ECUDA;                                                   \
     }                                                                     \
-    if (stage >= 0) {                                                     \
-      note_launch();                                                      \
-      prof_mark(stage, st);                                               \
-    }                                                                     \
+    note_launch();                                                        \
+    if (stage >= 0) prof_mark(stage, st);                                 \
   } while (0)
 
+// Phases of one pass.  Forward (with or without what the adjoint needs), loss, adjoint + gradients.
 template <int N>
-int run_pipeline(const Problem& pb) {
-  constexpr int T = Launch<N>::T;
-  constexpr int NN = N * N;
-  const Workspace& ws = pb.ws;
-  cudaStream_t st = pb.stream;
-  const bool grad = pb.mode == MODE_GRAD;
-  const int gm = pb.grad_mask;
-  const bool want_obj = grad && (gm & (PTY_GRAD_AMP | PTY_GRAD_PHASE));
-  const bool want_probe = grad && (gm & PTY_GRAD_PROBE);
-  const bool want_prop = grad && (gm & (PTY_GRAD_DZ | PTY_GRAD_TILT)) && pb.Nz > 1;
+struct Pass {
+  static constexpr int T = Launch<N>::T, TF = Launch<N>::TF, TA = Launch<N>::TA;
+  static constexpr int NN = N * N;
+  const Problem& pb;
+  const Workspace& ws;
+  cudaStream_t st;
+  bool save, want_obj, want_probe, want_prop;
+  int K, nseg;
 
-  constexpr int TF = Launch<N>::TF, TA = Launch<N>::TA;
-  const size_t fsm = fwd_smem_bytes<N>();
-  const size_t asm_ = adj_smem_bytes<N, TA>();
-  const size_t lsm = loss_smem_bytes<N>();
-  const size_t psm = sizeof(float2) * ((size_t)N * (N + 1) + N);
-  {  // cheap host calls; repeated every pass so that every device a caller uses gets them
-    if (cudaFuncSetAttribute(k_forward<N, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_adjoint<N, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_) != cudaSuccess ||
-        cudaFuncSetAttribute(k_loss<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lsm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_probe_spectrum<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess ||
-        cudaFuncSetAttribute(k_probe_grad<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psm) != cudaSuccess) {
+  explicit Pass(const Problem& p) : pb(p), ws(p.ws), st(p.stream) {
+    save = pb.mode != MODE_FORWARD;
+    const int gm = pb.grad_mask;
+    want_obj = save && (gm & (PTY_GRAD_AMP | PTY_GRAD_PHASE));
+    want_probe = save && (gm & PTY_GRAD_PROBE);
+    want_prop = save && (gm & (PTY_GRAD_DZ | PTY_GRAD_TILT)) && pb.Nz > 1;
+    K = pb.kstride;
+    nseg = (pb.Nz + K - 1) / K;
+  }
+
+  int set_attributes() {
+    if (cudaFuncSetAttribute(k_forward<N, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem_bytes<N>()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_recompute<N, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem_bytes<N>()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_adjoint<N, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem_bytes<N, TA>()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_loss<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)loss_smem_bytes<N>()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_probe_spectrum<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)probe_smem()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_probe_grad<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)probe_smem()) != cudaSuccess) {
       set_error("cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
       return PTY_ECUDA;
     }
+    return PTY_OK;
+  }
+  static size_t probe_smem() { return sizeof(float2) * ((size_t)N * (N + 1) + N); }
+  unsigned object_blocks() const {
+    const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
+    return (unsigned)((nobj + 255) / 256 < 152 * 16 ? (nobj + 255) / 256 : 152 * 16);
   }
 
-  const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
-  prof_begin(st);
-  k_prepare_object<<<(unsigned)((nobj + 255) / 256 < 152 * 16 ? (nobj + 255) / 256 : 152 * 16), 256, 0, st>>>(
-      pb.amp, pb.phase, ws.T, want_obj ? ws.gT : nullptr, nobj);
-  PTY_LAUNCH_CHECK("k_prepare_object", 0);
-  k_probe_spectrum<N, T><<<pb.M, T, psm, st>>>(pb.probe, ws.Phat, want_probe ? ws.gPhat : nullptr);
-  PTY_LAUNCH_CHECK("k_probe_spectrum", 1);
-
-  if (pb.B > 0) {
+  FwdArgs fwd_args() const {
     FwdArgs fa;
     fa.M = pb.M;
     fa.Nz = pb.Nz;
@@ -933,14 +1074,39 @@ int run_pipeline(const Problem& pb) {
     fa.dz = pb.dz;
     fa.T = ws.T;
     fa.Phat = ws.Phat;
-    fa.ckpt = want_obj ? ws.ckpt : nullptr;
-    fa.vhat = want_prop ? ws.vhat : nullptr;
-    fa.Psi = grad ? ws.Psi : nullptr;
+    fa.ckpt = nullptr;
+    fa.vhat = nullptr;
+    fa.anchors = nullptr;
+    fa.kstride = K;
+    fa.Psi = save ? ws.Psi : nullptr;
     fa.Imode = ws.Imode;
     fa.status = ws.status;
-    k_forward<N, TF><<<pb.B * pb.M, TF, fsm, st>>>(fa);
-    PTY_LAUNCH_CHECK("k_forward", 2);
+    fa.s0 = 0;
+    fa.s1 = pb.Nz;
+    return fa;
+  }
 
+  // T, probe spectra, the forward kernel (storing checkpoints when `save`) and the mode sum (and
+  // the loss when I_meas is given).
+  int forward(const float* I_meas) {
+    const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
+    prof_begin(st);
+    k_prepare_object<<<object_blocks(), 256, 0, st>>>(pb.amp, pb.phase, ws.T, nullptr, nobj);
+    PTY_LAUNCH_CHECK("k_prepare_object", 0);
+    k_probe_spectrum<N, T><<<pb.M, T, probe_smem(), st>>>(pb.probe, ws.Phat, nullptr);
+    PTY_LAUNCH_CHECK("k_probe_spectrum", 1);
+    if (pb.B == 0) return PTY_OK;
+    FwdArgs fa = fwd_args();
+    if (save) {
+      if (K == 1) {
+        fa.ckpt = want_obj ? ws.ckpt : nullptr;
+        fa.vhat = want_prop ? ws.vhat : nullptr;
+      } else if (nseg > 1) {
+        fa.anchors = ws.anchors;
+      }
+    }
+    k_forward<N, TF><<<pb.B * pb.M, TF, fwd_smem_bytes<N>(), st>>>(fa);
+    PTY_LAUNCH_CHECK("k_forward", 2);
     LossArgs la;
     la.M = pb.M;
     la.Ntot = pb.Ntot;
@@ -950,18 +1116,30 @@ int run_pipeline(const Problem& pb) {
     la.eps = pb.eps;
     la.idx = pb.idx;
     la.Imode = ws.Imode;
-    la.I_meas = grad ? pb.I_meas : nullptr;
+    la.I_meas = I_meas;
     la.I_model = pb.I_model;
-    la.u = grad ? ws.u : nullptr;
-    la.lpart = grad ? ws.lpart : nullptr;
-    k_loss<N, T><<<pb.B, T, lsm, st>>>(la);
+    la.u = I_meas ? ws.u : nullptr;
+    la.lpart = I_meas ? ws.lpart : nullptr;
+    k_loss<N, T><<<pb.B, T, loss_smem_bytes<N>(), st>>>(la);
     PTY_LAUNCH_CHECK("k_loss", 3);
+    if (I_meas) {
+      k_loss_finalize<<<1, 256, 0, st>>>(ws.lpart, pb.B, pb.loss, (double)pb.B * NN, ws.scal, pb.loss_out, ws.status);
+      PTY_LAUNCH_CHECK("k_loss_finalize", 4);
+    }
+    return PTY_OK;
   }
-  if (!grad) return PTY_OK;
 
-  if (pb.B > 0) {
-    k_loss_finalize<<<1, 256, 0, st>>>(ws.lpart, pb.B, pb.loss, (double)pb.B * NN, ws.scal, pb.loss_out, ws.status);
-    PTY_LAUNCH_CHECK("k_loss_finalize", 4);
+  // dL/dI from the caller instead of the loss (the adjoint of the forward model alone).
+  int external_dldi(const float* dldi) {
+    if (pb.B == 0) return PTY_OK;
+    const size_t n = (size_t)pb.B * NN;
+    const unsigned blocks = (unsigned)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
+    k_dldi_to_kspace<N><<<blocks, 256, 0, st>>>(dldi, ws.u, ws.scal, pb.B);
+    PTY_LAUNCH_CHECK("k_dldi_to_kspace", -1);
+    return PTY_OK;
+  }
+
+  AdjArgs adj_args() const {
     AdjArgs aa;
     aa.M = pb.M;
     aa.Nz = pb.Nz;
@@ -969,7 +1147,7 @@ int run_pipeline(const Problem& pb) {
     aa.W = pb.W;
     aa.Ntot = pb.Ntot;
     aa.global_tilt = pb.global_tilt;
-    aa.grad_mask = gm;
+    aa.grad_mask = pb.grad_mask;
     aa.dx = pb.dx;
     aa.lam = pb.lam;
     aa.idx = pb.idx;
@@ -978,8 +1156,6 @@ int run_pipeline(const Problem& pb) {
     aa.dz = pb.dz;
     aa.T = ws.T;
     aa.Phat = ws.Phat;
-    aa.ckpt = ws.ckpt;
-    aa.vhat = want_prop ? ws.vhat : nullptr;
     aa.Psi = ws.Psi;
     aa.u = ws.u;
     aa.scal = ws.scal;
@@ -987,40 +1163,119 @@ int run_pipeline(const Problem& pb) {
     aa.gPhat = ws.gPhat;
     aa.spart = ws.spart;
     aa.status = ws.status;
-    k_adjoint<N, TA><<<pb.B * pb.M, TA, asm_, st>>>(aa);
-    PTY_LAUNCH_CHECK("k_adjoint", 5);
-  } else if (pb.loss_out) {
-    cudaMemsetAsync(pb.loss_out, 0, sizeof(double), st);
+    aa.gstate = ws.gstate;
+    return aa;
   }
 
-  if (want_obj) {
-    const unsigned blocks = (unsigned)((nobj + 255) / 256 < 152 * 16 ? (nobj + 255) / 256 : 152 * 16);
-    k_object_grad<<<blocks, 256, 0, st>>>(pb.amp, pb.phase, ws.gT, (gm & PTY_GRAD_AMP) ? pb.g_amp : nullptr,
-                                          (gm & PTY_GRAD_PHASE) ? pb.g_phase : nullptr, pb.accumulate, nobj);
-    PTY_LAUNCH_CHECK("k_object_grad", 6);
-  }
-  if (want_probe) {
-    k_probe_grad<N, T><<<pb.M, T, psm, st>>>(ws.gPhat, pb.g_probe, pb.accumulate);
-    PTY_LAUNCH_CHECK("k_probe_grad", 7);
-  }
-  const bool want_scalar = gm & (PTY_GRAD_POS | PTY_GRAD_TILT | PTY_GRAD_DZ);
-  if (want_scalar) {
-    if (!pb.accumulate) {
-      if ((gm & PTY_GRAD_POS) && pb.g_pos) cudaMemsetAsync(pb.g_pos, 0, sizeof(float) * 2 * pb.Ntot, st);
-      if ((gm & PTY_GRAD_TILT) && pb.g_tilt && !pb.global_tilt)
-        cudaMemsetAsync(pb.g_tilt, 0, sizeof(float) * 2 * pb.Ntot, st);
-    }
+  // Adjoint over all slices (segment by segment in the recompute mode) and the gradient finalisers.
+  int adjoint() {
+    const int gm = pb.grad_mask;
+    const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
+    if (want_obj && cudaMemsetAsync(ws.gT, 0, sizeof(float2) * nobj, st) != cudaSuccess) return memset_failed();
+    if (want_probe && cudaMemsetAsync(ws.gPhat, 0, sizeof(float2) * pb.M * NN, st) != cudaSuccess) return memset_failed();
     if (pb.B > 0) {
-      k_scalar_grad<<<1, 256, 0, st>>>(ws.spart, pb.idx, pb.B, pb.M, pb.Ntot, pb.global_tilt, gm, pb.g_pos, pb.g_tilt,
-                                       pb.g_dz, pb.accumulate);
-      PTY_LAUNCH_CHECK("k_scalar_grad", 8);
-    } else if (!pb.accumulate) {
-      if ((gm & PTY_GRAD_DZ) && pb.g_dz) cudaMemsetAsync(pb.g_dz, 0, sizeof(float), st);
-      if ((gm & PTY_GRAD_TILT) && pb.g_tilt && pb.global_tilt) cudaMemsetAsync(pb.g_tilt, 0, 2 * sizeof(float), st);
+      if (cudaMemsetAsync(ws.spart, 0, sizeof(double) * 5 * pb.B * pb.M, st) != cudaSuccess) return memset_failed();
+      AdjArgs aa = adj_args();
+      if (K == 1) {
+        aa.ckpt = ws.ckpt;
+        aa.vhat = want_prop ? ws.vhat : nullptr;
+        aa.ck_first = 0;
+        aa.ck_per_wave = pb.Nz;
+        aa.vh_first = 0;
+        aa.vh_per_wave = pb.Nz - 1;
+        aa.s0 = 0;
+        aa.s1 = pb.Nz;
+        k_adjoint<N, TA><<<pb.B * pb.M, TA, adj_smem_bytes<N, TA>(), st>>>(aa);
+        PTY_LAUNCH_CHECK("k_adjoint", 5);
+      } else {
+        for (int q = nseg - 1; q >= 0; --q) {
+          const int s0 = q * K, s1 = (s0 + K < pb.Nz) ? s0 + K : pb.Nz;
+          if (want_obj || want_prop) {
+            FwdArgs fa = fwd_args();
+            fa.Psi = nullptr;
+            fa.anchors = ws.anchors;
+            fa.ckpt = want_obj ? ws.ckpt : nullptr;
+            fa.vhat = want_prop ? ws.vhat : nullptr;
+            fa.s0 = s0;
+            fa.s1 = s1;
+            k_recompute<N, TF><<<pb.B * pb.M, TF, fwd_smem_bytes<N>(), st>>>(fa);
+            PTY_LAUNCH_CHECK("k_recompute", -1);
+          }
+          aa.ckpt = ws.ckpt;
+          aa.vhat = want_prop ? ws.vhat : nullptr;
+          aa.ck_first = s0;
+          aa.ck_per_wave = K;
+          aa.vh_first = s0 - 1;
+          aa.vh_per_wave = K;
+          aa.s0 = s0;
+          aa.s1 = s1;
+          k_adjoint<N, TA><<<pb.B * pb.M, TA, adj_smem_bytes<N, TA>(), st>>>(aa);
+          PTY_LAUNCH_CHECK("k_adjoint", q == 0 ? 5 : -1);
+        }
+      }
     }
+    if (want_obj) {
+      k_object_grad<<<object_blocks(), 256, 0, st>>>(pb.amp, pb.phase, ws.gT, (gm & PTY_GRAD_AMP) ? pb.g_amp : nullptr,
+                                                     (gm & PTY_GRAD_PHASE) ? pb.g_phase : nullptr, pb.accumulate, nobj);
+      PTY_LAUNCH_CHECK("k_object_grad", 6);
+    }
+    if (want_probe) {
+      k_probe_grad<N, T><<<pb.M, T, probe_smem(), st>>>(ws.gPhat, pb.g_probe, pb.accumulate);
+      PTY_LAUNCH_CHECK("k_probe_grad", 7);
+    }
+    if (gm & (PTY_GRAD_POS | PTY_GRAD_TILT | PTY_GRAD_DZ)) {
+      if (!pb.accumulate) {
+        if ((gm & PTY_GRAD_POS) && pb.g_pos &&
+            cudaMemsetAsync(pb.g_pos, 0, sizeof(float) * 2 * pb.Ntot, st) != cudaSuccess)
+          return memset_failed();
+        if ((gm & PTY_GRAD_TILT) && pb.g_tilt && !pb.global_tilt &&
+            cudaMemsetAsync(pb.g_tilt, 0, sizeof(float) * 2 * pb.Ntot, st) != cudaSuccess)
+          return memset_failed();
+      }
+      if (pb.B > 0) {
+        k_scalar_grad<<<1, 256, 0, st>>>(ws.spart, pb.idx, pb.B, pb.M, pb.Ntot, pb.global_tilt, gm, pb.g_pos,
+                                         pb.g_tilt, pb.g_dz, pb.accumulate);
+        PTY_LAUNCH_CHECK("k_scalar_grad", 8);
+      } else if (!pb.accumulate) {
+        if ((gm & PTY_GRAD_DZ) && pb.g_dz && cudaMemsetAsync(pb.g_dz, 0, sizeof(float), st) != cudaSuccess)
+          return memset_failed();
+        if ((gm & PTY_GRAD_TILT) && pb.g_tilt && pb.global_tilt &&
+            cudaMemsetAsync(pb.g_tilt, 0, 2 * sizeof(float), st) != cudaSuccess)
+          return memset_failed();
+      }
+    }
+    return PTY_OK;
   }
-  PTY_LAUNCH_CHECK("pipeline", -1);
-  return PTY_OK;
+  int memset_failed() {
+    set_error("cudaMemsetAsync failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return PTY_ECUDA;
+  }
+};
+
+template <int N>
+int run_pipeline(const Problem& pb) {
+  Pass<N> ps(pb);
+  int rc = ps.set_attributes();
+  if (rc) return rc;
+  switch (pb.mode) {
+    case MODE_FORWARD:
+    case MODE_FORWARD_SAVE:
+      return ps.forward(nullptr);
+    case MODE_GRAD:
+      rc = ps.forward(pb.I_meas);
+      if (rc) return rc;
+      if (pb.B == 0 && pb.loss_out) {
+        if (cudaMemsetAsync(pb.loss_out, 0, sizeof(double), pb.stream) != cudaSuccess) return ps.memset_failed();
+      }
+      return ps.adjoint();
+    case MODE_BACKWARD:
+      rc = ps.external_dldi(pb.dldi);
+      if (rc) return rc;
+      return ps.adjoint();
+    default:
+      set_error("unknown pass mode %d", pb.mode);
+      return PTY_EINVAL;
+  }
 }
 
 }  // namespace pty

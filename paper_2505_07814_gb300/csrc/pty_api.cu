@@ -49,13 +49,25 @@ void prof_mark(int stage, cudaStream_t st) {
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Slices per recompute segment actually used: 1 (checkpoint every slice) unless the caller asked for
+// a stride and some gradient needs the forward waves.
+int effective_stride(const pty_geom& g) {
+  const bool needs = (g.grad_mask & (PTY_GRAD_AMP | PTY_GRAD_PHASE)) ||
+                     ((g.grad_mask & (PTY_GRAD_DZ | PTY_GRAD_TILT)) && g.Nz > 1);
+  if (!needs || g.ckpt_stride <= 1) return 1;
+  return g.ckpt_stride < g.Nz ? g.ckpt_stride : g.Nz;
+}
+
 size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspace* out) {
   const size_t NN = (size_t)g.N * g.N;
   const size_t nobj = (size_t)g.Nz * g.H * g.W;
-  const bool grad = mode == MODE_GRAD;
+  const size_t waves = (size_t)B * g.M;
+  const bool grad = mode != MODE_FORWARD;
   const bool want_obj = grad && (g.grad_mask & (PTY_GRAD_AMP | PTY_GRAD_PHASE));
   const bool want_prop = grad && (g.grad_mask & (PTY_GRAD_DZ | PTY_GRAD_TILT)) && g.Nz > 1;
   const bool want_probe = grad && (g.grad_mask & PTY_GRAD_PROBE);
+  const int K = effective_stride(g);
+  const int nseg = (g.Nz + K - 1) / K;
   size_t off = 0;
   Workspace w;
   memset(&w, 0, sizeof(w));
@@ -68,16 +80,23 @@ size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspac
   w.scal = (double*)take(sizeof(double) * 4);
   w.T = (float2*)take(sizeof(float2) * nobj);
   w.Phat = (float2*)take(sizeof(float2) * g.M * NN);
-  w.Imode = (float*)take(sizeof(float) * (size_t)B * g.M * NN);
+  w.Imode = (float*)take(sizeof(float) * waves * NN);
   if (grad) {
-    if (want_obj) w.ckpt = (float2*)take(sizeof(float2) * (size_t)B * g.M * g.Nz * NN);
-    if (want_prop) w.vhat = (float2*)take(sizeof(float2) * (size_t)B * g.M * (g.Nz - 1) * NN);
-    w.Psi = (float2*)take(sizeof(float2) * (size_t)B * g.M * NN);
+    if (K == 1) {
+      if (want_obj) w.ckpt = (float2*)take(sizeof(float2) * waves * g.Nz * NN);
+      if (want_prop) w.vhat = (float2*)take(sizeof(float2) * waves * (g.Nz - 1) * NN);
+    } else {
+      if (nseg > 1) w.anchors = (float2*)take(sizeof(float2) * waves * (nseg - 1) * NN);
+      if (want_obj) w.ckpt = (float2*)take(sizeof(float2) * waves * K * NN);
+      if (want_prop) w.vhat = (float2*)take(sizeof(float2) * waves * K * NN);
+      w.gstate = (float2*)take(sizeof(float2) * waves * NN);
+    }
+    w.Psi = (float2*)take(sizeof(float2) * waves * NN);
     w.u = (float*)take(sizeof(float) * (size_t)B * NN);
     w.lpart = (double*)take(sizeof(double) * 2 * (size_t)(B > 0 ? B : 1));
     if (want_obj) w.gT = (float2*)take(sizeof(float2) * nobj);
     if (want_probe) w.gPhat = (float2*)take(sizeof(float2) * g.M * NN);
-    w.spart = (double*)take(sizeof(double) * 5 * (size_t)(B > 0 ? B : 1) * g.M);
+    w.spart = (double*)take(sizeof(double) * 5 * (waves > 0 ? waves : 1));
   }
   if (out) *out = w;
   return off;
@@ -109,6 +128,10 @@ static int validate_geom(const pty_geom* g) {
   }
   if ((g->grad_mask & ~PTY_GRAD_ALL) != 0) {
     set_error("unknown bits in grad_mask 0x%x", g->grad_mask);
+    return PTY_EINVAL;
+  }
+  if (g->ckpt_stride < 0) {
+    set_error("ckpt_stride %d < 0", g->ckpt_stride);
     return PTY_EINVAL;
   }
   if ((double)g->Nz * g->H * g->W > 4.0e9) {
@@ -163,6 +186,7 @@ static int prepare(const pty_geom* g, int B, int mode, const int32_t* idx, const
   pb->grad_mask = g->grad_mask;
   pb->global_tilt = g->global_tilt ? 1 : 0;
   pb->mode = mode;
+  pb->kstride = effective_stride(*g);
   pb->idx = idx;
   pb->amp = amp;
   pb->phase = phase;
@@ -261,6 +285,43 @@ int pty_loss_grad(const pty_geom* geom, int B, const int32_t* idx, const float* 
   pb.I_meas = I_meas;
   pb.loss_out = loss;
   pb.I_model = I_model;
+  pb.g_amp = g_amp;
+  pb.g_phase = g_phase;
+  pb.g_probe = reinterpret_cast<float2*>(g_probe);
+  pb.g_pos = g_pos;
+  pb.g_tilt = g_tilt;
+  pb.g_dz = g_dz;
+  pb.accumulate = accumulate ? 1 : 0;
+  return dispatch(pb);
+}
+
+int pty_forward_save(const pty_geom* geom, int B, const int32_t* idx, const float* amp, const float* phase,
+                     const float* probe, const float* pos, const float* tilt, const float* dz, float* I_model,
+                     void* ws, size_t ws_bytes, void* stream) {
+  Problem pb;
+  int rc = prepare(geom, B, MODE_FORWARD_SAVE, idx, amp, phase, probe, pos, tilt, dz, ws, ws_bytes, stream, &pb);
+  if (rc) return rc;
+  REQUIRE(B == 0 || I_model, "I_model is NULL");
+  pb.I_model = I_model;
+  return dispatch(pb);
+}
+
+int pty_backward(const pty_geom* geom, int B, const int32_t* idx, const float* amp, const float* phase,
+                 const float* probe, const float* pos, const float* tilt, const float* dz, const float* dL_dI,
+                 float* g_amp, float* g_phase, float* g_probe, float* g_pos, float* g_tilt, float* g_dz,
+                 int accumulate, void* ws, size_t ws_bytes, void* stream) {
+  Problem pb;
+  int rc = prepare(geom, B, MODE_BACKWARD, idx, amp, phase, probe, pos, tilt, dz, ws, ws_bytes, stream, &pb);
+  if (rc) return rc;
+  const int gm = geom->grad_mask;
+  REQUIRE(B == 0 || dL_dI, "dL_dI is NULL");
+  REQUIRE(!(gm & PTY_GRAD_AMP) || g_amp, "g_amp is NULL but PTY_GRAD_AMP is requested");
+  REQUIRE(!(gm & PTY_GRAD_PHASE) || g_phase, "g_phase is NULL but PTY_GRAD_PHASE is requested");
+  REQUIRE(!(gm & PTY_GRAD_PROBE) || (g_probe && aligned(g_probe, 8)), "g_probe is NULL or misaligned");
+  REQUIRE(!(gm & PTY_GRAD_POS) || g_pos, "g_pos is NULL but PTY_GRAD_POS is requested");
+  REQUIRE(!(gm & PTY_GRAD_TILT) || g_tilt, "g_tilt is NULL but PTY_GRAD_TILT is requested");
+  REQUIRE(!(gm & PTY_GRAD_DZ) || g_dz, "g_dz is NULL but PTY_GRAD_DZ is requested");
+  pb.dldi = dL_dI;
   pb.g_amp = g_amp;
   pb.g_phase = g_phase;
   pb.g_probe = reinterpret_cast<float2*>(g_probe);

@@ -14,8 +14,12 @@ struct Workspace {
   int* status;     // [1]   device status bits
   float2* T;       // [Nz][H][W]      transmission amp * exp(i phase)
   float2* Phat;    // [M][N*N]        probe spectra F[P_m] (k-space layout)
-  float2* ckpt;    // [B][M][Nz][N*N] wave entering each slice (natural layout)
-  float2* vhat;    // [B][M][Nz-1][N*N] propagated spectra / N^2 (k-space), for dz/tilt gradients
+  float2* ckpt;     // [B][M][Nz][N*N] wave entering each slice (natural layout); recompute mode:
+                    // [B][M][K][N*N], the current segment's entering waves
+  float2* vhat;     // [B][M][Nz-1][N*N] propagated spectra / N^2 (k-space), for dz/tilt gradients;
+                    // recompute mode: [B][M][K][N*N], slot j = spectrum entering slice s0 + j
+  float2* anchors;  // recompute mode: [B][M][nseg-1][N*N] spectrum entering slices K, 2K, ...
+  float2* gstate;   // recompute mode: [B][M][N*N] adjoint wave handed between segments
   float2* Psi;     // [B][M][N*N]     far-field waves (k-space)
   float* Imode;    // [B][M][N*N]     per-mode far-field intensity (k-space)
   float* u;        // [B][N*N]        dL/dI before the batch normaliser (k-space)
@@ -26,7 +30,10 @@ struct Workspace {
   double* spart;   // [B][M][5]       per-wave {pos0, pos1, tilt0, tilt1, dz} gradient partials
 };
 
-enum Mode { MODE_FORWARD = 0, MODE_GRAD = 1 };
+// MODE_FORWARD: patterns only.  MODE_FORWARD_SAVE: patterns, keeping in the workspace what a later
+// MODE_BACKWARD needs.  MODE_GRAD: loss and gradients in one pass.  MODE_BACKWARD: gradients for a
+// caller-supplied dL/dI, after a MODE_FORWARD_SAVE pass on the same workspace.
+enum Mode { MODE_FORWARD = 0, MODE_GRAD = 1, MODE_FORWARD_SAVE = 2, MODE_BACKWARD = 3 };
 
 struct Problem {
   int N, M, Nz, H, W, Ntot, B;
@@ -34,10 +41,12 @@ struct Problem {
   int loss;
   float p, eps;
   int grad_mask, global_tilt, accumulate, mode;
+  int kstride;  // slices per recompute segment (1: every slice's checkpoint is stored)
   const int32_t* idx;
   const float *amp, *phase, *pos, *tilt, *dz;
   const float2* probe;
   const float* I_meas;
+  const float* dldi;  // MODE_BACKWARD: dL/dI [B][N][N], DC-centred
   double* loss_out;
   float* I_model;
   float *g_amp, *g_phase, *g_pos, *g_tilt, *g_dz;
@@ -45,6 +54,9 @@ struct Problem {
   Workspace ws;
   cudaStream_t stream;
 };
+
+// Slices per recompute segment a pass will use (see pty_geom.ckpt_stride).
+int effective_stride(const pty_geom& g);
 
 // Byte offsets of the workspace pieces; returns the total size.  base may be NULL (size query).
 size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspace* out);

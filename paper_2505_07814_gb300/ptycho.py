@@ -31,6 +31,7 @@ class Geometry:
     eps: float = 1e-6
     grads: tuple = ("amp", "phase", "probe", "pos", "tilt", "dz")
     global_tilt: bool = False
+    ckpt_stride: int = 1  # 1: checkpoint every slice; K > 1: re-run K-slice segments in the adjoint
 
     @property
     def grad_mask(self) -> int:
@@ -41,7 +42,16 @@ class Geometry:
 
     def c(self) -> _lib.pty_geom:
         return _lib.pty_geom(self.N, self.M, self.Nz, self.H, self.W, self.Ntot, self.dx, self.lam,
-                             LOSS[self.loss], self.p, self.eps, self.grad_mask, int(self.global_tilt))
+                             LOSS[self.loss], self.p, self.eps, self.grad_mask, int(self.global_tilt),
+                             int(self.ckpt_stride))
+
+    def checkpoint_bytes(self, B: int) -> int:
+        """Bytes the adjoint's forward record takes for a batch of B positions (see ckpt_stride)."""
+        wave = 8 * self.N * self.N * B * self.M
+        if self.ckpt_stride <= 1:
+            return wave * (2 * self.Nz - 1)
+        K = min(self.ckpt_stride, self.Nz)
+        return wave * ((self.Nz + K - 1) // K - 1 + 2 * K + 1)
 
 
 @dataclasses.dataclass
@@ -94,6 +104,8 @@ class Ptycho:
         self.ws_bytes = _lib.pty_workspace_size(self.cg, max_batch)
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=self.device)
         self.loss = torch.zeros(1, dtype=torch.float64, device=self.device)
+        self._generation = 0  # bumped by every forward_save (one saved forward per workspace)
+        self._saved = None
 
     def _stream(self):
         return torch.cuda.current_stream(self.device).cuda_stream
@@ -141,6 +153,31 @@ class Ptycho:
                            self.ws.data_ptr(), self.ws_bytes, self._stream())
         return self.loss, grads
 
+    def forward_save(self, params: Params, idx, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Modelled patterns, keeping in the workspace what `backward` needs (pty_forward_save)."""
+        idx = self._idx(idx)
+        B, N = idx.numel(), self.geom.N
+        if out is None:
+            out = torch.empty((B, N, N), dtype=torch.float32, device=self.device)
+        self._generation += 1
+        _lib.pty_forward_save(self.cg, B, _ptr(idx), *self._param_ptrs(params),
+                              _ptr(out, torch.float32, B * N * N, "I_model"), self.ws.data_ptr(), self.ws_bytes,
+                              self._stream())
+        self._saved = (idx, self._generation)
+        return out
+
+    def backward(self, params: Params, idx, dL_dI: torch.Tensor, grads: Params | None = None,
+                 accumulate: bool = False) -> Params:
+        """Gradients for dL/dI [B,N,N] (DC-centred) through the forward of the last `forward_save`."""
+        idx = self._idx(idx)
+        B, N = idx.numel(), self.geom.N
+        if grads is None:
+            grads = params.zeros_like()
+        _lib.pty_backward(self.cg, B, _ptr(idx), *self._param_ptrs(params),
+                          _ptr(dL_dI.contiguous(), torch.float32, B * N * N, "dL_dI"), *self._param_ptrs(grads),
+                          int(accumulate), self.ws.data_ptr(), self.ws_bytes, self._stream())
+        return grads
+
     def status(self) -> int:
         """Device status bits of the last call (synchronises the current stream)."""
         return _lib.pty_status(self.ws.data_ptr(), self._stream())
@@ -177,3 +214,37 @@ def step(pt: Ptycho, params: Params, grads: Params, adam: Adam, idx, I_meas: tor
                   _ptr(I_meas, torch.float32, g.Ntot * g.N * g.N, "I_meas"), pt.loss.data_ptr(),
                   *pt._param_ptrs(grads), adam.c(), adam.t, pt.ws.data_ptr(), pt.ws_bytes, pt._stream())
     return pt.loss
+
+
+class _ForwardModel(torch.autograd.Function):
+    """I = f(amp, phase, probe, pos, tilt, dz) for one batch, differentiated by the library's adjoint."""
+
+    @staticmethod
+    def forward(ctx, pt, idx, amp, phase, probe, pos, tilt, dz):
+        params = Params(amp.detach(), phase.detach(), probe.detach(), pos.detach(), tilt.detach(), dz.detach())
+        I = pt.forward_save(params, idx)
+        ctx.pt, ctx.idx, ctx.gen = pt, idx, pt._generation
+        ctx.params = params
+        return I
+
+    @staticmethod
+    def backward(ctx, gI):
+        pt = ctx.pt
+        if pt._generation != ctx.gen:
+            raise RuntimeError("another forward ran on this Ptycho workspace before backward; one forward "
+                               "per workspace may be differentiated at a time")
+        g = pt.backward(ctx.params, ctx.idx, gI.to(torch.float32))
+        want = set(pt.geom.grads)
+        out = [g.amp, g.phase, g.probe, g.pos, g.tilt, g.dz]
+        out = [t if n in want else None for n, t in zip(("amp", "phase", "probe", "pos", "tilt", "dz"), out)]
+        return (None, None, *out)
+
+
+def forward_model(pt: Ptycho, params: Params, idx) -> torch.Tensor:
+    """Differentiable modelled patterns [B,N,N] (DC-centred) for scan positions idx.
+
+    The backward pass runs the library's hand-written adjoint (pty_backward) with the checkpoint /
+    recompute plan of pt.geom.ckpt_stride; gradients flow to every tensor in `params` named in
+    pt.geom.grads.  One forward per Ptycho workspace may be differentiated at a time."""
+    return _ForwardModel.apply(pt, pt._idx(idx), params.amp, params.phase, params.probe, params.pos,
+                               params.tilt, params.dz)

@@ -42,7 +42,7 @@ def test_missing_library_fails_loudly(tmp_path):
 
 def _geom(**kw):
     g = dict(N=64, M=2, Nz=3, H=100, W=110, Ntot=12, dx=0.1, lambda_=0.0251, loss=0, p=0.0, eps=1e-6,
-             grad_mask=63, global_tilt=0)
+             grad_mask=63, global_tilt=0, ckpt_stride=0)
     g.update(kw)
     return _lib.pty_geom(**g)
 
@@ -53,7 +53,7 @@ def test_workspace_size_and_validation(lib):
     assert n >= 8 * 2 * 3 * 64 * 64 * 8
     assert lib.pty_workspace_size(ctypes.byref(_geom(grad_mask=_lib.PTY_GRAD_PROBE)), 8) < n
     for bad in (dict(N=32), dict(N=96), dict(M=0), dict(Nz=0), dict(H=63), dict(loss=7), dict(dx=0.0),
-                dict(grad_mask=64)):
+                dict(grad_mask=64), dict(ckpt_stride=-1)):
         assert lib.pty_workspace_size(ctypes.byref(_geom(**bad)), 8) == 0, bad
         assert lib.pty_last_error()
     assert lib.pty_supported_sizes() == (1 << 6) | (1 << 7)
@@ -91,3 +91,17 @@ def test_bad_arguments_rejected_before_launch(lib):
     rc = lib.pty_adam_update(ctypes.byref(g), fake, fake, fake, fake, fake, fake, fake, fake, fake, fake, fake, fake,
                              ctypes.byref(a), 0, null)
     assert rc == _lib.PTY_EINVAL
+
+
+def test_recompute_plan_shrinks_the_workspace(lib):
+    """ckpt_stride K > 1 keeps one spectrum per K slices plus one K-slice segment instead of every slice."""
+    full = lib.pty_workspace_size(ctypes.byref(_geom(Nz=12, ckpt_stride=1)), 16)
+    k3 = lib.pty_workspace_size(ctypes.byref(_geom(Nz=12, ckpt_stride=3)), 16)
+    k12 = lib.pty_workspace_size(ctypes.byref(_geom(Nz=12, ckpt_stride=12)), 16)
+    wave = 16 * 2 * 64 * 64 * 8
+    assert full - k3 >= wave * ((2 * 12 - 1) - (12 // 3 - 1 + 2 * 3 + 1)) - (1 << 16)
+    assert k3 < full and k3 < k12  # K = Nz replays everything but needs Nz-slot segment buffers
+    # without object, dz or tilt gradients nothing is recorded, whatever the stride
+    g = _geom(Nz=12, ckpt_stride=3, grad_mask=_lib.PTY_GRAD_PROBE | _lib.PTY_GRAD_POS)
+    g1 = _geom(Nz=12, ckpt_stride=1, grad_mask=_lib.PTY_GRAD_PROBE | _lib.PTY_GRAD_POS)
+    assert lib.pty_workspace_size(ctypes.byref(g), 16) == lib.pty_workspace_size(ctypes.byref(g1), 16)
