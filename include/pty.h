@@ -67,7 +67,8 @@ enum {
   PTY_GRAD_ALL = 63
 };
 
-/* Problem geometry.  N is the probe window, detector and FFT size: 64 or 128. */
+/* Problem geometry.  N is the probe window, detector and FFT size: 64, 128 or 256 (N = 256 runs
+ * each wave on a four-CTA thread-block cluster). */
 typedef struct {
   int N;           /* probe / detector pixels per side */
   int M;           /* incoherent probe modes, >= 1 (Eq. 2) */

@@ -96,21 +96,33 @@ __device__ __forceinline__ void dft(float2* x) {
 }
 
 // Position of frequency bin k along axis 0 / axis 1 of the k-space layout, and the inverse maps.
+// N <= 128: axis 0 split k = k1 + A k2 at position 4 k1 + k2, axis 1 split k = k1 + 4 k2 at A k1 + k2.
+// N = 256 (four-CTA cluster, fft_cluster.cuh): axis 0 position 64 q + 4 j1 + j2 holds bin
+// q + 4 j1 + 64 j2; axis 1 position 16 k1 + k2 holds bin k1 + 16 k2.
 template <int N>
 __host__ __device__ constexpr int kpos0(int k) {
-  return 4 * (k % (N / 4)) + k / (N / 4);
+  if constexpr (N == 256) return 64 * (k % 4) + 4 * ((k / 4) % 16) + k / 64;
+  else return 4 * (k % (N / 4)) + k / (N / 4);
 }
 template <int N>
 __host__ __device__ constexpr int kbin0(int p) {
-  return p / 4 + (N / 4) * (p % 4);
+  if constexpr (N == 256) return p / 64 + 4 * ((p % 64) / 4) + 64 * (p % 4);
+  else return p / 4 + (N / 4) * (p % 4);
 }
 template <int N>
 __host__ __device__ constexpr int kpos1(int k) {
-  return (N / 4) * (k % 4) + k / 4;
+  if constexpr (N == 256) return 16 * (k % 16) + k / 16;
+  else return (N / 4) * (k % 4) + k / 4;
 }
 template <int N>
 __host__ __device__ constexpr int kbin1(int p) {
-  return p / (N / 4) + 4 * (p % (N / 4));
+  if constexpr (N == 256) return p / 16 + 16 * (p % 16);
+  else return p / (N / 4) + 4 * (p % (N / 4));
+}
+// Index of k-space element (p0, p1) in global k-space buffers (stored transposed).
+template <int N>
+__host__ __device__ constexpr int kidx(int p0, int p1) {
+  return p1 * N + p0;
 }
 
 // Element hooks fused into the FFT steps.  A hook sees K elements of one task in registers: element
@@ -130,6 +142,8 @@ template <int N, int T>
 struct Fft2 {
   static constexpr int A = N / 4, RS = N + 1;
   static_assert(A == 16 || A == 32, "N = 64 or 128");
+  static constexpr int C = 1, ROWS = N;  // CTAs per wave, rows of the wave held by this CTA
+  __device__ static int rank() { return 0; }
   static constexpr int NCOL = 4 * N / T;    // col-step tasks per thread: (c, n2)
   static constexpr int NBLK = A * A / T;    // block-step tasks per thread: (k1, n2)
   static constexpr int NROW = 4 * N / T;    // row-step tasks per thread: (r, k1)
@@ -239,7 +253,7 @@ struct Fft2 {
     }
     __syncthreads();
   }
-  __device__ static void block_inv(float2* s) {
+  __device__ static void block_inv(float2* s, const float2*) {
 #pragma unroll
     for (int i = 0; i < NBLK; ++i) {
       const int t = threadIdx.x + i * T;
@@ -341,7 +355,7 @@ struct Fft2 {
   template <class LH = NoHook>
   __device__ static void inverse(float2* s, const float2* tw, LH&& load = LH()) {
     row_inv(s, tw, load);
-    block_inv(s);
+    block_inv(s, tw);
     col_inv(s, tw);
   }
 
@@ -383,6 +397,12 @@ struct Fft2 {
       for (int u = 0; u < U; ++u) s[r * RS + c0 + (i0 + u) * CPI] = v[u];
     }
     __syncthreads();
+  }
+
+  // k-space pointwise pass (lanes on consecutive rows, matching the transposed global buffers)
+  template <int U, class H>
+  __device__ static void pointwise_k(float2* s, H& h) {
+    pointwise_rows<U>(s, h);
   }
 
   // Apply a hook to every element of the natural-layout array (same task shape as the col step).

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include "fft_cluster.cuh"
 #include "fft_smem.cuh"
 #include "pty_internal.h"
 
@@ -79,6 +80,17 @@ template <>
 struct Launch<128> {
   static constexpr int T = 512, TF = PTY_TF128, TA = PTY_TA128, MINB_F = 1, MINB_A = 1;
 };
+// N = 256: every wave kernel runs as four-CTA clusters (fft_cluster.cuh), 512 threads per CTA.
+template <>
+struct Launch<256> {
+  static constexpr int T = 512, TF = 512, TA = 512, MINB_F = 1, MINB_A = 1;
+};
+
+// Rows of a wave one CTA holds in shared memory (a quarter of the wave at N = 256).
+template <int N>
+__host__ __device__ constexpr int wave_rows() {
+  return N == 256 ? 64 : N;
+}
 
 // exp(i pi x); x is reduced modulo 2 in double precision before the float sincospi.
 __device__ __forceinline__ float2 expipi(double x) {
@@ -156,21 +168,22 @@ template <int N, int T>
 __global__ void __launch_bounds__(T) k_probe_spectrum(const float2* __restrict__ probe, float2* __restrict__ Phat,
                                                       float2* __restrict__ gPhat) {
   using F = Fft2<N, T>;
-  constexpr int RS = F::RS;
+  constexpr int RS = F::RS, R = F::ROWS;
   extern __shared__ __align__(16) float2 sm[];
   float2* s = sm;
-  float2* tw = s + N * RS;
-  const int m = blockIdx.x, tid = threadIdx.x;
+  float2* tw = s + R * RS;
+  const int m = blockIdx.x / F::C, q = F::rank(), tid = threadIdx.x;
   build_twiddles<N>(tw);
-  const float2* P = probe + (size_t)m * N * N;
-  for (int e = tid; e < N * N; e += T) s[(e / N) * RS + e % N] = P[e];
+  const float2* P = probe + (size_t)m * N * N + (size_t)q * R * N;  // this CTA's rows of mode m
+  for (int e = tid; e < R * N; e += T) s[(e / N) * RS + e % N] = P[e];
   __syncthreads();
   F::forward(s, tw);
   float2* out = Phat + (size_t)m * N * N;
   float2* g = gPhat ? gPhat + (size_t)m * N * N : nullptr;
-  for (int e = tid; e < N * N; e += T) {  // e = p1 * N + p0
-    out[e] = s[(e % N) * RS + e / N];
-    if (g) g[e] = make_float2(0.f, 0.f);
+  for (int e = tid; e < R * N; e += T) {  // local k-space row e % R, column e / R
+    const int k = kidx<N>(q * R + e % R, e / R);
+    out[k] = s[(e % R) * RS + e / R];
+    if (g) g[k] = make_float2(0.f, 0.f);
   }
 }
 
@@ -197,7 +210,7 @@ struct FwdArgs {
 
 template <int N>
 __host__ __device__ constexpr size_t fwd_smem_bytes() {
-  return sizeof(float2) * ((size_t)N * (N + 1) + 5 * N);
+  return sizeof(float2) * ((size_t)wave_rows<N>() * (N + 1) + 5 * N);
 }
 
 // Loads of data written by earlier kernels and read-only here (checkpoints, spectra, transmission):
@@ -245,7 +258,7 @@ struct ShiftLoad {
   __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     float2 p[K];
 #pragma unroll
-    for (int k = 0; k < K; ++k) p[k] = ld_ro(Ph + (c0 + k * cs) * N + r0 + k * rs);
+    for (int k = 0; k < K; ++k) p[k] = ld_ro(Ph + kidx<N>(r0 + k * rs, c0 + k * cs));
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = cmul(cmul(p[k], ra0[r0 + k * rs]), ra1[c0 + k * cs]);
   }
@@ -284,7 +297,7 @@ struct PropStore {
     for (int k = 0; k < K; ++k) {
       const int r = r0 + k * rs, c = c0 + k * cs;
       v[k] = cmul(cmul(v[k], m0[r]), m1[c]);
-      if (vh) __stcs(vh + c * N + r, v[k]);
+      if (vh) __stcs(vh + kidx<N>(r, c), v[k]);
     }
   }
 };
@@ -300,7 +313,7 @@ struct FarStore {
     const float inv_n = 1.0f / (float)N;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int e = (c0 + k * cs) * N + r0 + k * rs;
+      const int e = kidx<N>(r0 + k * rs, c0 + k * cs);
       const float2 x = cscale(v[k], inv_n);
       if (Psi) __stcs(Psi + e, x);
       Im[e] = fmaf(x.x, x.x, x.y * x.y);
@@ -315,13 +328,13 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   constexpr int NN = N * N;
   extern __shared__ __align__(16) float2 sm[];
   float2* s = sm;
-  float2* tw = s + N * RS;
+  float2* tw = s + F::ROWS * RS;
   float2* ra0 = tw + N;   // shift ramp along axis 0, carries 1/N^2 of the inverse DFT
   float2* ra1 = ra0 + N;  // shift ramp along axis 1
   float2* pm0 = ra1 + N;  // propagator factor along axis 0, carries 1/N^2
   float2* pm1 = pm0 + N;  // propagator factor along axis 1
   const int tid = threadIdx.x;
-  const int bm = blockIdx.x;
+  const int bm = blockIdx.x / F::C;  // wave (position, mode); a cluster of F::C CTAs per wave
   const int b = bm / a.M, m = bm % a.M;
   const int j = checked_index(a.idx, b, a.Ntot, a.status);
   int i0, i1;
@@ -353,7 +366,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   // (forward end, M, inverse start), block step.
   ShiftLoad<N> shift{a.Phat + (size_t)m * NN, ra0, ra1};
   F::row_inv(s, tw, shift);
-  F::block_inv(s);
+  F::block_inv(s, tw);
   for (int sl = 0; sl < a.Nz; ++sl) {
     if (sl + 1 < a.Nz) prefetch_patch<N>(Tpatch + (sl + 1) * plane, a.W);
     TransLoad<N> trans{Tpatch + sl * plane, a.W, a.ckpt ? a.ckpt + ((size_t)bm * a.Nz + sl) * NN : nullptr};
@@ -376,7 +389,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
       }
       PropStore<N> prop{pm0, pm1, vh};
       F::row_fwd_inv(s, tw, prop);
-      F::block_inv(s);
+      F::block_inv(s, tw);
     } else {
       FarStore<N> far{a.Psi ? a.Psi + (size_t)bm * NN : nullptr, a.Imode + (size_t)bm * NN};
       F::template row_fwd<false>(s, far);
@@ -401,10 +414,10 @@ struct AnchorLoad {
   template <int K>
   __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = ld_ro(an + (c0 + k * cs) * N + r0 + k * rs);
+    for (int k = 0; k < K; ++k) v[k] = ld_ro(an + kidx<N>(r0 + k * rs, c0 + k * cs));
     if (slot0) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) __stcs(slot0 + (c0 + k * cs) * N + r0 + k * rs, v[k]);
+      for (int k = 0; k < K; ++k) __stcs(slot0 + kidx<N>(r0 + k * rs, c0 + k * cs), v[k]);
     }
   }
 };
@@ -428,13 +441,13 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_recompute(FwdArgs a) {
   constexpr int NN = N * N;
   extern __shared__ __align__(16) float2 sm[];
   float2* s = sm;
-  float2* tw = s + N * RS;
+  float2* tw = s + F::ROWS * RS;
   float2* ra0 = tw + N;
   float2* ra1 = ra0 + N;
   float2* pm0 = ra1 + N;
   float2* pm1 = pm0 + N;
   const int tid = threadIdx.x;
-  const int bm = blockIdx.x;
+  const int bm = blockIdx.x / F::C;  // wave (position, mode); a cluster of F::C CTAs per wave
   const int b = bm / a.M, m = bm % a.M;
   const int j = checked_index(a.idx, b, a.Ntot, a.status);
   int i0, i1;
@@ -466,7 +479,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_recompute(FwdArgs a) {
     AnchorLoad<N> anc{a.anchors + ((size_t)bm * nanch + a.s0 / K - 1) * NN, vh_seg};
     F::row_inv(s, tw, anc);
   }
-  F::block_inv(s);
+  F::block_inv(s, tw);
   for (int sl = a.s0; sl < a.s1; ++sl) {
     float2* ck = ck_seg ? ck_seg + (size_t)(sl - a.s0) * NN : nullptr;
     if (sl + 1 < a.s1) {
@@ -475,7 +488,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_recompute(FwdArgs a) {
       F::block_fwd(s, tw);
       PropStore<N> prop{pm0, pm1, vh_seg ? vh_seg + (size_t)(sl + 1 - a.s0) * NN : nullptr};
       F::row_fwd_inv(s, tw, prop);
-      F::block_inv(s);
+      F::block_inv(s, tw);
     } else if (ck) {
       CkptStore<N> store{ck};
       F::template col_inv_fwd<false>(s, tw, store);
@@ -539,6 +552,34 @@ __device__ __forceinline__ void block_sum2(double& x, double& y, double* red) {
   }
 }
 
+// Eq. 5 / 6 at one detector pixel: the summand of the loss (term), the pattern term of its
+// normaliser (Dp = I_meas^p) and dL/dI up to the batch-wide normaliser (u).
+__device__ __forceinline__ void loss_pixel(float I, float d, float p, float eps, int loss, float* term, float* Dp,
+                                           float* u) {
+  float Ip, dpow;
+  if (p == 1.0f) {
+    Ip = I;
+    *Dp = d;
+    dpow = 1.0f;
+  } else if (p == 0.5f) {
+    Ip = sqrtf(fmaxf(I, 0.f));
+    *Dp = sqrtf(fmaxf(d, 0.f));
+    dpow = I > 0.f ? 0.5f / Ip : 0.f;
+  } else {
+    Ip = powf(fmaxf(I, 0.f), p);
+    *Dp = powf(fmaxf(d, 0.f), p);
+    dpow = I > 0.f ? p * powf(I, p - 1.0f) : 0.f;
+  }
+  if (loss == PTY_LOSS_POISSON) {
+    *term = *Dp * logf(Ip + eps) - Ip;
+    *u = -(*Dp / (Ip + eps) - 1.0f) * dpow;
+  } else {
+    const float df = Ip - *Dp;
+    *term = df * df;
+    *u = df * dpow;
+  }
+}
+
 template <int N, int T>
 __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
   constexpr int RS = N + 1;
@@ -564,29 +605,8 @@ __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
     if (a.I_model) a.I_model[(size_t)b * NN + q] = I;
     if (Id) {
       const float d = Id[q];
-      float Ip, Dp, dpow;
-      if (p == 1.0f) {
-        Ip = I;
-        Dp = d;
-        dpow = 1.0f;
-      } else if (p == 0.5f) {
-        Ip = sqrtf(fmaxf(I, 0.f));
-        Dp = sqrtf(fmaxf(d, 0.f));
-        dpow = I > 0.f ? 0.5f / Ip : 0.f;
-      } else {
-        Ip = powf(fmaxf(I, 0.f), p);
-        Dp = powf(fmaxf(d, 0.f), p);
-        dpow = I > 0.f ? p * powf(I, p - 1.0f) : 0.f;
-      }
-      float term, u;
-      if (a.loss == PTY_LOSS_POISSON) {
-        term = Dp * logf(Ip + a.eps) - Ip;
-        u = -(Dp / (Ip + a.eps) - 1.0f) * dpow;
-      } else {
-        const float df = Ip - Dp;
-        term = df * df;
-        u = df * dpow;
-      }
+      float term, u, Dp;
+      loss_pixel(I, d, p, a.eps, a.loss, &term, &Dp, &u);
       sd += Dp;
       st += term;
       L[l] = u;
@@ -595,6 +615,41 @@ __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
   __syncthreads();
   if (a.u) {
     for (int e = tid; e < NN; e += T) a.u[(size_t)b * NN + e] = L[(e / N) * RS + e % N];
+  }
+  if (a.lpart) {
+    double x = sd, y = st;
+    block_sum2<T>(x, y, red);
+    if (tid == 0) {
+      a.lpart[2 * b] = x;
+      a.lpart[2 * b + 1] = y;
+    }
+  }
+}
+
+// The same without shared-memory staging (the N = 256 staging area would not fit): walks the
+// pattern in k-space order (coalesced mode sum and dL/dI), gathering the measured pattern and
+// scattering the modelled one in detector order.
+template <int N, int T>
+__global__ void __launch_bounds__(T) k_loss_gather(LossArgs a) {
+  constexpr int NN = N * N;
+  __shared__ double red[2 * (T / 32)];
+  const int b = blockIdx.x, tid = threadIdx.x;
+  const float* Im = a.Imode + (size_t)b * a.M * NN;
+  const float* Id = a.I_meas ? a.I_meas + (size_t)checked_index(a.idx, b, a.Ntot, a.status) * NN : nullptr;
+  float sd = 0.f, st = 0.f;
+  for (int e = tid; e < NN; e += T) {  // e = p1 * N + p0
+    float I = 0.f;
+    for (int m = 0; m < a.M; ++m) I += Im[(size_t)m * NN + e];
+    const int k0 = kbin0<N>(e % N), k1 = kbin1<N>(e / N);
+    const int q = ((k0 + N / 2) & (N - 1)) * N + ((k1 + N / 2) & (N - 1));
+    if (a.I_model) a.I_model[(size_t)b * NN + q] = I;
+    if (Id) {
+      float term, u, Dp;
+      loss_pixel(I, Id[q], a.p, a.eps, a.loss, &term, &Dp, &u);
+      sd += Dp;
+      st += term;
+      a.u[(size_t)b * NN + e] = u;
+    }
   }
   if (a.lpart) {
     double x = sd, y = st;
@@ -664,7 +719,8 @@ struct AdjArgs {
 
 template <int N, int T>
 __host__ __device__ constexpr size_t adj_smem_bytes() {
-  return sizeof(float2) * ((size_t)N * (N + 1) + 5 * N) + sizeof(float) * 6 * N + sizeof(double) * 5 * (T / 32);
+  return sizeof(float2) * ((size_t)wave_rows<N>() * (N + 1) + 5 * N) + sizeof(float) * 6 * N +
+         sizeof(double) * 5 * (T / 32);
 }
 
 // ---- adjoint hooks ----
@@ -682,7 +738,7 @@ struct FarGradLoad {
     float w[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      const int e = (c0 + k * cs) * N + r0 + k * rs;
+      const int e = kidx<N>(r0 + k * rs, c0 + k * cs);
       p[k] = ld_ro(Psi + e);
       w[k] = ld_ro(u + e);
     }
@@ -730,7 +786,7 @@ struct AdjPropStore {
     if (vh) {
       float2 x[K];
 #pragma unroll
-      for (int k = 0; k < K; ++k) x[k] = ld_ro(vh + (c0 + k * cs) * N + r0 + k * rs);
+      for (int k = 0; k < K; ++k) x[k] = ld_ro(vh + kidx<N>(r0 + k * rs, c0 + k * cs));
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int r = r0 + k * rs, c = c0 + k * cs;
@@ -761,13 +817,13 @@ struct ProbeStore {
     float2 ph[K];
     if (pos) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) ph[k] = ld_ro(Ph + (c0 + k * cs) * N + r0 + k * rs);
+      for (int k = 0; k < K; ++k) ph[k] = ld_ro(Ph + kidx<N>(r0 + k * rs, c0 + k * cs));
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int r = r0 + k * rs, c = c0 + k * cs;
       const float2 cr = cmul(cr0[r], cr1[c]);  // conj(R)
-      if (gP) atomicAdd(gP + c * N + r, cmul(cr, v[k]));
+      if (gP) atomicAdd(gP + kidx<N>(r, c), cmul(cr, v[k]));
       if (pos) {
         const float2 PR = cmulc(cr, ph[k]);  // R P^
         const float w = v[k].x * PR.y - v[k].y * PR.x;
@@ -785,7 +841,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   constexpr int NN = N * N;
   extern __shared__ __align__(16) float2 sm[];
   float2* s = sm;
-  float2* tw = s + N * RS;
+  float2* tw = s + F::ROWS * RS;
   float2* cm0 = tw + N;   // conj propagator, axis 0, carries 1/N^2
   float2* cm1 = cm0 + N;  // conj propagator, axis 1
   float2* cr0 = cm1 + N;  // conj shift ramp, axis 0
@@ -798,7 +854,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   float* f1 = f0 + N;
   double* red = reinterpret_cast<double*>(f1 + N);
   const int tid = threadIdx.x, lane = tid & 31;
-  const int bm = blockIdx.x;
+  const int bm = blockIdx.x / F::C;  // wave (position, mode); a cluster of F::C CTAs per wave
   const int b = bm / a.M, m = bm % a.M;
   const int j = checked_index(a.idx, b, a.Ntot, a.status);
   int i0, i1;
@@ -846,10 +902,10 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
     // is fused with the last slice's transmission below (same step structure as the forward kernel).
     FarGradLoad<N> farg{a.u + (size_t)b * NN, a.Psi + (size_t)bm * NN, (float)(2.0 * a.scal[0] / N)};
     F::row_inv(s, tw, farg);
-    F::block_inv(s);
+    F::block_inv(s, tw);
   } else {
-    const float2* g = a.gstate + (size_t)bm * NN;
-    for (int e = tid; e < NN; e += T) s[(e / N) * RS + e % N] = ld_ro(g + e);
+    const float2* g = a.gstate + (size_t)bm * NN + (size_t)F::rank() * F::ROWS * N;
+    for (int e = tid; e < F::ROWS * N; e += T) s[(e / N) * RS + e % N] = ld_ro(g + e);
     __syncthreads();
   }
 
@@ -877,12 +933,12 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
                              gdz, gt0, gt1};
 #if PTY_ADJ_SPLIT_ROW
         F::template row_fwd<true>(s, none);
-        F::template pointwise_rows<PTY_ADJ_BATCH>(s, prop);
+        F::template pointwise_k<PTY_ADJ_BATCH>(s, prop);
         F::row_inv(s, tw, none);
 #else
         F::row_fwd_inv(s, tw, prop);
 #endif
-        F::block_inv(s);
+        F::block_inv(s, tw);
       } else {
         ProbeStore<N> probe{want_probe ? a.gPhat + (size_t)m * NN : nullptr, a.Phat + (size_t)m * NN, cr0, cr1, f0,
                             f1, want_pos, gp0, gp1};
@@ -907,11 +963,15 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   if (tid < 5) {
     double acc = 0.0;
     for (int i = 0; i < T / 32; ++i) acc += red[5 * i + tid];
-    a.spart[(size_t)bm * 5 + tid] += acc;
+    if constexpr (F::C == 1) {
+      a.spart[(size_t)bm * 5 + tid] += acc;
+    } else {  // the CTAs of a cluster each hold part of the wave
+      atomicAdd(a.spart + (size_t)bm * 5 + tid, acc);
+    }
   }
   if (a.s0 > 0) {  // hand the adjoint wave to the launch of the previous segment
-    float2* g = a.gstate + (size_t)bm * NN;
-    for (int e = tid; e < NN; e += T) g[e] = s[(e / N) * RS + e % N];
+    float2* g = a.gstate + (size_t)bm * NN + (size_t)F::rank() * F::ROWS * N;
+    for (int e = tid; e < F::ROWS * N; e += T) g[e] = s[(e / N) * RS + e % N];
   }
 }
 
@@ -943,16 +1003,17 @@ __global__ void __launch_bounds__(T) k_probe_grad(const float2* __restrict__ gPh
   constexpr int RS = F::RS;
   extern __shared__ __align__(16) float2 sm[];
   float2* s = sm;
-  float2* tw = s + N * RS;
-  const int m = blockIdx.x, tid = threadIdx.x;
+  float2* tw = s + F::ROWS * RS;
+  const int m = blockIdx.x / F::C, q = F::rank(), tid = threadIdx.x;
+  constexpr int R = F::ROWS;
   build_twiddles<N>(tw);
   const float2* G = gPhat + (size_t)m * N * N;
-  for (int e = tid; e < N * N; e += T) s[(e % N) * RS + e / N] = G[e];  // e = p1 * N + p0
+  for (int e = tid; e < R * N; e += T) s[(e % R) * RS + e / R] = G[kidx<N>(q * R + e % R, e / R)];
   __syncthreads();
   F::inverse(s, tw);
   const float sc = 1.0f / (float)(N * N);
-  float2* out = g_probe + (size_t)m * N * N;
-  for (int e = tid; e < N * N; e += T) {
+  float2* out = g_probe + (size_t)m * N * N + (size_t)q * R * N;  // this CTA's rows
+  for (int e = tid; e < R * N; e += T) {
     const float2 v = cscale(s[(e / N) * RS + e % N], sc);
     out[e] = accumulate ? cadd(out[e], v) : v;
   }
@@ -1019,11 +1080,48 @@ static __global__ void k_scalar_grad(const double* __restrict__ spart, const int
     if (stage >= 0) prof_mark(stage, st);                                 \
   } while (0)
 
+// Launch of a per-wave kernel: plain for one CTA per wave, as clusters of C CTAs otherwise.
+template <int C, class... KArgs, class... Args>
+cudaError_t launch_waves(void (*kern)(KArgs...), unsigned grid, unsigned block, size_t smem, cudaStream_t st,
+                         Args... args) {
+  if constexpr (C == 1) {
+    kern<<<grid, block, smem, st>>>(args...);
+    return cudaGetLastError();
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid * C);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+  }
+}
+
+#define PTY_LAUNCH_RC(expr, what, stage)                                  \
+  do {                                                                    \
+    cudaError_t e_ = (expr);                                              \
+    if (e_ == cudaSuccess) e_ = cudaGetLastError();                       \
+    if (e_ != cudaSuccess) {                                              \
+      set_error("%s launch failed: %s", what, cudaGetErrorString(e_));    \
+      return PTY_ECUDA;                                                   \
+    }                                                                     \
+    note_launch();                                                        \
+    if (stage >= 0) prof_mark(stage, st);                                 \
+  } while (0)
+
 // Phases of one pass.  Forward (with or without what the adjoint needs), loss, adjoint + gradients.
 template <int N>
 struct Pass {
   static constexpr int T = Launch<N>::T, TF = Launch<N>::TF, TA = Launch<N>::TA;
   static constexpr int NN = N * N;
+  static constexpr int C = Fft2<N, TF>::C;  // CTAs per wave
   const Problem& pb;
   const Workspace& ws;
   cudaStream_t st;
@@ -1041,18 +1139,27 @@ struct Pass {
   }
 
   int set_attributes() {
-    if (cudaFuncSetAttribute(k_forward<N, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem_bytes<N>()) != cudaSuccess ||
-        cudaFuncSetAttribute(k_recompute<N, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd_smem_bytes<N>()) != cudaSuccess ||
-        cudaFuncSetAttribute(k_adjoint<N, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_smem_bytes<N, TA>()) != cudaSuccess ||
-        cudaFuncSetAttribute(k_loss<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)loss_smem_bytes<N>()) != cudaSuccess ||
-        cudaFuncSetAttribute(k_probe_spectrum<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)probe_smem()) != cudaSuccess ||
-        cudaFuncSetAttribute(k_probe_grad<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)probe_smem()) != cudaSuccess) {
+    bool ok = cudaFuncSetAttribute(k_forward<N, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)fwd_smem_bytes<N>()) == cudaSuccess &&
+              cudaFuncSetAttribute(k_recompute<N, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)fwd_smem_bytes<N>()) == cudaSuccess &&
+              cudaFuncSetAttribute(k_adjoint<N, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)adj_smem_bytes<N, TA>()) == cudaSuccess &&
+              cudaFuncSetAttribute(k_probe_spectrum<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)probe_smem()) == cudaSuccess &&
+              cudaFuncSetAttribute(k_probe_grad<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)probe_smem()) == cudaSuccess;
+    if constexpr (N != 256) {
+      ok = ok && cudaFuncSetAttribute(k_loss<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)loss_smem_bytes<N>()) == cudaSuccess;
+    }
+    if (!ok) {
       set_error("cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
       return PTY_ECUDA;
     }
     return PTY_OK;
   }
-  static size_t probe_smem() { return sizeof(float2) * ((size_t)N * (N + 1) + N); }
+  static size_t probe_smem() { return sizeof(float2) * ((size_t)wave_rows<N>() * (N + 1) + N); }
   unsigned object_blocks() const {
     const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
     return (unsigned)((nobj + 255) / 256 < 152 * 16 ? (nobj + 255) / 256 : 152 * 16);
@@ -1093,8 +1200,9 @@ struct Pass {
     prof_begin(st);
     k_prepare_object<<<object_blocks(), 256, 0, st>>>(pb.amp, pb.phase, ws.T, nullptr, nobj);
     PTY_LAUNCH_CHECK("k_prepare_object", 0);
-    k_probe_spectrum<N, T><<<pb.M, T, probe_smem(), st>>>(pb.probe, ws.Phat, nullptr);
-    PTY_LAUNCH_CHECK("k_probe_spectrum", 1);
+    PTY_LAUNCH_RC(launch_waves<C>(k_probe_spectrum<N, T>, pb.M, T, probe_smem(), st, pb.probe, ws.Phat,
+                                   (float2*)nullptr),
+                  "k_probe_spectrum", 1);
     if (pb.B == 0) return PTY_OK;
     FwdArgs fa = fwd_args();
     if (save) {
@@ -1105,8 +1213,7 @@ struct Pass {
         fa.anchors = ws.anchors;
       }
     }
-    k_forward<N, TF><<<pb.B * pb.M, TF, fwd_smem_bytes<N>(), st>>>(fa);
-    PTY_LAUNCH_CHECK("k_forward", 2);
+    PTY_LAUNCH_RC(launch_waves<C>(k_forward<N, TF>, pb.B * pb.M, TF, fwd_smem_bytes<N>(), st, fa), "k_forward", 2);
     LossArgs la;
     la.M = pb.M;
     la.Ntot = pb.Ntot;
@@ -1120,7 +1227,11 @@ struct Pass {
     la.I_model = pb.I_model;
     la.u = I_meas ? ws.u : nullptr;
     la.lpart = I_meas ? ws.lpart : nullptr;
-    k_loss<N, T><<<pb.B, T, loss_smem_bytes<N>(), st>>>(la);
+    if constexpr (N == 256) {
+      k_loss_gather<N, T><<<pb.B, T, 0, st>>>(la);
+    } else {
+      k_loss<N, T><<<pb.B, T, loss_smem_bytes<N>(), st>>>(la);
+    }
     PTY_LAUNCH_CHECK("k_loss", 3);
     if (I_meas) {
       k_loss_finalize<<<1, 256, 0, st>>>(ws.lpart, pb.B, pb.loss, (double)pb.B * NN, ws.scal, pb.loss_out, ws.status);
@@ -1185,8 +1296,8 @@ struct Pass {
         aa.vh_per_wave = pb.Nz - 1;
         aa.s0 = 0;
         aa.s1 = pb.Nz;
-        k_adjoint<N, TA><<<pb.B * pb.M, TA, adj_smem_bytes<N, TA>(), st>>>(aa);
-        PTY_LAUNCH_CHECK("k_adjoint", 5);
+        PTY_LAUNCH_RC(launch_waves<C>(k_adjoint<N, TA>, pb.B * pb.M, TA, adj_smem_bytes<N, TA>(), st, aa),
+                      "k_adjoint", 5);
       } else {
         for (int q = nseg - 1; q >= 0; --q) {
           const int s0 = q * K, s1 = (s0 + K < pb.Nz) ? s0 + K : pb.Nz;
@@ -1198,8 +1309,8 @@ struct Pass {
             fa.vhat = want_prop ? ws.vhat : nullptr;
             fa.s0 = s0;
             fa.s1 = s1;
-            k_recompute<N, TF><<<pb.B * pb.M, TF, fwd_smem_bytes<N>(), st>>>(fa);
-            PTY_LAUNCH_CHECK("k_recompute", -1);
+            PTY_LAUNCH_RC(launch_waves<C>(k_recompute<N, TF>, pb.B * pb.M, TF, fwd_smem_bytes<N>(), st, fa),
+                          "k_recompute", -1);
           }
           aa.ckpt = ws.ckpt;
           aa.vhat = want_prop ? ws.vhat : nullptr;
@@ -1209,8 +1320,8 @@ struct Pass {
           aa.vh_per_wave = K;
           aa.s0 = s0;
           aa.s1 = s1;
-          k_adjoint<N, TA><<<pb.B * pb.M, TA, adj_smem_bytes<N, TA>(), st>>>(aa);
-          PTY_LAUNCH_CHECK("k_adjoint", q == 0 ? 5 : -1);
+          PTY_LAUNCH_RC(launch_waves<C>(k_adjoint<N, TA>, pb.B * pb.M, TA, adj_smem_bytes<N, TA>(), st, aa),
+                        "k_adjoint", q == 0 ? 5 : -1);
         }
       }
     }
@@ -1220,8 +1331,9 @@ struct Pass {
       PTY_LAUNCH_CHECK("k_object_grad", 6);
     }
     if (want_probe) {
-      k_probe_grad<N, T><<<pb.M, T, probe_smem(), st>>>(ws.gPhat, pb.g_probe, pb.accumulate);
-      PTY_LAUNCH_CHECK("k_probe_grad", 7);
+      PTY_LAUNCH_RC(launch_waves<C>(k_probe_grad<N, T>, pb.M, T, probe_smem(), st, (const float2*)ws.gPhat,
+                                     pb.g_probe, pb.accumulate),
+                    "k_probe_grad", 7);
     }
     if (gm & (PTY_GRAD_POS | PTY_GRAD_TILT | PTY_GRAD_DZ)) {
       if (!pb.accumulate) {

@@ -102,7 +102,7 @@ size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspac
   return off;
 }
 
-static bool supported_N(int N) { return N == 64 || N == 128; }
+static bool supported_N(int N) { return N == 64 || N == 128 || N == 256; }
 
 static int validate_geom(const pty_geom* g) {
   if (!g) {
@@ -110,7 +110,7 @@ static int validate_geom(const pty_geom* g) {
     return PTY_EINVAL;
   }
   if (!supported_N(g->N)) {
-    set_error("N = %d is not supported (64 or 128)", g->N);
+    set_error("N = %d is not supported (64, 128 or 256)", g->N);
     return PTY_EINVAL;
   }
   if (g->M < 1 || g->Nz < 1 || g->H < g->N || g->W < g->N || g->Ntot < 0) {
@@ -208,6 +208,7 @@ static int dispatch(const Problem& pb) {
   switch (pb.N) {
     case 64: return run_pipeline<64>(pb);
     case 128: return run_pipeline<128>(pb);
+    case 256: return run_pipeline<256>(pb);
     default: set_error("N = %d not supported", pb.N); return PTY_EINVAL;
   }
 }
@@ -409,7 +410,7 @@ int pty_status(const void* ws, void* stream) {
 
 const char* pty_last_error(void) { return g_err; }
 
-int pty_supported_sizes(void) { return (1 << 6) | (1 << 7); }
+int pty_supported_sizes(void) { return (1 << 6) | (1 << 7) | (1 << 8); }
 
 // ---------------------------------------------------------------------------------------------
 // pty_loss_grad_noalloc: the same pass, with its scratch in a fixed device array of this library.

@@ -39,7 +39,7 @@ def _np(t):
 
 
 @pytest.mark.parametrize("N,M,Nz,scan,K", [(64, 2, 5, (2, 3), 2), (64, 2, 5, (2, 3), 3), (64, 2, 5, (2, 3), 5),
-                                           (128, 2, 8, (2, 2), 3)])
+                                           (128, 2, 8, (2, 2), 3), (256, 2, 5, (2, 1), 2)])
 def test_recompute_plan_matches_oracle(N, M, Nz, scan, K):
     case = make_case(N=N, M=M, Nz=Nz, scan=scan, seed=30 + K)
     idx = list(range(case.Ntot))[::-1]

@@ -72,6 +72,18 @@ def test_multislice_n128():
     _check_all(case, [0, 1, 2, 3, 4, 5])
 
 
+def test_multislice_n256_cluster():
+    """256 x 256 windows: each wave spread over a four-CTA cluster."""
+    case = make_case(N=256, M=3, Nz=3, scan=(2, 2), seed=12, step=9)
+    _check_all(case, [2, 0, 3, 1])
+
+
+@pytest.mark.parametrize("loss", [O.GAUSSIAN])
+def test_n256_gaussian_global_tilt(loss):
+    case = make_case(N=256, M=2, Nz=2, scan=(1, 3), seed=13, loss=loss, global_tilt=True)
+    _check_all(case, [1, 2, 0])
+
+
 def test_single_slice_single_mode_n64():
     """The 2D ptychography shape (1 mode, 1 slice): no propagation, dz/tilt gradients are 0."""
     case = make_case(N=64, M=1, Nz=1, scan=(4, 4), seed=2)

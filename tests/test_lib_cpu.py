@@ -52,11 +52,11 @@ def test_workspace_size_and_validation(lib):
     # at least the checkpoints: B*M*Nz*N^2 complex64
     assert n >= 8 * 2 * 3 * 64 * 64 * 8
     assert lib.pty_workspace_size(ctypes.byref(_geom(grad_mask=_lib.PTY_GRAD_PROBE)), 8) < n
-    for bad in (dict(N=32), dict(N=96), dict(M=0), dict(Nz=0), dict(H=63), dict(loss=7), dict(dx=0.0),
+    for bad in (dict(N=32), dict(N=96), dict(N=512), dict(N=256, H=200), dict(M=0), dict(Nz=0), dict(H=63), dict(loss=7), dict(dx=0.0),
                 dict(grad_mask=64), dict(ckpt_stride=-1)):
         assert lib.pty_workspace_size(ctypes.byref(_geom(**bad)), 8) == 0, bad
         assert lib.pty_last_error()
-    assert lib.pty_supported_sizes() == (1 << 6) | (1 << 7)
+    assert lib.pty_supported_sizes() == (1 << 6) | (1 << 7) | (1 << 8)
 
 
 def test_bad_arguments_rejected_before_launch(lib):
