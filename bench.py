@@ -28,7 +28,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "wavefield updates/s (fwd+adjoint, 1 GB300)"
 UNIT = "position*mode*slice updates/s"
-WORKLOAD = "multislice N=128 M=6 Nz=8, object 8x512x512, 4096 positions, batch 512"
+# name -> (description, default batch).  c2 is the configuration the headline metric is quoted on.
+WORKLOADS = {
+    "c2": ("multislice N=128 M=6 Nz=8, object 8x512x512, 4096 positions", 512),
+    "c1": ("single-slice N=64 M=1 Nz=1, object 128x128, 256 positions", 256),
+    "c3": ("multislice N=256 M=12 Nz=20, object 20x1024x1024, 16384 positions", 256),
+    "paper": ("paper-shaped N=128 M=12 Nz=6, object 6x614x614, 16384 positions", 16),
+}
 
 # FP32 CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz max clock.
 ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
@@ -137,15 +143,16 @@ def gpu_smi_id(torch, dev):
         return str(dev.index or 0)
 
 
-def make_inputs(args):
-    import numpy as np
-
+def make_inputs(workload, positions):
+    """The workload, the default flat start and measured patterns for the given scan positions
+    (a dict position -> row of the returned [len(positions)][N][N] float32 array)."""
     from paper_2505_07814_gb300 import synth
 
-    w = synth.workload("c2")
+    w = synth.workload(workload)
     amp0, phase0 = synth.flat_object(w.Nz, w.H, w.W)  # default start of a reconstruction
-    I_meas = synth.vacuum_patterns(w.probe, w.Ntot)
-    return w, amp0, phase0, I_meas
+    used = sorted(set(positions))
+    I_rows = synth.vacuum_patterns(w.probe, len(used))
+    return w, amp0, phase0, I_rows, {p: r for r, p in enumerate(used)}
 
 
 def batch_indices(step, B, Ntot):
@@ -163,22 +170,35 @@ def row_runs(idx):
     return runs
 
 
-def cpu_oracle_sample(w, amp0, phase0, I_meas, B, seconds):
+def cpu_oracle_sample(w, amp0, phase0, I_meas, idx_all, seconds):
     """Time the FP64 oracle's loss and gradient on a bounded sample of one batch."""
     import numpy as np
 
     from oracle import ptycho as O
 
     geom = O.Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, dx=w.dx, lam=w.lam)
-    idx_all = batch_indices(0, B, w.Ntot)
     t0 = time.perf_counter()
     O.loss_and_grad(geom, amp0, phase0, w.probe, w.pos, w.tilt, w.dz, I_meas, idx_all[:1])
     t1 = time.perf_counter() - t0
-    P = max(1, min(B, int(seconds / max(t1, 1e-3))))
+    P = max(1, min(len(idx_all), int(seconds / max(t1, 1e-3))))
     t0 = time.perf_counter()
     O.loss_and_grad(geom, amp0, phase0, w.probe, w.pos, w.tilt, w.dz, I_meas, idx_all[:P])
     dt = time.perf_counter() - t0
     return P, dt
+
+
+def _ntot(workload):
+    return {"c1": 256, "c2": 4096, "c3": 16384, "paper": 16384}[workload]
+
+
+class _Rows:
+    """Measured patterns indexed by scan position, backed by the rows that were generated."""
+
+    def __init__(self, rows, row_of):
+        self.rows, self.row_of = rows, row_of
+
+    def __getitem__(self, j):
+        return self.rows[self.row_of[j]]
 
 
 def run_reference(args, rank):
@@ -186,14 +206,17 @@ def run_reference(args, rank):
         return
     import numpy as np
 
-    w, amp0, phase0, I_meas = make_inputs(args)
+    P = 2  # positions per step: a bounded sample of one batch
+    batches = [batch_indices(k, args.batch, _ntot(args.workload))[:P] for k in range(args.warmup + args.steps)]
+    w, amp0, phase0, I_rows, row_of = make_inputs(args.workload, [p for b in batches for p in b])
     from oracle import ptycho as O
+    import numpy as np
 
+    I_meas = _Rows(I_rows, row_of)
     geom = O.Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, dx=w.dx, lam=w.lam)
-    P = 2  # positions per step: a bounded sample of one batch (2 x 6 modes x 8 slices = 96 updates)
     times = []
     for k in range(args.warmup + args.steps):
-        idx = batch_indices(k, args.batch, w.Ntot)[:P]
+        idx = batches[k]
         t0 = time.perf_counter()
         O.loss_and_grad(geom, amp0, phase0, w.probe, w.pos, w.tilt, w.dz, I_meas, idx)
         if k >= args.warmup:
@@ -204,11 +227,40 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "N": w.N, "M": w.M, "Nz": w.Nz, "positions": w.Ntot,
-                       "batch": args.batch, "sample_positions_per_step": P},
+            "config": {"workload": WORKLOADS[args.workload][0], "N": w.N, "M": w.M, "Nz": w.Nz,
+                       "positions": w.Ntot, "batch": args.batch, "sample_positions_per_step": P},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def sweep_ckpt(args, w, geometry, params, I_meas, idx_t, flush, dev, torch, Ptycho):
+    """Checkpoint-vs-recompute sweep: one JSON line per ckpt_stride with the step time and the bytes
+    the forward record takes."""
+    B = args.batch
+    for K in [int(x) for x in args.sweep_ckpt.split(",")]:
+        geom = geometry(K)
+        pt = Ptycho(geom, B, device=dev)
+        grads = params.zeros_like()
+        for k in range(args.warmup):
+            pt.loss_grad(params, idx_t[k % 8], I_meas, grads=grads)
+        torch.cuda.synchronize()
+        ms = 0.0
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for k in range(args.steps):
+            flush.zero_()
+            ev[0].record()
+            pt.loss_grad(params, idx_t[k % 8], I_meas, grads=grads)
+            ev[1].record()
+            ev[1].synchronize()
+            ms += ev[0].elapsed_time(ev[1])
+        assert pt.status() == 0
+        print(json.dumps({"workload": WORKLOADS[args.workload][0], "batch": B, "ckpt_stride": K,
+                          "checkpoint_bytes": geom.checkpoint_bytes(B), "workspace_bytes": pt.ws_bytes,
+                          "ms_per_step": ms / args.steps,
+                          "updates_per_s": B * w.M * w.Nz * args.steps / (ms / 1e3)}), flush=True)
+        del pt, grads
+        torch.cuda.empty_cache()
 
 
 def main():
@@ -217,11 +269,16 @@ def main():
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--batch", type=int, default=512)
+    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--batch", type=int, default=0, help="positions per step (0: the workload's default)")
+    ap.add_argument("--ckpt-stride", type=int, default=1, help="adjoint memory plan (pty_geom.ckpt_stride)")
+    ap.add_argument("--sweep-ckpt", default="", help="comma-separated strides: print one timing line per stride")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
+    if args.batch <= 0:
+        args.batch = WORKLOADS[args.workload][1]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -245,20 +302,34 @@ def main():
     build.build()
     _lib.load()
 
-    w, amp0, phase0, I_meas_np = make_inputs(args)
     B = args.batch
-    geom = Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, Ntot=w.Ntot, dx=w.dx, lam=w.lam, loss="poisson")
+    Ntot = _ntot(args.workload)
+    # each rank takes its own batches (weak scaling: independent position blocks, no collective)
+    idx_h = [batch_indices(k * world + rank, B, Ntot) for k in range(8)]
+    w, amp0, phase0, I_rows, row_of = make_inputs(args.workload, [p for b in idx_h for p in b])
     f32 = dict(dtype=torch.float32, device=dev)
     params = Params(amp=torch.tensor(amp0, **f32), phase=torch.tensor(phase0, **f32),
                     probe=torch.tensor(w.probe, dtype=torch.complex64, device=dev), pos=torch.tensor(w.pos, **f32),
                     tilt=torch.tensor(w.tilt, **f32), dz=torch.tensor([w.dz], **f32))
-    I_meas = torch.tensor(I_meas_np, **f32)
+    # measured patterns [Ntot][N][N] on the device; only the rows the timed batches read are filled
+    I_meas = torch.zeros((w.Ntot, w.N, w.N), **f32)
+    rows_t = torch.tensor(I_rows, **f32)
+    for p_, r_ in row_of.items():
+        I_meas[p_] = rows_t[r_]
+    del rows_t
+    idx_t = [torch.tensor(i, dtype=torch.int32, device=dev) for i in idx_h]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > 129 MB L2
+
+    def geometry(stride):
+        return Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, Ntot=w.Ntot, dx=w.dx, lam=w.lam, loss="poisson",
+                        ckpt_stride=stride)
+
+    if args.sweep_ckpt:
+        sweep_ckpt(args, w, geometry, params, I_meas, idx_t, flush, dev, torch, Ptycho)
+        return
+    geom = geometry(args.ckpt_stride)
     pt = Ptycho(geom, B, device=dev)
     grads = params.zeros_like()
-    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > 129 MB L2
-    # each rank takes its own batches (weak scaling: independent position blocks, no collective)
-    idx_h = [batch_indices(k * world + rank, B, w.Ntot) for k in range(8)]
-    idx_t = [torch.tensor(i, dtype=torch.int32, device=dev) for i in idx_h]
 
     for k in range(args.warmup):
         pt.loss_grad(params, idx_t[k % 8], I_meas, grads=grads)
@@ -306,7 +377,7 @@ def main():
 
     # end to end through the public API from pinned host buffers
     host = {n: getattr(params, n).cpu().pin_memory() for n in ("amp", "phase", "probe", "pos", "tilt", "dz")}
-    h_meas = I_meas.cpu().pin_memory()
+    h_rows = torch.tensor(I_rows).pin_memory()
     h_grads = {n: torch.empty_like(getattr(grads, n), device="cpu").pin_memory()
                for n in ("amp", "phase", "probe", "pos", "tilt", "dz")}
     h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
@@ -324,7 +395,8 @@ def main():
             getattr(params, n).copy_(host[n], non_blocking=True)
             h2d += host[n].numel() * host[n].element_size()
         for lo, hi in row_runs(idx_h[k % 8]):  # the measured patterns this batch reads
-            I_meas[lo:hi].copy_(h_meas[lo:hi], non_blocking=True)
+            r0 = row_of[lo]
+            I_meas[lo:hi].copy_(h_rows[r0:r0 + hi - lo], non_blocking=True)
             h2d += (hi - lo) * w.N * w.N * 4
         loss, _ = pt.loss_grad(params, idx, I_meas, grads=grads)
         for n in h_grads:
@@ -339,7 +411,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        P, dt = cpu_oracle_sample(w, amp0, phase0, I_meas_np, B, args.cpu_seconds)
+        P, dt = cpu_oracle_sample(w, amp0, phase0, _Rows(I_rows, row_of), idx_h[0], args.cpu_seconds)
         cpu = {"value": P * w.M * w.Nz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "FP64 numpy oracle, loss + all gradients for the first %d positions of one %d-position "
                          "batch (%d updates, %.1f s, single-threaded pocketfft)" % (P, B, P * w.M * w.Nz, dt)}
@@ -348,7 +420,9 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "N": w.N, "M": w.M, "Nz": w.Nz, "positions": w.Ntot, "batch": B,
+                "config": {"workload": "%s, batch %d" % (WORKLOADS[args.workload][0], B), "N": w.N, "M": w.M,
+                           "Nz": w.Nz, "positions": w.Ntot, "batch": B, "ckpt_stride": args.ckpt_stride,
+                           "checkpoint_bytes": geom.checkpoint_bytes(B),
                            "object": [w.Nz, w.H, w.W], "loss": "poisson", "grads": "amp,phase,probe,pos,tilt,dz",
                            "batches": "contiguous raster blocks", "start": "flat object (amp 1, phase U[0,1e-8])",
                            "l2": "flushed before every step (256 MiB write outside the step events)",

@@ -194,7 +194,11 @@ def vacuum_patterns(probe: np.ndarray, n: int, seed: int = 1237) -> np.ndarray:
     for P in probe:
         disc += np.abs(np.fft.fftshift(np.fft.fft2(P, norm="ortho"))) ** 2
     rng = np.random.default_rng(seed)
-    return rng.poisson(np.broadcast_to(disc, (n, N, N))).astype(np.float32)
+    out = np.empty((n, N, N), dtype=np.float32)
+    for i in range(0, n, 64):  # chunks keep the integer draws small
+        k = min(64, n - i)
+        out[i:i + k] = rng.poisson(np.broadcast_to(disc, (k, N, N)))
+    return out
 
 
 # ---------------------------------------------------------------------------------------------
@@ -220,6 +224,11 @@ def workload(name: str, **over) -> Workload:
         N, M, Nz, H, W, dz = 256, 12, 20, 1024, 1024, 2.0
         amp, phase = make_object_3d(Nz, H, W, dx)
         pos = make_scan(128, 128, 4, N, H, W)
+        tilt = np.tile(np.array([0.5e-3, -0.3e-3]), (pos.shape[0], 1))
+    elif name == "paper":  # shaped like the paper's twisted-bilayer reconstruction: 12 modes, 6 slices
+        N, M, Nz, H, W, dz = 128, 12, 6, 614, 614, 2.0
+        amp, phase = make_object_3d(Nz, H, W, dx)
+        pos = make_scan(128, 128, 3.8, N, H, W)
         tilt = np.tile(np.array([0.5e-3, -0.3e-3]), (pos.shape[0], 1))
     elif name == "small":  # ragged multislice case for parity tests
         N = over.pop("N", 64)
