@@ -272,6 +272,8 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--batch", type=int, default=0, help="positions per step (0: the workload's default)")
     ap.add_argument("--ckpt-stride", type=int, default=1, help="adjoint memory plan (pty_geom.ckpt_stride)")
+    ap.add_argument("--fft", default="fp32", choices=["fp32", "bf16", "fp16", "bf16x3"],
+                    help="per-slice DFTs: FP32 shared-memory FFT or split-precision tensor-core GEMMs")
     ap.add_argument("--sweep-ckpt", default="", help="comma-separated strides: print one timing line per stride")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -322,7 +324,7 @@ def main():
 
     def geometry(stride):
         return Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, Ntot=w.Ntot, dx=w.dx, lam=w.lam, loss="poisson",
-                        ckpt_stride=stride)
+                        ckpt_stride=stride, fft=args.fft)
 
     if args.sweep_ckpt:
         sweep_ckpt(args, w, geometry, params, I_meas, idx_t, flush, dev, torch, Ptycho)
@@ -419,9 +421,12 @@ def main():
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": "f32" if args.fft == "fp32" else "f32 (DFTs: %s split, f32 accumulate)" % args.fft,
+                "data": "synthetic",
                 "config": {"workload": "%s, batch %d" % (WORKLOADS[args.workload][0], B), "N": w.N, "M": w.M,
                            "Nz": w.Nz, "positions": w.Ntot, "batch": B, "ckpt_stride": args.ckpt_stride,
+                           "fft": args.fft,
                            "checkpoint_bytes": geom.checkpoint_bytes(B),
                            "object": [w.Nz, w.H, w.W], "loss": "poisson", "grads": "amp,phase,probe,pos,tilt,dz",
                            "batches": "contiguous raster blocks", "start": "flat object (amp 1, phase U[0,1e-8])",

@@ -89,7 +89,19 @@ typedef struct {
                       re-runs each K-slice segment from there before differentiating it:
                       B*M*(ceil(Nz/K) - 1 + 2K + 1)*N^2*8 bytes and about one more forward pass of
                       work.  K >= Nz re-runs the whole forward. */
+  int fft_impl;    /* PTY_FFT_*: how the per-slice 2D DFTs are computed.  PTY_FFT_FP32: FP32 FFTs in
+                      shared memory (every N).  The split modes (N = 64, 128) run dense DFT matrix
+                      products on the tensor cores with every FP32 operand cut into 16-bit pieces and
+                      FP32 accumulation: PTY_FFT_SPLIT_BF16 and PTY_FFT_SPLIT_FP16 keep a high part
+                      and a remainder (three products; 16 and 22 significant bits, fp16 after a
+                      power-of-two rescaling of each batch), PTY_FFT_SPLIT3_BF16 three bf16 pieces
+                      (six products, 24 bits).  The split modes keep every slice's checkpoint
+                      (ckpt_stride is ignored) and add 2*B*M*N^2*8 bytes of workspace.  The first
+                      split call on a device builds its DFT tables and waits for them (not
+                      capturable into a CUDA graph). */
 } pty_geom;
+
+enum { PTY_FFT_FP32 = 0, PTY_FFT_SPLIT_BF16 = 1, PTY_FFT_SPLIT_FP16 = 2, PTY_FFT_SPLIT3_BF16 = 3 };
 
 /* Adam state and hyper-parameters for pty_step / pty_adam (PyTorch's Adam: bias-corrected first and
  * second moments; complex tensors are treated as pairs of reals).  m_* and v_* are device float

@@ -29,6 +29,7 @@ PTY_GRAD_POS = 8
 PTY_GRAD_TILT = 16
 PTY_GRAD_DZ = 32
 PTY_GRAD_ALL = 63
+PTY_FFT_FP32, PTY_FFT_SPLIT_BF16, PTY_FFT_SPLIT_FP16, PTY_FFT_SPLIT3_BF16 = 0, 1, 2, 3
 
 # Every symbol include/pty.h declares (checked by the CPU test suite).
 EXPORTS = ("pty_workspace_size", "pty_forward", "pty_loss_grad", "pty_adam_update", "pty_step",
@@ -43,7 +44,7 @@ class pty_geom(ctypes.Structure):
                 ("W", ctypes.c_int), ("Ntot", ctypes.c_int), ("dx", ctypes.c_float),
                 ("lambda_", ctypes.c_float), ("loss", ctypes.c_int), ("p", ctypes.c_float),
                 ("eps", ctypes.c_float), ("grad_mask", ctypes.c_int), ("global_tilt", ctypes.c_int),
-                ("ckpt_stride", ctypes.c_int)]
+                ("ckpt_stride", ctypes.c_int), ("fft_impl", ctypes.c_int)]
 
 
 class pty_adam(ctypes.Structure):

@@ -1,0 +1,184 @@
+// gemm_mma.cuh -- tensor-core GEMM C = A * B^T with 16-bit operands (bf16 or fp16) and FP32
+// accumulation, for the split-precision DFT passes and the CNN layers.
+//
+// A is M x K and B is N x K, both K-contiguous ("TN": the layout mma.sync reads directly).  A is
+// produced by a loader functor (plain matrix, split-precision expansion of complex data, or an
+// implicit-GEMM gather of convolution patches), B is a plain 16-bit matrix, and each finished
+// 2-element pair of C goes to an epilogue functor.  M, N must be multiples of the CTA tile (128 x
+// 128) and K of 32; the callers guarantee it.
+//
+// CTA tile 128 x 128 x 32, eight warps as 2 (M) x 4 (N), warp tile 64 x 32 = 4 x 4 mma.sync
+// m16n8k16 tiles; A and B tiles double-buffered in shared memory with an 80-byte row pitch (the
+// ldmatrix row addresses of one 8 x 8 matrix then fall in distinct bank groups).
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pty {
+
+constexpr int GB_M = 128, GB_N = 128, GB_K = 32, GB_PITCH = 40, GB_THREADS = 256;
+
+template <class H>
+struct MmaOp;
+template <>
+struct MmaOp<__nv_bfloat16> {
+  __device__ static void run(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  }
+  // d = a b (zero accumulator in)
+  __device__ static void run0(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%10,%10,%10};"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(0.f));
+  }
+};
+template <>
+struct MmaOp<__half> {
+  __device__ static void run(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  }
+  __device__ static void run0(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%10,%10,%10,%10};"
+        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]), "f"(0.f));
+  }
+};
+
+__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Plain A loader: 8 consecutive K elements of row m starting at k (16-byte aligned).
+template <class H>
+struct PlainLoader {
+  const H* A;
+  size_t lda;
+  __device__ __forceinline__ uint4 operator()(int m, int k) const {
+    return *reinterpret_cast<const uint4*>(A + (size_t)m * lda + k);
+  }
+};
+
+// C[M x N] = A[M x K] * B[N x K]^T.  grid = (N / 128, M / 128).
+//
+// PROMOTE: the tensor core's addition of each MMA's products into its FP32 accumulator does not
+// round like an IEEE FP32 add, and over a long K the error compounds (measured on the split DFTs:
+// it grew with K and with the number of split products).  With PROMOTE the products of each 32-wide
+// K tile are summed by the MMAs into a fresh register tile that is then added to the running sum
+// with an ordinary round-to-nearest FP32 add, so the long sum rounds like a plain FP32 dot product.
+template <class H, class Loader, class Epi, bool PROMOTE = false>
+__global__ void __launch_bounds__(GB_THREADS) k_gemm_tn(Loader load, const H* __restrict__ B, size_t ldb, int K,
+                                                        Epi epi) {
+  __shared__ __align__(16) H sA[2][GB_M * GB_PITCH];
+  __shared__ __align__(16) H sB[2][GB_N * GB_PITCH];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp / 4, wn = warp % 4;  // warp position: 2 x 4
+  const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+  float acc[4][4][4];
+  [[maybe_unused]] float part[PROMOTE ? 4 : 1][4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+
+  // each thread moves two 16-byte chunks of A and two of B per K tile (128 rows x 4 chunks)
+  auto fetch = [&](int buf, int k0) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = tid + h * GB_THREADS;  // 0..511
+      const int r = c >> 2, kc = (c & 3) * 8;
+      *reinterpret_cast<uint4*>(&sA[buf][r * GB_PITCH + kc]) = load(m0 + r, k0 + kc);
+      cp_async16(&sB[buf][r * GB_PITCH + kc], B + (size_t)(n0 + r) * ldb + k0 + kc);
+    }
+    cp_async_commit();
+  };
+
+  const int ktiles = K / GB_K;
+  fetch(0, 0);
+  for (int kt = 0; kt < ktiles; ++kt) {
+    const int buf = kt & 1;
+    cp_async_wait0();
+    __syncthreads();
+    if (kt + 1 < ktiles) fetch(buf ^ 1, (kt + 1) * GB_K);
+#pragma unroll
+    for (int kk = 0; kk < GB_K; kk += 16) {
+      uint32_t af[4][4], bf[4][2];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int r = wm * 64 + i * 16 + (lane & 7) + 8 * ((lane >> 3) & 1);
+        ldsm_x4(af[i], &sA[buf][r * GB_PITCH + kk + 8 * (lane >> 4)]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; j += 2) {
+        const int r = wn * 32 + j * 8 + (lane & 7) + 8 * (lane >> 4);
+        uint32_t t[4];
+        ldsm_x4(t, &sB[buf][r * GB_PITCH + kk + 8 * ((lane >> 3) & 1)]);
+        bf[j][0] = t[0];
+        bf[j][1] = t[1];
+        bf[j + 1][0] = t[2];
+        bf[j + 1][1] = t[3];
+      }
+      if constexpr (PROMOTE) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (kk == 0) {
+              MmaOp<H>::run0(part[i][j], af[i], bf[j]);
+            } else {
+              MmaOp<H>::run(part[i][j], af[i], bf[j]);
+            }
+          }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) MmaOp<H>::run(acc[i][j], af[i], bf[j]);
+      }
+    }
+    if constexpr (PROMOTE) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[i][j][q] += part[i][j][q];
+    }
+  }
+  // epilogue: thread holds C(row, col..col+1) and C(row+8, col..col+1) of every 16 x 8 tile
+  const int g = lane >> 2, t4 = lane & 3;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int row = m0 + wm * 64 + i * 16 + g, col = n0 + wn * 32 + j * 8 + 2 * t4;
+      epi(row, col, acc[i][j][0], acc[i][j][1]);
+      epi(row + 8, col, acc[i][j][2], acc[i][j][3]);
+    }
+}
+
+}  // namespace pty

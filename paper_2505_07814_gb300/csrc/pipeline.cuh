@@ -244,6 +244,53 @@ __device__ __forceinline__ void prefetch_block(const float2* base) {
   if (threadIdx.x < 8) prefetch_l2(reinterpret_cast<const char*>(base) + threadIdx.x * chunk, chunk);
 }
 
+// Per-wave tables, written by the first N threads (axis-0 tables indexed by k-space row p0, axis-1
+// tables by k-space column p1).  Forward: shift ramps R (axis 0 carries the 1/N^2 of the inverse
+// DFT) and the two factors of Eq. 4's propagator (axis 0 carries 1/N^2).
+template <int N>
+__device__ void fwd_tables(float2* ra0, float2* ra1, float2* pm0, float2* pm1, float d0, float d1, float th0, float th1,
+                           float dz, float dx, float lam) {
+  const int tid = threadIdx.x;
+  if (tid < N) {
+    const int q0 = signed_bin<N>(kbin0<N>(tid)), q1 = signed_bin<N>(kbin1<N>(tid));
+    const float inv_nn = 1.0f / (float)(N * N);
+    ra0[tid] = cscale(expipi(-2.0 * q0 * (double)d0 / N), inv_nn);
+    ra1[tid] = expipi(-2.0 * q1 * (double)d1 / N);
+    // Eq. 4 split into its two axes: exp(i pi (-lam dz k_a^2 + 2 dz k_a tan th_a))
+    const double k0 = q0 / (N * (double)dx), k1 = q1 / (N * (double)dx);
+    pm0[tid] = cscale(expipi(-(double)lam * dz * k0 * k0 + 2.0 * dz * k0 * tan((double)th0)), inv_nn);
+    pm1[tid] = expipi(-(double)lam * dz * k1 * k1 + 2.0 * dz * k1 * tan((double)th1));
+  }
+}
+// Adjoint: conjugate propagator factors (axis 0 with 1/N^2), conjugate shift ramps, and the real
+// factors of the dz, tilt and position terms (signs and 2 pi / N^2 folded in).
+template <int N>
+__device__ void adj_tables(float2* cm0, float2* cm1, float2* cr0, float2* cr1, float* e0, float* e1, float* c0,
+                           float* c1, float* f0, float* f1, float d0, float d1, float th0, float th1, float dz,
+                           float dx, float lam) {
+  const int tid = threadIdx.x;
+  constexpr int NN = N * N;
+  if (tid < N) {
+    // axis-0 tables are indexed by k-space row p0, axis-1 tables by k-space column p1
+    const int q0 = signed_bin<N>(kbin0<N>(tid)), q1 = signed_bin<N>(kbin1<N>(tid));
+    const float inv_nn = 1.0f / (float)NN;
+    const double k0 = q0 / (N * (double)dx), k1 = q1 / (N * (double)dx);
+    const double tn0 = tan((double)th0), tn1 = tan((double)th1);
+    cm0[tid] = cscale(cconj(expipi(-(double)lam * dz * k0 * k0 + 2.0 * dz * k0 * tn0)), inv_nn);
+    cm1[tid] = cconj(expipi(-(double)lam * dz * k1 * k1 + 2.0 * dz * k1 * tn1));
+    cr0[tid] = expipi(2.0 * q0 * (double)d0 / N);
+    cr1[tid] = expipi(2.0 * q1 * (double)d1 / N);
+    const double PI = 3.14159265358979323846;
+    const double cs0 = cos((double)th0), cs1 = cos((double)th1);
+    e0[tid] = (float)(PI * lam * k0 * k0 - 2.0 * PI * k0 * tn0);
+    e1[tid] = (float)(PI * lam * k1 * k1 - 2.0 * PI * k1 * tn1);
+    c0[tid] = (float)(-2.0 * PI * dz * k0 / (cs0 * cs0));
+    c1[tid] = (float)(-2.0 * PI * dz * k1 / (cs1 * cs1));
+    f0[tid] = (float)(2.0 * PI * q0 / ((double)N * NN));
+    f1[tid] = (float)(2.0 * PI * q1 / ((double)N * NN));
+  }
+}
+
 // ---- forward hooks (see NoHook for the calling convention).  Natural-layout hooks run in the
 // col step (lanes own consecutive columns); k-space hooks run in the row step (lanes own
 // consecutive k-space rows p0, so global k-space buffers are indexed p1 * N + p0). ----
@@ -347,17 +394,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   prefetch_patch<N>(Tpatch, a.W);
 
   build_twiddles<N>(tw);
-  if (tid < N) {
-    // axis-0 tables are indexed by k-space row p0, axis-1 tables by k-space column p1
-    const int q0 = signed_bin<N>(kbin0<N>(tid)), q1 = signed_bin<N>(kbin1<N>(tid));
-    const float inv_nn = 1.0f / (float)NN;
-    ra0[tid] = cscale(expipi(-2.0 * q0 * (double)d0 / N), inv_nn);
-    ra1[tid] = expipi(-2.0 * q1 * (double)d1 / N);
-    // Eq. 4 split into its two axes: exp(i pi (-lam dz k_a^2 + 2 dz k_a tan th_a))
-    const double k0 = q0 / (N * (double)a.dx), k1 = q1 / (N * (double)a.dx);
-    pm0[tid] = cscale(expipi(-(double)a.lam * dz * k0 * k0 + 2.0 * dz * k0 * tan((double)th0)), inv_nn);
-    pm1[tid] = expipi(-(double)a.lam * dz * k1 * k1 + 2.0 * dz * k1 * tan((double)th1));
-  }
+  fwd_tables<N>(ra0, ra1, pm0, pm1, d0, d1, th0, th1, dz, a.dx, a.lam);
   __syncthreads();
 
   // Shifted probe P_j = F^-1[P^_m R]: the row and block steps of the inverse here; its column step
@@ -459,15 +496,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_recompute(FwdArgs a) {
   const float2* Tpatch = a.T + (size_t)i0 * a.W + i1;
   const int K = a.kstride;
   build_twiddles<N>(tw);
-  if (tid < N) {
-    const int q0 = signed_bin<N>(kbin0<N>(tid)), q1 = signed_bin<N>(kbin1<N>(tid));
-    const float inv_nn = 1.0f / (float)NN;
-    ra0[tid] = cscale(expipi(-2.0 * q0 * (double)d0 / N), inv_nn);
-    ra1[tid] = expipi(-2.0 * q1 * (double)d1 / N);
-    const double k0 = q0 / (N * (double)a.dx), k1 = q1 / (N * (double)a.dx);
-    pm0[tid] = cscale(expipi(-(double)a.lam * dz * k0 * k0 + 2.0 * dz * k0 * tan((double)th0)), inv_nn);
-    pm1[tid] = expipi(-(double)a.lam * dz * k1 * k1 + 2.0 * dz * k1 * tan((double)th1));
-  }
+  fwd_tables<N>(ra0, ra1, pm0, pm1, d0, d1, th0, th1, dz, a.dx, a.lam);
   __syncthreads();
   float2* ck_seg = a.ckpt ? a.ckpt + (size_t)bm * K * NN : nullptr;
   float2* vh_seg = a.vhat ? a.vhat + (size_t)bm * K * NN : nullptr;
@@ -876,25 +905,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   if (want_prop && a.s1 - 1 > a.s0 - 1 && a.s1 >= 2) prefetch_block<N>(vh_base + (size_t)(a.s1 - 2) * NN);
 
   build_twiddles<N>(tw);
-  if (tid < N) {
-    // axis-0 tables are indexed by k-space row p0, axis-1 tables by k-space column p1
-    const int q0 = signed_bin<N>(kbin0<N>(tid)), q1 = signed_bin<N>(kbin1<N>(tid));
-    const float inv_nn = 1.0f / (float)NN;
-    const double k0 = q0 / (N * (double)a.dx), k1 = q1 / (N * (double)a.dx);
-    const double tn0 = tan((double)th0), tn1 = tan((double)th1);
-    cm0[tid] = cscale(cconj(expipi(-(double)a.lam * dz * k0 * k0 + 2.0 * dz * k0 * tn0)), inv_nn);
-    cm1[tid] = cconj(expipi(-(double)a.lam * dz * k1 * k1 + 2.0 * dz * k1 * tn1));
-    cr0[tid] = expipi(2.0 * q0 * (double)d0 / N);
-    cr1[tid] = expipi(2.0 * q1 * (double)d1 / N);
-    const double PI = 3.14159265358979323846;
-    const double cs0 = cos((double)th0), cs1 = cos((double)th1);
-    e0[tid] = (float)(PI * a.lam * k0 * k0 - 2.0 * PI * k0 * tn0);
-    e1[tid] = (float)(PI * a.lam * k1 * k1 - 2.0 * PI * k1 * tn1);
-    c0[tid] = (float)(-2.0 * PI * dz * k0 / (cs0 * cs0));
-    c1[tid] = (float)(-2.0 * PI * dz * k1 / (cs1 * cs1));
-    f0[tid] = (float)(2.0 * PI * q0 / ((double)N * NN));
-    f1[tid] = (float)(2.0 * PI * q1 / ((double)N * NN));
-  }
+  adj_tables<N>(cm0, cm1, cr0, cr1, e0, e1, c0, c1, f0, f1, d0, d1, th0, th1, dz, a.dx, a.lam);
   __syncthreads();
 
   if (a.s1 == a.Nz) {
@@ -1193,9 +1204,8 @@ struct Pass {
     return fa;
   }
 
-  // T, probe spectra, the forward kernel (storing checkpoints when `save`) and the mode sum (and
-  // the loss when I_meas is given).
-  int forward(const float* I_meas) {
+  // T and probe spectra (start of every forward).
+  int forward_begin() {
     const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
     prof_begin(st);
     k_prepare_object<<<object_blocks(), 256, 0, st>>>(pb.amp, pb.phase, ws.T, nullptr, nobj);
@@ -1203,7 +1213,10 @@ struct Pass {
     PTY_LAUNCH_RC(launch_waves<C>(k_probe_spectrum<N, T>, pb.M, T, probe_smem(), st, pb.probe, ws.Phat,
                                    (float2*)nullptr),
                   "k_probe_spectrum", 1);
-    if (pb.B == 0) return PTY_OK;
+    return PTY_OK;
+  }
+  // Forward arguments with the checkpoint outputs of this pass's memory plan.
+  FwdArgs fwd_args_saved() const {
     FwdArgs fa = fwd_args();
     if (save) {
       if (K == 1) {
@@ -1213,7 +1226,10 @@ struct Pass {
         fa.anchors = ws.anchors;
       }
     }
-    PTY_LAUNCH_RC(launch_waves<C>(k_forward<N, TF>, pb.B * pb.M, TF, fwd_smem_bytes<N>(), st, fa), "k_forward", 2);
+    return fa;
+  }
+  // Mode sum, and the loss when I_meas is given.
+  int loss_phase(const float* I_meas) {
     LossArgs la;
     la.M = pb.M;
     la.Ntot = pb.Ntot;
@@ -1238,6 +1254,15 @@ struct Pass {
       PTY_LAUNCH_CHECK("k_loss_finalize", 4);
     }
     return PTY_OK;
+  }
+  // T, probe spectra, the forward kernel (storing checkpoints when `save`) and the mode sum (and
+  // the loss when I_meas is given).
+  int forward(const float* I_meas) {
+    int rc = forward_begin();
+    if (rc || pb.B == 0) return rc;
+    PTY_LAUNCH_RC(launch_waves<C>(k_forward<N, TF>, pb.B * pb.M, TF, fwd_smem_bytes<N>(), st, fwd_args_saved()),
+                  "k_forward", 2);
+    return loss_phase(I_meas);
   }
 
   // dL/dI from the caller instead of the loss (the adjoint of the forward model alone).
@@ -1278,14 +1303,19 @@ struct Pass {
     return aa;
   }
 
-  // Adjoint over all slices (segment by segment in the recompute mode) and the gradient finalisers.
-  int adjoint() {
-    const int gm = pb.grad_mask;
+  // Zero the accumulators of the adjoint.
+  int adjoint_begin() {
     const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
     if (want_obj && cudaMemsetAsync(ws.gT, 0, sizeof(float2) * nobj, st) != cudaSuccess) return memset_failed();
     if (want_probe && cudaMemsetAsync(ws.gPhat, 0, sizeof(float2) * pb.M * NN, st) != cudaSuccess) return memset_failed();
+    if (pb.B > 0 && cudaMemsetAsync(ws.spart, 0, sizeof(double) * 5 * pb.B * pb.M, st) != cudaSuccess)
+      return memset_failed();
+    return PTY_OK;
+  }
+
+  // The adjoint kernels over all slices (segment by segment in the recompute mode).
+  int adjoint_waves() {
     if (pb.B > 0) {
-      if (cudaMemsetAsync(ws.spart, 0, sizeof(double) * 5 * pb.B * pb.M, st) != cudaSuccess) return memset_failed();
       AdjArgs aa = adj_args();
       if (K == 1) {
         aa.ckpt = ws.ckpt;
@@ -1325,6 +1355,13 @@ struct Pass {
         }
       }
     }
+    return PTY_OK;
+  }
+
+  // dL/damp, dL/dphase, dL/dprobe and the scalar gradients from the accumulators.
+  int finalize() {
+    const int gm = pb.grad_mask;
+    const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
     if (want_obj) {
       k_object_grad<<<object_blocks(), 256, 0, st>>>(pb.amp, pb.phase, ws.gT, (gm & PTY_GRAD_AMP) ? pb.g_amp : nullptr,
                                                      (gm & PTY_GRAD_PHASE) ? pb.g_phase : nullptr, pb.accumulate, nobj);
@@ -1357,6 +1394,12 @@ struct Pass {
       }
     }
     return PTY_OK;
+  }
+  int adjoint() {
+    int rc = adjoint_begin();
+    if (!rc) rc = adjoint_waves();
+    if (!rc) rc = finalize();
+    return rc;
   }
   int memset_failed() {
     set_error("cudaMemsetAsync failed: %s", cudaGetErrorString(cudaGetLastError()));

@@ -54,7 +54,7 @@ static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 int effective_stride(const pty_geom& g) {
   const bool needs = (g.grad_mask & (PTY_GRAD_AMP | PTY_GRAD_PHASE)) ||
                      ((g.grad_mask & (PTY_GRAD_DZ | PTY_GRAD_TILT)) && g.Nz > 1);
-  if (!needs || g.ckpt_stride <= 1) return 1;
+  if (!needs || g.ckpt_stride <= 1 || g.fft_impl != PTY_FFT_FP32) return 1;
   return g.ckpt_stride < g.Nz ? g.ckpt_stride : g.Nz;
 }
 
@@ -98,6 +98,11 @@ size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspac
     if (want_probe) w.gPhat = (float2*)take(sizeof(float2) * g.M * NN);
     w.spart = (double*)take(sizeof(double) * 5 * (waves > 0 ? waves : 1));
   }
+  if (g.fft_impl != PTY_FFT_FP32) {
+    w.wave = (float2*)take(sizeof(float2) * waves * NN);
+    w.tmp = (float2*)take(sizeof(float2) * waves * NN);
+    w.gscal = (float*)take(sizeof(float) * 4);
+  }
   if (out) *out = w;
   return off;
 }
@@ -128,6 +133,14 @@ static int validate_geom(const pty_geom* g) {
   }
   if ((g->grad_mask & ~PTY_GRAD_ALL) != 0) {
     set_error("unknown bits in grad_mask 0x%x", g->grad_mask);
+    return PTY_EINVAL;
+  }
+  if (g->fft_impl < PTY_FFT_FP32 || g->fft_impl > PTY_FFT_SPLIT3_BF16) {
+    set_error("unknown fft_impl %d", g->fft_impl);
+    return PTY_EINVAL;
+  }
+  if (g->fft_impl != PTY_FFT_FP32 && g->N != 64 && g->N != 128) {
+    set_error("split-precision DFTs support N = 64 and 128, not %d", g->N);
     return PTY_EINVAL;
   }
   if (g->ckpt_stride < 0) {
@@ -187,6 +200,7 @@ static int prepare(const pty_geom* g, int B, int mode, const int32_t* idx, const
   pb->global_tilt = g->global_tilt ? 1 : 0;
   pb->mode = mode;
   pb->kstride = effective_stride(*g);
+  pb->fft_impl = g->fft_impl;
   pb->idx = idx;
   pb->amp = amp;
   pb->phase = phase;
@@ -205,6 +219,9 @@ static int dispatch(const Problem& pb) {
     set_error("cudaMemsetAsync failed: %s", cudaGetErrorString(cudaGetLastError()));
     return PTY_ECUDA;
   }
+  if (pb.fft_impl == PTY_FFT_SPLIT_BF16) return pb.N == 64 ? run_pipeline_gemm<64, 1>(pb) : run_pipeline_gemm<128, 1>(pb);
+  if (pb.fft_impl == PTY_FFT_SPLIT_FP16) return pb.N == 64 ? run_pipeline_gemm<64, 2>(pb) : run_pipeline_gemm<128, 2>(pb);
+  if (pb.fft_impl == PTY_FFT_SPLIT3_BF16) return pb.N == 64 ? run_pipeline_gemm<64, 3>(pb) : run_pipeline_gemm<128, 3>(pb);
   switch (pb.N) {
     case 64: return run_pipeline<64>(pb);
     case 128: return run_pipeline<128>(pb);

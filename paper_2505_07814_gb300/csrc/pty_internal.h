@@ -28,6 +28,10 @@ struct Workspace {
   float2* gT;      // [Nz][H][W]      dL/dT accumulator
   float2* gPhat;   // [M][N*N]        probe-spectrum gradient accumulator (k-space)
   double* spart;   // [B][M][5]       per-wave {pos0, pos1, tilt0, tilt1, dz} gradient partials
+  // split-precision DFT modes only
+  float2* wave;    // [B][M][N*N]     current wave of every (position, mode)
+  float2* tmp;     // [B][M][N*N]     half-transformed waves (transposed per wave)
+  float* gscal;    // [4]             fp16 batch scaling: {max |x| bits, scale, -, -}
 };
 
 // MODE_FORWARD: patterns only.  MODE_FORWARD_SAVE: patterns, keeping in the workspace what a later
@@ -42,6 +46,7 @@ struct Problem {
   float p, eps;
   int grad_mask, global_tilt, accumulate, mode;
   int kstride;  // slices per recompute segment (1: every slice's checkpoint is stored)
+  int fft_impl;  // PTY_FFT_*
   const int32_t* idx;
   const float *amp, *phase, *pos, *tilt, *dz;
   const float2* probe;
@@ -64,6 +69,9 @@ size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspac
 // One pass of the hot path for FFT size N (instantiated in pty_n<N>.cu).  Returns a PTY_* code.
 template <int N>
 int run_pipeline(const Problem& pb);
+// The same pass with split-precision DFT-GEMMs (P = PTY_FFT_SPLIT_BF16 or _FP16; N = 64, 128).
+template <int N, int P>
+int run_pipeline_gemm(const Problem& pb);
 
 void set_error(const char* fmt, ...);
 

@@ -12,6 +12,8 @@ import torch
 from . import _lib
 
 LOSS = {"poisson": _lib.PTY_LOSS_POISSON, "gaussian": _lib.PTY_LOSS_GAUSSIAN}
+FFT_IMPL = {"fp32": _lib.PTY_FFT_FP32, "bf16": _lib.PTY_FFT_SPLIT_BF16, "fp16": _lib.PTY_FFT_SPLIT_FP16,
+            "bf16x3": _lib.PTY_FFT_SPLIT3_BF16}
 GRAD_BITS = {"amp": _lib.PTY_GRAD_AMP, "phase": _lib.PTY_GRAD_PHASE, "probe": _lib.PTY_GRAD_PROBE,
              "pos": _lib.PTY_GRAD_POS, "tilt": _lib.PTY_GRAD_TILT, "dz": _lib.PTY_GRAD_DZ}
 
@@ -32,6 +34,9 @@ class Geometry:
     grads: tuple = ("amp", "phase", "probe", "pos", "tilt", "dz")
     global_tilt: bool = False
     ckpt_stride: int = 1  # 1: checkpoint every slice; K > 1: re-run K-slice segments in the adjoint
+    # per-slice DFTs: "fp32" shared-memory FFT; split-precision tensor-core GEMMs "bf16" / "fp16"
+    # (hi + lo pieces, three products) or "bf16x3" (three bf16 pieces, six products)
+    fft: str = "fp32"
 
     @property
     def grad_mask(self) -> int:
@@ -43,12 +48,12 @@ class Geometry:
     def c(self) -> _lib.pty_geom:
         return _lib.pty_geom(self.N, self.M, self.Nz, self.H, self.W, self.Ntot, self.dx, self.lam,
                              LOSS[self.loss], self.p, self.eps, self.grad_mask, int(self.global_tilt),
-                             int(self.ckpt_stride))
+                             int(self.ckpt_stride), FFT_IMPL[self.fft])
 
     def checkpoint_bytes(self, B: int) -> int:
         """Bytes the adjoint's forward record takes for a batch of B positions (see ckpt_stride)."""
         wave = 8 * self.N * self.N * B * self.M
-        if self.ckpt_stride <= 1:
+        if self.ckpt_stride <= 1 or self.fft != "fp32":
             return wave * (2 * self.Nz - 1)
         K = min(self.ckpt_stride, self.Nz)
         return wave * ((self.Nz + K - 1) // K - 1 + 2 * K + 1)

@@ -42,7 +42,7 @@ def test_missing_library_fails_loudly(tmp_path):
 
 def _geom(**kw):
     g = dict(N=64, M=2, Nz=3, H=100, W=110, Ntot=12, dx=0.1, lambda_=0.0251, loss=0, p=0.0, eps=1e-6,
-             grad_mask=63, global_tilt=0, ckpt_stride=0)
+             grad_mask=63, global_tilt=0, ckpt_stride=0, fft_impl=0)
     g.update(kw)
     return _lib.pty_geom(**g)
 
@@ -53,10 +53,22 @@ def test_workspace_size_and_validation(lib):
     assert n >= 8 * 2 * 3 * 64 * 64 * 8
     assert lib.pty_workspace_size(ctypes.byref(_geom(grad_mask=_lib.PTY_GRAD_PROBE)), 8) < n
     for bad in (dict(N=32), dict(N=96), dict(N=512), dict(N=256, H=200), dict(M=0), dict(Nz=0), dict(H=63), dict(loss=7), dict(dx=0.0),
-                dict(grad_mask=64), dict(ckpt_stride=-1)):
+                dict(grad_mask=64), dict(ckpt_stride=-1), dict(fft_impl=4), dict(fft_impl=-1),
+                dict(N=256, H=300, W=300, fft_impl=1)):
         assert lib.pty_workspace_size(ctypes.byref(_geom(**bad)), 8) == 0, bad
         assert lib.pty_last_error()
     assert lib.pty_supported_sizes() == (1 << 6) | (1 << 7) | (1 << 8)
+
+
+def test_split_dft_workspace(lib):
+    """The split-precision DFT modes keep every slice's checkpoint and add two wave buffers."""
+    full = lib.pty_workspace_size(ctypes.byref(_geom(Nz=12, ckpt_stride=1)), 16)
+    for impl in (_lib.PTY_FFT_SPLIT_BF16, _lib.PTY_FFT_SPLIT_FP16, _lib.PTY_FFT_SPLIT3_BF16):
+        for K in (1, 4):
+            n = lib.pty_workspace_size(ctypes.byref(_geom(Nz=12, ckpt_stride=K, fft_impl=impl)), 16)
+            assert n >= full + 2 * 16 * 2 * 64 * 64 * 8
+            assert n <= full + 2 * 16 * 2 * 64 * 64 * 8 + 4096
+        assert lib.pty_workspace_size(ctypes.byref(_geom(N=128, H=200, W=200, fft_impl=impl)), 4) > 0
 
 
 def test_bad_arguments_rejected_before_launch(lib):
