@@ -342,14 +342,14 @@ struct GemmPass {
     }
     SplitLoader<N, P> ld{src, rows, sc};
     constexpr int K = S::kTerms * 2 * N;
-    const H* Bt = tables + (size_t)mat * 2 * N * K;
-    const dim3 grid(2 * N / GB_N, rows_pad / GB_M);
+    PlainLoader<H> lb{tables + (size_t)mat * 2 * N * K, (size_t)K, 2 * N};
+    const dim3 grid(2 * N / GB_N, rows_pad / GB_M, 1);
     if (transpose) {
-      k_gemm_tn<H, SplitLoader<N, P>, DftEpilogue<N, true>, true>
-          <<<grid, GB_THREADS, 0, st>>>(ld, Bt, K, K, DftEpilogue<N, true>{(float*)dst, rows, sc});
+      k_gemm_tn<H, SplitLoader<N, P>, PlainLoader<H>, DftEpilogue<N, true>, true>
+          <<<grid, GB_THREADS, 0, st>>>(ld, lb, K, K / GB_K, DftEpilogue<N, true>{(float*)dst, rows, sc});
     } else {
-      k_gemm_tn<H, SplitLoader<N, P>, DftEpilogue<N, false>, true>
-          <<<grid, GB_THREADS, 0, st>>>(ld, Bt, K, K, DftEpilogue<N, false>{(float*)dst, rows, sc});
+      k_gemm_tn<H, SplitLoader<N, P>, PlainLoader<H>, DftEpilogue<N, false>, true>
+          <<<grid, GB_THREADS, 0, st>>>(ld, lb, K, K / GB_K, DftEpilogue<N, false>{(float*)dst, rows, sc});
     }
     PTY_LAUNCH_CHECK("k_gemm_tn", -1);
     return PTY_OK;

@@ -1,11 +1,10 @@
 // gemm_mma.cuh -- tensor-core GEMM C = A * B^T with 16-bit operands (bf16 or fp16) and FP32
 // accumulation, for the split-precision DFT passes and the CNN layers.
 //
-// A is M x K and B is N x K, both K-contiguous ("TN": the layout mma.sync reads directly).  A is
-// produced by a loader functor (plain matrix, split-precision expansion of complex data, or an
-// implicit-GEMM gather of convolution patches), B is a plain 16-bit matrix, and each finished
-// 2-element pair of C goes to an epilogue functor.  M, N must be multiples of the CTA tile (128 x
-// 128) and K of 32; the callers guarantee it.
+// A is M x K and B is N x K, both K-contiguous ("TN": the layout mma.sync reads directly).  Both are
+// produced by loader functors (plain matrix, split-precision expansion of complex data, or an
+// implicit-GEMM gather of convolution patches or of their gradients), and each finished 2-element
+// pair of C goes to an epilogue functor.  K must be a multiple of 32 (the loaders pad with zeros).
 //
 // CTA tile 128 x 128 x 32, eight warps as 2 (M) x 4 (N), warp tile 64 x 32 = 4 x 4 mma.sync
 // m16n8k16 tiles; A and B tiles double-buffered in shared memory with an 80-byte row pitch (the
@@ -64,38 +63,42 @@ __device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
                : "r"(a));
 }
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(a), "l"(gmem));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// Plain A loader: 8 consecutive K elements of row m starting at k (16-byte aligned).
+// Plain operand loader: 8 consecutive K elements of row r starting at k (16-byte aligned); rows at
+// or beyond `rows` read as zero.
 template <class H>
 struct PlainLoader {
   const H* A;
-  size_t lda;
-  __device__ __forceinline__ uint4 operator()(int m, int k) const {
-    return *reinterpret_cast<const uint4*>(A + (size_t)m * lda + k);
+  size_t ld;
+  int rows;
+  __device__ __forceinline__ uint4 operator()(int r, int k) const {
+    if (r >= rows) return make_uint4(0u, 0u, 0u, 0u);
+    return __ldg(reinterpret_cast<const uint4*>(A + (size_t)r * ld + k));
   }
 };
 
-// C[M x N] = A[M x K] * B[N x K]^T.  grid = (N / 128, M / 128).
+// C[M x N] = A[M x K] * B[N x K]^T, A row m / B row n delivered 8 K-elements at a time by the
+// loaders.  grid = (ceil(N / 128), ceil(M / 128), splits): blockIdx.z takes K tiles
+// [z * kt_per, min((z + 1) * kt_per, K / 32)) (split-K; the epilogue then accumulates).  The loaders
+// return zeros outside the matrices and the epilogue discards what lies outside C.
+//
+// The next K tile is fetched into registers while the tensor cores work on the current one and
+// stored to the other shared-memory buffer afterwards (one barrier per K tile).
 //
 // PROMOTE: the tensor core's addition of each MMA's products into its FP32 accumulator does not
 // round like an IEEE FP32 add, and over a long K the error compounds (measured on the split DFTs:
 // it grew with K and with the number of split products).  With PROMOTE the products of each 32-wide
 // K tile are summed by the MMAs into a fresh register tile that is then added to the running sum
 // with an ordinary round-to-nearest FP32 add, so the long sum rounds like a plain FP32 dot product.
-template <class H, class Loader, class Epi, bool PROMOTE = false>
-__global__ void __launch_bounds__(GB_THREADS) k_gemm_tn(Loader load, const H* __restrict__ B, size_t ldb, int K,
-                                                        Epi epi) {
+template <class H, class LoadA, class LoadB, class Epi, bool PROMOTE = false>
+__global__ void __launch_bounds__(GB_THREADS) k_gemm_tn(LoadA la, LoadB lb, int K, int kt_per, Epi epi) {
   __shared__ __align__(16) H sA[2][GB_M * GB_PITCH];
   __shared__ __align__(16) H sB[2][GB_N * GB_PITCH];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int wm = warp / 4, wn = warp % 4;  // warp position: 2 x 4
   const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+  const int kt_all = K / GB_K;
+  const int kt0 = blockIdx.z * kt_per;
+  const int kt1 = kt0 + kt_per < kt_all ? kt0 + kt_per : kt_all;
   float acc[4][4][4];
   [[maybe_unused]] float part[PROMOTE ? 4 : 1][4][4];
 #pragma unroll
@@ -106,24 +109,35 @@ __global__ void __launch_bounds__(GB_THREADS) k_gemm_tn(Loader load, const H* __
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
 
   // each thread moves two 16-byte chunks of A and two of B per K tile (128 rows x 4 chunks)
-  auto fetch = [&](int buf, int k0) {
+  uint4 ra[2], rb[2];
+  auto fetch = [&](int k0) {
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int c = tid + h * GB_THREADS;  // 0..511
       const int r = c >> 2, kc = (c & 3) * 8;
-      *reinterpret_cast<uint4*>(&sA[buf][r * GB_PITCH + kc]) = load(m0 + r, k0 + kc);
-      cp_async16(&sB[buf][r * GB_PITCH + kc], B + (size_t)(n0 + r) * ldb + k0 + kc);
+      ra[h] = la(m0 + r, k0 + kc);
+      rb[h] = lb(n0 + r, k0 + kc);
     }
-    cp_async_commit();
+  };
+  auto stash = [&](int buf) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = tid + h * GB_THREADS;
+      const int r = c >> 2, kc = (c & 3) * 8;
+      *reinterpret_cast<uint4*>(&sA[buf][r * GB_PITCH + kc]) = ra[h];
+      *reinterpret_cast<uint4*>(&sB[buf][r * GB_PITCH + kc]) = rb[h];
+    }
   };
 
-  const int ktiles = K / GB_K;
-  fetch(0, 0);
-  for (int kt = 0; kt < ktiles; ++kt) {
-    const int buf = kt & 1;
-    cp_async_wait0();
-    __syncthreads();
-    if (kt + 1 < ktiles) fetch(buf ^ 1, (kt + 1) * GB_K);
+  if (kt0 < kt1) {
+    fetch(kt0 * GB_K);
+    stash(0);
+  }
+  __syncthreads();
+  for (int kt = kt0; kt < kt1; ++kt) {
+    const int buf = (kt - kt0) & 1;
+    const bool more = kt + 1 < kt1;
+    if (more) fetch((kt + 1) * GB_K);  // in flight during the MMAs below
 #pragma unroll
     for (int kk = 0; kk < GB_K; kk += 16) {
       uint32_t af[4][4], bf[4][2];
@@ -168,6 +182,9 @@ __global__ void __launch_bounds__(GB_THREADS) k_gemm_tn(Loader load, const H* __
 #pragma unroll
           for (int q = 0; q < 4; ++q) acc[i][j][q] += part[i][j][q];
     }
+    // the other buffer was last read in the previous iteration, before this iteration's barrier
+    if (more) stash(buf ^ 1);
+    __syncthreads();
   }
   // epilogue: thread holds C(row, col..col+1) and C(row+8, col..col+1) of every 16 x 8 tile
   const int g = lane >> 2, t4 = lane & 3;
