@@ -127,7 +127,7 @@ def conv_backward(x, w, stride, up, dz):
         for kx in range(3):
             sl = (slice(None), slice(ky, ky + stride * (OH - 1) + 1, stride),
                   slice(kx, kx + stride * (OW - 1) + 1, stride), slice(None))
-            dw[:, ky, kx, :] = np.einsum("bhwo,bhwc->oc", dz, up_[sl])
+            dw[:, ky, kx, :] = np.tensordot(dz, up_[sl], axes=([0, 1, 2], [0, 1, 2]))
             du_[sl] += dz @ w[:, ky, kx, :]
     db = dz.sum(axis=(0, 1, 2))
     dx = block_sum(du_[:, 1:H + 1, 1:W + 1, :], up)

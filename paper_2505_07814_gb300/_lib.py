@@ -34,7 +34,9 @@ PTY_FFT_FP32, PTY_FFT_SPLIT_BF16, PTY_FFT_SPLIT_FP16, PTY_FFT_SPLIT3_BF16 = 0, 1
 # Every symbol include/pty.h declares (checked by the CPU test suite).
 EXPORTS = ("pty_workspace_size", "pty_forward", "pty_loss_grad", "pty_adam_update", "pty_step",
            "pty_status", "pty_last_error", "pty_supported_sizes", "pty_launch_count", "pty_profile_enable",
-           "pty_profile_read", "pty_loss_grad_noalloc", "pty_forward_save", "pty_backward")
+           "pty_profile_read", "pty_loss_grad_noalloc", "pty_forward_save", "pty_backward",
+           "pty_cnn_param_count", "pty_cnn_workspace_size", "pty_cnn_forward", "pty_cnn_loss_grad", "pty_cnn_adam",
+           "pty_cnn_train_step", "pty_cnn_targets", "pty_cnn_stitch", "pty_cnn_stitch_finish", "pty_cnn_read_state")
 PROF_STAGES = ("prepare_object", "probe_spectrum", "forward", "loss", "loss_finalize", "adjoint", "object_grad",
                "probe_grad", "scalar_grad")
 
@@ -104,6 +106,27 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pty_profile_enable.restype = I
     lib.pty_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), I]
     lib.pty_profile_read.restype = I
+    F = ctypes.c_float
+    lib.pty_cnn_param_count.argtypes = []
+    lib.pty_cnn_param_count.restype = SZ
+    lib.pty_cnn_workspace_size.argtypes = [I, I]
+    lib.pty_cnn_workspace_size.restype = SZ
+    lib.pty_cnn_forward.argtypes = [I, I, P, P, F, P, P, SZ, P]
+    lib.pty_cnn_forward.restype = I
+    lib.pty_cnn_loss_grad.argtypes = [I, I, P, P, P, F, P, P, P, P, SZ, P]
+    lib.pty_cnn_loss_grad.restype = I
+    lib.pty_cnn_adam.argtypes = [P, P, P, P, I, F, F, F, F, P]
+    lib.pty_cnn_adam.restype = I
+    lib.pty_cnn_train_step.argtypes = [I, I, P, P, P, P, I, F, P, P, F, P, P, SZ, P]
+    lib.pty_cnn_train_step.restype = I
+    lib.pty_cnn_targets.argtypes = [I, I, I, I, P, P, P, P, I, P, P]
+    lib.pty_cnn_targets.restype = I
+    lib.pty_cnn_stitch.argtypes = [I, I, I, P, P, P, I, P, P, P, P]
+    lib.pty_cnn_stitch.restype = I
+    lib.pty_cnn_stitch_finish.argtypes = [I, I, I, P, P, P, P, P]
+    lib.pty_cnn_stitch_finish.restype = I
+    lib.pty_cnn_read_state.argtypes = [I, I, P, SZ, I, I, P, P]
+    lib.pty_cnn_read_state.restype = I
     _lib = lib
     return lib
 
@@ -189,3 +212,47 @@ def pty_loss_grad_noalloc(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas
     _check(load().pty_loss_grad_noalloc(ctypes.byref(geom), B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss,
                                         I_model, g_amp, g_phase, g_probe, g_pos, g_tilt, g_dz, int(accumulate),
                                         status, stream))
+
+
+# ---- learned initialiser (include/pty_cnn.h) ----
+def pty_cnn_param_count() -> int:
+    return load().pty_cnn_param_count()
+
+
+def pty_cnn_workspace_size(S: int, B: int) -> int:
+    n = load().pty_cnn_workspace_size(S, B)
+    if n == 0:
+        raise PtyError(PTY_EINVAL, load().pty_last_error().decode())
+    return n
+
+
+def pty_cnn_forward(S, B, params, I, s_in, pred, ws, ws_bytes, stream):
+    _check(load().pty_cnn_forward(S, B, params, I, s_in, pred, ws, ws_bytes, stream))
+
+
+def pty_cnn_loss_grad(S, B, params, I, Y, s_in, loss, grad, pred, ws, ws_bytes, stream):
+    _check(load().pty_cnn_loss_grad(S, B, params, I, Y, s_in, loss, grad, pred, ws, ws_bytes, stream))
+
+
+def pty_cnn_adam(params, m, v, grad, step, lr, beta1, beta2, eps, stream):
+    _check(load().pty_cnn_adam(params, m, v, grad, step, lr, beta1, beta2, eps, stream))
+
+
+def pty_cnn_train_step(S, B, params, m, v, grad, step, lr, I, Y, s_in, loss, ws, ws_bytes, stream):
+    _check(load().pty_cnn_train_step(S, B, params, m, v, grad, step, lr, I, Y, s_in, loss, ws, ws_bytes, stream))
+
+
+def pty_cnn_targets(S, Nz, H, W, amp, phase, pos, idx, B, Y, stream):
+    _check(load().pty_cnn_targets(S, Nz, H, W, amp, phase, pos, idx, B, Y, stream))
+
+
+def pty_cnn_stitch(S, H, W, pred, pos, idx, B, weight, num, den, stream):
+    _check(load().pty_cnn_stitch(S, H, W, pred, pos, idx, B, weight, num, den, stream))
+
+
+def pty_cnn_stitch_finish(Nz, H, W, num, den, amp, phase, stream):
+    _check(load().pty_cnn_stitch_finish(Nz, H, W, num, den, amp, phase, stream))
+
+
+def pty_cnn_read_state(S, B, ws, ws_bytes, layer, what, out, stream):
+    _check(load().pty_cnn_read_state(S, B, ws, ws_bytes, layer, what, out, stream))

@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI that need no GPU: the library builds for sm_103a, loads, exports
-every function include/pty.h declares, and rejects bad arguments before launching anything."""
+every function include/*.h declares, and rejects bad arguments before launching anything."""
 import ctypes
 import os
 import re
@@ -18,9 +18,13 @@ def lib():
 
 
 def _declared_functions():
-    src = open(os.path.join(ROOT, "include", "pty.h")).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pty_[a-z_]+)\s*\(", src)))
+    names = set()
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(pty_[a-z_]+)\s*\(", src))
+    return sorted(names)
 
 
 def test_exports_every_declared_symbol(lib):
