@@ -263,6 +263,76 @@ def sweep_ckpt(args, w, geometry, params, I_meas, idx_t, flush, dev, torch, Ptyc
         torch.cuda.empty_cache()
 
 
+def run_nmse(args):
+    """Time to object NMSE <= target on the multislice workload (object seed 1234, measured counts
+    simulated by the forward model): the flat start (Sec. "Preprocessing and initialization") with
+    FP32 FFTs and with split-precision DFT-GEMMs, against the start stitched from the learned
+    initialiser's predictions (network trained on 65536 pairs from 16 other random volumes).  Adam
+    on the object phase only (probe, positions, tilt, dz at the truth), batch 64, each start at the
+    better of two phase learning rates.  Times are GPU seconds of reconstruction (and of inference +
+    stitching for the learned start), NMSE evaluation excluded."""
+    import torch
+
+    from paper_2505_07814_gb300 import _lib, build
+    from paper_2505_07814_gb300 import learned_init as L
+    from paper_2505_07814_gb300.cnn import Cnn
+
+    build.build()
+    _lib.load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    target, batch, lrs = args.nmse_target, 64, (1e-3, 3e-3)
+    prob = L.problem("c2")
+    amp_f, ph_f = L.flat_object(prob)
+
+    def best(amp0, ph0, fft="fp32", iters=6):
+        runs = []
+        for lr in lrs:
+            hist, _ = L.reconstruct(prob, amp0, ph0, iters=iters, batch=batch, lr={"phase": lr}, target=target, fft=fft)
+            it, e, t = hist[-1]
+            runs.append({"lr_phase": lr, "reached": e <= target, "iterations": it, "nmse": e, "seconds": t,
+                         "nmse_start": hist[0][1]})
+        ok = [r for r in runs if r["reached"]]
+        return (min(ok, key=lambda r: r["seconds"]) if ok else None), runs
+
+    L.reconstruct(prob, amp_f, ph_f, iters=1, batch=batch, lr={"phase": lrs[0]}, target=1.0)  # warm-up
+    flat, flat_runs = best(amp_f, ph_f)
+    split = {}
+    for fft in args.nmse_split.split(",") if args.nmse_split else []:
+        split[fft] = best(amp_f, ph_f, fft=fft)[0]
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    I, Y = L.training_set(prob, n_objects=16, per_object=4096)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    net = Cnn(S=128, max_batch=256)
+    ev0.record()
+    losses = L.train(net, I, Y, epochs=args.nmse_epochs, batch=256, lr=1e-3)
+    ev1.record()
+    ev1.synchronize()
+    train_s = ev0.elapsed_time(ev1) / 1e3
+    del I, Y
+    L.initial_object(net, prob)  # warm-up
+    ev0.record()
+    amp_c, ph_c = L.initial_object(net, prob)
+    ev1.record()
+    ev1.synchronize()
+    infer_s = ev0.elapsed_time(ev1) / 1e3
+    learned, learned_runs = best(amp_c, ph_c)
+    value = learned["seconds"] + infer_s if learned else None
+    line = {"metric": "time to object NMSE <= %g (learned start vs flat start, 1 GB300)" % target, "value": value,
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
+            "config": {"workload": WORKLOADS["c2"][0] + ", measured counts from the forward model (dose 1e5)",
+                       "batch": batch, "optimiser": "Adam, object phase only", "nmse": "depth-summed phase, ROI of the "
+                       "window centres, offset removed", "lr_grid_phase": list(lrs)},
+            "flat_fp32": flat, "flat_runs": flat_runs, "split_precision_flat": split,
+            "learned": dict(learned or {}, inference_stitch_seconds=infer_s), "learned_runs": learned_runs,
+            "training": {"pairs": 65536, "objects": 16, "epochs": args.nmse_epochs, "batch": 256,
+                         "generation_seconds": gen_s, "training_seconds": train_s, "epoch_losses": losses},
+            "speedup_vs_flat": (flat["seconds"] / value) if (flat and value) else None}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -278,7 +348,15 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nmse", action="store_true",
+                    help="time to object NMSE: flat start vs learned initialiser (and split precision)")
+    ap.add_argument("--nmse-target", type=float, default=0.05)
+    ap.add_argument("--nmse-epochs", type=int, default=8)
+    ap.add_argument("--nmse-split", default="bf16,fp16", help="split-precision forms to time from the flat start")
     args = ap.parse_args()
+    if args.nmse:
+        run_nmse(args)
+        return
     if args.batch <= 0:
         args.batch = WORKLOADS[args.workload][1]
     rank = int(os.environ.get("RANK", "0"))
