@@ -160,6 +160,20 @@ def batch_indices(step, B, Ntot):
     return [(s + i) % Ntot for i in range(B)]
 
 
+def rank_batches(rank, world, B, Ntot, n=8):
+    """The n position batches rank `rank` of `world` takes: global batches rank, rank + world, ... of
+    contiguous raster blocks (weak scaling: every rank its own blocks, no collective on the data path)."""
+    return [batch_indices(k * world + rank, B, Ntot) for k in range(n)]
+
+
+def max_over_ranks(value, dist, device):
+    """The largest `value` over all ranks (the job's time is its slowest rank's)."""
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
 def row_runs(idx):
     """Maximal runs [lo, hi) of consecutive indices (a contiguous batch that wraps gives two)."""
     runs, lo = [], idx[0] if idx else 0
@@ -385,7 +399,7 @@ def main():
     B = args.batch
     Ntot = _ntot(args.workload)
     # each rank takes its own batches (weak scaling: independent position blocks, no collective)
-    idx_h = [batch_indices(k * world + rank, B, Ntot) for k in range(8)]
+    idx_h = rank_batches(rank, world, B, Ntot)
     w, amp0, phase0, I_rows, row_of = make_inputs(args.workload, [p for b in idx_h for p in b])
     f32 = dict(dtype=torch.float32, device=dev)
     params = Params(amp=torch.tensor(amp0, **f32), phase=torch.tensor(phase0, **f32),
@@ -438,9 +452,7 @@ def main():
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
     if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = t.item()
+        total_ms = max_over_ranks(total_ms, dist, dev)
     upd_step = B * w.M * w.Nz
     value = world * upd_step * args.steps / (total_ms / 1e3)
 
