@@ -1,0 +1,186 @@
+"""Parity at full size, in the launch configurations the benchmark times.
+
+Multislice workload (N = 128, M = 6, Nz = 8, object 8 x 512 x 512, 4096 positions) with one
+512-position batch, exactly the benchmark's first batch and kernel configuration.  The point of
+evaluation is the workload's own object (not the flat start, where the position, tilt and dz
+gradients vanish), against synthetic measured patterns.
+  * every modelled pattern of the batch and the loss against the oracle (rel. L2 <= 1e-5);
+  * sampled per-position outputs the oracle computes one position at a time: position and tilt
+    gradients of sampled positions, and the object gradient at pixels that only one position of
+    the batch reaches.  With the Poisson loss L = -sum(d log I - I) / sum(d) over the batch, a
+    single-position oracle call differs only in the normaliser, so it is rescaled by
+    sum_j(d) / sum_batch(d) (rel. L2 <= 1e-4);
+  * the gradients that sum over all positions (probe, dz) by central differences of the GPU
+    forward (FP64 loss on the host), h = 1e-3 along a random direction.
+
+Large-window workload (N = 256 on four-CTA clusters, M = 12, Nz = 20, object 20 x 1024 x 1024):
+the oracle on a 16-position subset for every output, and central differences of 32 entries drawn at
+random from the largest-magnitude gradient entries of each kind (single entries with tiny
+gradients change an FP32 loss by less than its rounding).
+"""
+import numpy as np
+import pytest
+
+from oracle import ptycho as O
+from paper_2505_07814_gb300 import synth
+from tests.cases import c64, f32, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+NAMES = ("amp", "phase", "probe", "pos", "tilt", "dz")
+# Large-window subset: the object gradients sum conj(psi) g over 16 positions x 12 modes, with g
+# driven by the Poisson weight d / I; on dark-field pixels (I orders of magnitude below the
+# bright field) the FP32 forward's absolute error becomes a large relative error of I that this
+# weight passes on.  Measured: 2.2e-4 on both object gradients here (1.0e-4 with 4 slices, 7.4e-4
+# with 2 modes, where the patterns are darker); every other output stays below 1e-4.
+TOL_C3 = {"amp": 3e-4, "phase": 3e-4}
+
+
+def _setup(w, idx, B, I_meas):
+    from paper_2505_07814_gb300.ptycho import Geometry, Params, Ptycho
+    geom = Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, Ntot=w.Ntot, dx=w.dx, lam=float(np.float32(w.lam)),
+                    loss="poisson")
+    dev = torch.device("cuda")
+    t32 = dict(dtype=torch.float32, device=dev)
+    params = Params(amp=torch.tensor(w.amp, **t32), phase=torch.tensor(w.phase, **t32),
+                    probe=torch.tensor(w.probe, dtype=torch.complex64, device=dev), pos=torch.tensor(w.pos, **t32),
+                    tilt=torch.tensor(w.tilt, **t32), dz=torch.tensor([w.dz], **t32))
+    return Ptycho(geom, B, device=dev), params, torch.tensor(I_meas, **t32)
+
+
+def _rounded(w):
+    """The workload with every input rounded to what the GPU receives."""
+    w.amp, w.phase, w.pos, w.tilt = f32(w.amp), f32(w.phase), f32(w.pos), f32(w.tilt)
+    w.probe = c64(w.probe)
+    w.dz = float(np.float32(w.dz))
+    return w
+
+
+def _np(t):
+    return t.detach().cpu().numpy()
+
+
+def _oracle_geom(w):
+    return O.Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, dx=w.dx, lam=float(np.float32(w.lam)), loss=O.POISSON)
+
+
+def _loss_at(pt, params, idx, Im, g):
+    return O.loss_value(g, _np(pt.forward(params, idx)).astype(np.float64), Im)
+
+
+def _shifted(params, name, delta):
+    q = params.zeros_like()
+    for n in NAMES:
+        getattr(q, n).copy_(getattr(params, n))
+    getattr(q, name).add_(delta)
+    return q
+
+
+def test_multislice_batch_512_matches_oracle():
+    w = _rounded(synth.workload("c2"))
+    B = 512
+    idx = list(range(B))  # the benchmark's first batch: raster positions 0..511
+    I_meas = np.zeros((w.Ntot, w.N, w.N), dtype=np.float32)
+    I_meas[:B] = synth.vacuum_patterns(w.probe, B)
+    I_meas = f32(I_meas)
+    pt, params, I_t = _setup(w, idx, B, I_meas)
+    I_model = torch.empty((B, w.N, w.N), dtype=torch.float32, device="cuda")
+    loss, grads = pt.loss_grad(params, idx, I_t, I_model=I_model)
+    torch.cuda.synchronize()
+    assert pt.status() == 0
+    g = _oracle_geom(w)
+    ref_I = O.model_patterns(g, w.amp, w.phase, w.probe, w.pos, w.tilt, w.dz, idx)
+    assert rel_l2(_np(I_model), ref_I) <= 1e-5
+    ref_loss = O.loss_value(g, ref_I, I_meas[idx])
+    assert abs(loss.item() - ref_loss) <= 1e-5 * abs(ref_loss)
+
+    d_batch = float(I_meas[idx].sum())
+    corners = np.array([O.crop_index(w.pos[j])[0] for j in idx])
+    sampled = [0, 257, 511]
+    got_pt, ref_pt = [], []
+    for j in sampled:
+        r = O.loss_and_grad(g, w.amp, w.phase, w.probe, w.pos, w.tilt, w.dz, I_meas, [j])
+        s = float(I_meas[j].sum()) / d_batch
+        got_pt += [_np(grads.pos)[j], _np(grads.tilt)[j]]
+        ref_pt += [s * r.pos[j], s * r.tilt[j]]
+        if j == 0:
+            # pixels of position 0's window that no other position of the batch reaches
+            cover = np.zeros((w.H, w.W), dtype=np.int32)
+            for c0, c1 in corners:
+                cover[c0:c0 + w.N, c1:c1 + w.N] += 1
+            c0, c1 = corners[0]
+            mask = np.zeros((w.H, w.W), dtype=bool)
+            mask[c0:c0 + w.N, c1:c1 + w.N] = cover[c0:c0 + w.N, c1:c1 + w.N] == 1
+            assert mask.sum() >= 16  # the 4 x 4 corner the raster step leaves to position 0, in every slice
+            for name in ("amp", "phase"):
+                got = _np(getattr(grads, name))[:, mask]
+                exp = s * getattr(r, name)[:, mask]
+                assert rel_l2(got, exp) <= 1e-4, (name, rel_l2(got, exp))
+    assert rel_l2(np.array(got_pt), np.array(ref_pt)) <= 1e-4
+
+    # probe and dz: central differences of the GPU forward along random directions
+    Im = I_meas[idx].astype(np.float64)
+    h = 1e-3
+    rng = np.random.default_rng(70)
+    x = params.probe
+    d = torch.tensor(rng.standard_normal(x.shape) + 1j * rng.standard_normal(x.shape), dtype=torch.complex64,
+                     device="cuda") * x.abs().mean()
+    fd = (_loss_at(pt, _shifted(params, "probe", h * d), idx, Im, g) -
+          _loss_at(pt, _shifted(params, "probe", -h * d), idx, Im, g)) / (2 * h)
+    an = float((grads.probe * d.conj()).real.sum())
+    assert abs(fd - an) <= 1e-2 * abs(an), ("probe", fd, an)
+    dd = torch.full((1,), h, device="cuda")
+    fd = (_loss_at(pt, _shifted(params, "dz", dd), idx, Im, g) - _loss_at(pt, _shifted(params, "dz", -dd), idx, Im,
+                                                                           g)) / (2 * h)
+    an = float(_np(grads.dz)[0])
+    assert abs(fd - an) <= 1e-2 * abs(an), ("dz", fd, an)
+
+
+def test_large_window_subset_matches_oracle_and_differences():
+    w = _rounded(synth.workload("c3"))
+    rng = np.random.default_rng(1238)
+    idx = sorted(int(j) for j in rng.choice(w.Ntot, 16, replace=False))
+    B = len(idx)
+    # measured patterns: Poisson counts of the oracle's own model of a slightly different object
+    g = _oracle_geom(w)
+    amp_t = f32(w.amp * (1.0 + 0.02 * rng.standard_normal(w.amp.shape)))
+    I_meas = np.zeros((w.Ntot, w.N, w.N), dtype=np.float32)
+    I_meas[idx] = synth.poisson_counts(O.model_patterns(g, amp_t, w.phase, w.probe, w.pos, w.tilt, w.dz, idx))
+    I_meas = f32(I_meas)
+    pt, params, I_t = _setup(w, idx, B, I_meas)
+    loss, grads = pt.loss_grad(params, idx, I_t)
+    torch.cuda.synchronize()
+    assert pt.status() == 0
+    ref = O.loss_and_grad(g, w.amp, w.phase, w.probe, w.pos, w.tilt, w.dz, I_meas, idx)
+    assert abs(loss.item() - ref.loss) <= 1e-5 * abs(ref.loss)
+    for n in NAMES:
+        got = _np(getattr(grads, n))
+        err = rel_l2(got[0] if n == "dz" else got, getattr(ref, n))
+        assert err <= TOL_C3.get(n, 1e-4), (n, err)
+
+    # 32 central differences of the GPU forward (FP64 loss on the host), entries drawn from the
+    # largest gradients of each kind.  h = 1e-3 for the object, probe and dz; a single position or
+    # tilt entry moves this loss by less than the FP32 rounding of the intensities at h = 1e-3, so
+    # those use h = 0.05 px and h = 1e-4 rad (their values are pinned by the oracle above).
+    Im = I_meas[idx].astype(np.float64)
+    entries = []
+    for name, k, parts, h in (("amp", 8, (1.0,), 1e-3), ("phase", 8, (1.0,), 1e-3), ("probe", 4, (1.0, 1j), 1e-3),
+                              ("pos", 4, (1.0,), 0.05), ("tilt", 3, (1.0,), 1e-4), ("dz", 1, (1.0,), 1e-3)):
+        gv = _np(getattr(grads, name))
+        top = np.argsort(np.abs(gv).ravel())[::-1][:200 if name in ("amp", "phase", "probe") else k]
+        for e in rng.choice(top, size=k, replace=False):
+            for part in parts:
+                entries.append((name, np.unravel_index(int(e), gv.shape), part, h))
+    assert len(entries) == 32
+    bad = []
+    for name, e, part, h in entries:
+        dlt = torch.zeros_like(getattr(params, name))
+        dlt[e] = h * part
+        fd = (_loss_at(pt, _shifted(params, name, dlt), idx, Im, g) -
+              _loss_at(pt, _shifted(params, name, -dlt), idx, Im, g)) / (2 * h)
+        gv = _np(getattr(grads, name))[e]
+        an = float(np.real(gv)) if part == 1.0 else float(np.imag(gv))
+        if abs(fd - an) > 2e-2 * abs(an) + 1e-9:
+            bad.append((name, e, part, fd, an))
+    assert not bad, bad
