@@ -173,7 +173,7 @@ int pty_step(const pty_geom* geom, int B, const int32_t* idx, float* amp, float*
              float* g_dz, const pty_adam* adam, int step, void* ws, size_t ws_bytes, void* stream);
 
 /* Synchronises `stream` and returns the OR of the device status bits (PTY_EBOUNDS,
- * PTY_ENONFINITE) set since the last call that used this workspace began; a negative value if the
+ * PTY_ENONFINITE, PTY_ETIMEOUT) set since the last call that used this workspace began; a negative value if the
  * status could not be read.  Each pty_forward / pty_loss_grad / pty_step clears the word first. */
 int pty_status(const void* ws, void* stream);
 

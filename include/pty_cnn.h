@@ -26,7 +26,9 @@
  * All pointers are device pointers unless stated; arrays must be 16-byte aligned.  Calls are
  * asynchronous on `stream` (a cudaStream_t, NULL = legacy default stream) and return PTY_OK or a
  * PTY_* code from pty.h with the reason in pty_last_error(); arguments are checked before any
- * launch.  S must be a multiple of 16 between 16 and 512. */
+ * launch.  S must be a multiple of 16 between 16 and 512.  The workspace starts with a status word
+ * that pty_status() (pty.h) reads: PTY_ETIMEOUT if a tensor-core pipeline wait gave up (the
+ * outputs of that call are then invalid). */
 #ifndef PTY_CNN_H
 #define PTY_CNN_H
 

@@ -1,13 +1,17 @@
 // cnn.cu -- the learned initialiser of include/pty_cnn.h: bf16 implicit-GEMM convolutions on the
-// tensor cores (forward, input gradient, weight gradient), the two-channel output layer on the CUDA
-// cores, the loss, Adam, training targets and stitching.
+// tensor cores (tcgen05 with TMEM accumulators, gemm_tc.cuh: forward, input gradient, weight
+// gradient), the two-channel output layer on the CUDA cores, the loss, Adam, training targets and
+// stitching.
 //
 // Layout: activations channels-last [B][H][W][C] in bf16, so one 16-byte load gathers 8 channels of
 // one tap.  GEMM views (rows x cols, reduction K):
 //   forward    z[pixel][oc]   = sum_k col[pixel][k] W[oc][k],        k = (ky, kx, ic)
 //   dgrad      du[pixel][ic]  = sum_k' dz[pixel'(k')][oc] Wt[ic][k'], k' = (ky, kx, oc), pixels of the
 //                                (upsampled) input grid; pixel' is the output that reads it by tap
-//   wgrad      dW[oc][k]      = sum_pixels dz[pixel][oc] col[pixel][k] (split over pixels, float atomics)
+//   wgrad      dW[oc][k]      = sum_pixels dz[pixel][oc] col[pixel][k]: dz and the im2col matrix are
+//                                first transposed to pixel-contiguous rows (chunks of at most 2^18
+//                                pixels), then one plain GEMM per chunk, split over pixels with
+//                                float atomics
 // Layer 6 (upsampling x4, 2 output channels) would waste 126 of 128 GEMM columns, so it runs on the
 // CUDA cores: nearest upsampling makes every output pixel read, for each tap, one low-resolution
 // pixel, so the per-tap channel sums P[p][tap][o] = sum_c W[o][tap][c] a5[p][c] are formed once per
@@ -20,6 +24,7 @@
 #include <string.h>
 
 #include "gemm_mma.cuh"
+#include "gemm_tc.cuh"
 #include "pty_cnn.h"
 #include "pty_internal.h"
 
@@ -37,8 +42,9 @@ constexpr LayerDef kNet[kLayers] = {{1, 48, 2, 1}, {48, 96, 2, 1}, {96, 192, 2, 
 constexpr int kOut = 2;     // output channels
 constexpr int kTaps6 = 18;  // layer 6: 9 taps x 2 output channels
 constexpr int kC6 = 256;    // layer 6 input channels
+constexpr int kPixChunk = 1 << 18;  // output pixels per weight-gradient chunk
 
-__host__ __device__ constexpr int round32(int x) { return (x + 31) / 32 * 32; }
+__host__ __device__ constexpr int round64(int x) { return (x + 63) / 64 * 64; }
 
 // ---------------------------------------------------------------------------------------------
 // Plan: per-layer sizes and workspace offsets for patterns of S x S and batches of B
@@ -49,7 +55,9 @@ struct Plan {
   size_t woff[kLayers], boff[kLayers];           // offsets of weights / biases in the parameters
   int kp[kLayers], ktp[kLayers];                 // padded K of the forward and dgrad GEMMs
   // workspace pieces (byte offsets)
-  size_t wp[kLayers], wt[kLayers], w6, act[kLayers], dz[kLayers + 1], p6, dp6, du5, lpart, total;
+  size_t status, wp[kLayers], wt[kLayers], w6, act[kLayers], dz[kLayers + 1], p6, dp6, du5, lpart, colt, dzt,
+      total;
+  int pchunk[kLayers];  // pixels per weight-gradient chunk (multiple of 64)
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -71,8 +79,8 @@ static bool make_plan(int S, int B, Plan* pl) {
     o += (size_t)9 * kNet[l].ic * kNet[l].oc;
     p.boff[l] = o;
     o += kNet[l].oc;
-    p.kp[l] = round32(9 * kNet[l].ic);
-    p.ktp[l] = round32(9 * kNet[l].oc);
+    p.kp[l] = round64(9 * kNet[l].ic);
+    p.ktp[l] = round64(9 * kNet[l].oc);
   }
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -80,6 +88,7 @@ static bool make_plan(int S, int B, Plan* pl) {
     off += align256(bytes);
     return r;
   };
+  p.status = take(sizeof(int) * 64);
   for (int l = 0; l < 5; ++l) {
     p.wp[l] = take(sizeof(bf16) * kNet[l].oc * p.kp[l]);
     if (l > 0) p.wt[l] = take(sizeof(bf16) * kNet[l].ic * p.ktp[l]);
@@ -93,6 +102,18 @@ static bool make_plan(int S, int B, Plan* pl) {
   p.dp6 = take(sizeof(float) * lowres * kTaps6);
   p.du5 = take(sizeof(float) * (size_t)B * p.hu[4] * p.hu[4] * kNet[4].ic);
   p.lpart = take(sizeof(double) * 1024);
+  // weight gradients run over chunks of at most kPixChunk output pixels, with the im2col matrix and
+  // dL/dz transposed to pixel-contiguous rows
+  size_t colt = 0, dzt = 0;
+  for (int l = 0; l < 5; ++l) {
+    const size_t pix = (size_t)B * p.hout[l] * p.hout[l];
+    p.pchunk[l] = (int)((pix < (size_t)kPixChunk ? (pix + 63) / 64 * 64 : (size_t)kPixChunk));
+    if (p.pchunk[l] < 64) p.pchunk[l] = 64;
+    colt = colt > (size_t)9 * kNet[l].ic * p.pchunk[l] ? colt : (size_t)9 * kNet[l].ic * p.pchunk[l];
+    dzt = dzt > (size_t)kNet[l].oc * p.pchunk[l] ? dzt : (size_t)kNet[l].oc * p.pchunk[l];
+  }
+  p.colt = take(sizeof(bf16) * colt);
+  p.dzt = take(sizeof(bf16) * dzt);
   p.total = off;
   *pl = p;
   return true;
@@ -197,6 +218,44 @@ struct Im2col {
     if (uy < 0 || uy >= hu || ux < 0 || ux >= hu) return make_uint4(0u, 0u, 0u, 0u);
     return __ldg(reinterpret_cast<const uint4*>(a + (((size_t)b * hin + uy / up) * hin + ux / up) * ic + c0));
   }
+  // cursor: the output pixel decoded once, (tap, channel) stepped through K
+  struct Cursor {
+    const bf16* img;  // sample b of the input, or nullptr past the last row
+    int y0, x0;       // stride * (oy, ox) - 1 on the upsampled grid
+    int ky, kx, c0;
+  };
+  __device__ __forceinline__ Cursor cursor(int m, int k) const {
+    Cursor c;
+    c.img = nullptr;
+    c.y0 = c.x0 = 0;
+    if (m < B * hout * hout) {
+      const int b = m / (hout * hout), rem = m % (hout * hout);
+      c.img = a + (size_t)b * hin * hin * ic;
+      c.y0 = stride * (rem / hout) - 1;
+      c.x0 = stride * (rem % hout) - 1;
+    }
+    const int tap = k / ic;
+    c.ky = tap / 3;
+    c.kx = tap % 3;
+    c.c0 = k - tap * ic;
+    return c;
+  }
+  __device__ __forceinline__ uint4 load(const Cursor& c) const {
+    const int uy = c.y0 + c.ky, ux = c.x0 + c.kx;
+    if (!c.img || c.ky > 2 || uy < 0 || uy >= hu || ux < 0 || ux >= hu) return make_uint4(0u, 0u, 0u, 0u);
+    const int sh = up == 2 ? 1 : 0;  // up is 1 or 2 for the layers that gather this way
+    return __ldg(reinterpret_cast<const uint4*>(c.img + ((size_t)(uy >> sh) * hin + (ux >> sh)) * ic + c.c0));
+  }
+  __device__ __forceinline__ void advance(Cursor& c, int dk) const {
+    c.c0 += dk;
+    while (c.c0 >= ic) {
+      c.c0 -= ic;
+      if (++c.kx == 3) {
+        c.kx = 0;
+        ++c.ky;
+      }
+    }
+  }
 };
 
 // Input gradient of layers 2..5: rows = pixels of the upsampled input grid, k' = (tap, oc); the
@@ -214,49 +273,44 @@ struct DgradGather {
     if (oy >= hout || ox >= hout) return make_uint4(0u, 0u, 0u, 0u);
     return __ldg(reinterpret_cast<const uint4*>(dz + (((size_t)b * hout + oy) * hout + ox) * oc + o0));
   }
-};
-
-// Weight gradient, A operand: row oc, 8 consecutive pixels of dz (channel stride oc).
-struct DzRows {
-  const bf16* dz;  // [pixels][oc]
-  int pixels, oc;
-  __device__ __forceinline__ uint4 operator()(int o, int m) const {
-    Pack8 r;
-    r.u = make_uint4(0u, 0u, 0u, 0u);
-    if (o >= oc) return r.u;
-#pragma unroll
-    for (int e = 0; e < 8; ++e)
-      if (m + e < pixels) r.h[e] = dz[(size_t)(m + e) * oc + o];
-    return r.u;
+  struct Cursor {
+    const bf16* img;  // sample b of dz, or nullptr past the last row
+    int y1, x1;       // (uy + 1, ux + 1)
+    int ky, kx, o0;
+  };
+  __device__ __forceinline__ Cursor cursor(int m, int k) const {
+    Cursor c;
+    c.img = nullptr;
+    c.y1 = c.x1 = 0;
+    if (m < B * hu * hu) {
+      const int b = m / (hu * hu), rem = m % (hu * hu);
+      c.img = dz + (size_t)b * hout * hout * oc;
+      c.y1 = rem / hu + 1;
+      c.x1 = rem % hu + 1;
+    }
+    const int tap = k / oc;
+    c.ky = tap / 3;
+    c.kx = tap % 3;
+    c.o0 = k - tap * oc;
+    return c;
   }
-};
-
-// Weight gradient, B operand: row k = (tap, ic) of the im2col matrix, 8 consecutive output pixels.
-struct ColRows {
-  const bf16* a;   // layer input [B][hin][hin][ic] (layers 2..5)
-  const float* I;  // layer 1: the patterns
-  float s_in;
-  int B, hin, hu, hout, ic, stride, up;
-  __device__ __forceinline__ uint4 operator()(int k, int m) const {
-    Pack8 r;
-    r.u = make_uint4(0u, 0u, 0u, 0u);
-    if (k >= 9 * ic) return r.u;
-    const int tap = k / ic, c = k - tap * ic, ky = tap / 3, kx = tap % 3;
-    const int hw = hout * hout;
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int mm = m + e;
-      if (mm >= B * hw) break;
-      const int b = mm / hw, rem = mm % hw, oy = rem / hout, ox = rem % hout;
-      const int uy = stride * oy + ky - 1, ux = stride * ox + kx - 1;
-      if (uy < 0 || uy >= hu || ux < 0 || ux >= hu) continue;
-      if (I) {
-        r.h[e] = input_value(I, s_in, hin, b, uy, ux);
-      } else {
-        r.h[e] = a[(((size_t)b * hin + uy / up) * hin + ux / up) * ic + c];
+  __device__ __forceinline__ uint4 load(const Cursor& c) const {
+    const int ty = c.y1 - c.ky, tx = c.x1 - c.kx;
+    const int sm = stride - 1, sh = stride == 2 ? 1 : 0;  // stride is 1 or 2
+    if (!c.img || c.ky > 2 || ty < 0 || tx < 0 || ((ty | tx) & sm)) return make_uint4(0u, 0u, 0u, 0u);
+    const int oy = ty >> sh, ox = tx >> sh;
+    if (oy >= hout || ox >= hout) return make_uint4(0u, 0u, 0u, 0u);
+    return __ldg(reinterpret_cast<const uint4*>(c.img + ((size_t)oy * hout + ox) * oc + c.o0));
+  }
+  __device__ __forceinline__ void advance(Cursor& c, int dk) const {
+    c.o0 += dk;
+    while (c.o0 >= oc) {
+      c.o0 -= oc;
+      if (++c.kx == 3) {
+        c.kx = 0;
+        ++c.ky;
       }
     }
-    return r.u;
   }
 };
 
@@ -542,6 +596,90 @@ __global__ void k_stitch_finish(int Nz, int H, int W, const float* __restrict__ 
 
 
 // ---------------------------------------------------------------------------------------------
+// Weight-gradient operands with pixel-contiguous rows
+// ---------------------------------------------------------------------------------------------
+// colT[k][m - p0] = im2col[m][k] for k = (tap, ic) < 9 IC and output pixels m in [p0, p0 + P); zero
+// past the last pixel (layers 2..5, ic a multiple of 8).  A thread takes one pixel and 8 channels:
+// per tap one 16-byte load and 8 stores into 8 rows; consecutive threads take consecutive pixels, so
+// every row is written 64 bytes per warp at a time.
+__global__ void k_im2col_t(const bf16* __restrict__ a, bf16* __restrict__ colt, int B, int hin, int hu, int hout,
+                           int ic, int stride, int up, int p0, int P) {
+  const int hw = hout * hout, pixels = B * hw, groups = ic / 8;
+  const size_t n = (size_t)groups * P;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int mm = (int)(i % P), c0 = 8 * (int)(i / P), m = p0 + mm;
+    int b = 0, y0 = -1 << 20, x0 = -1 << 20;
+    if (m < pixels) {
+      b = m / hw;
+      const int rem = m % hw;
+      y0 = stride * (rem / hout) - 1;
+      x0 = stride * (rem % hout) - 1;
+    }
+    const bf16* img = a + (size_t)b * hin * hin * ic + c0;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      const int uy = y0 + tap / 3, ux = x0 + tap % 3;
+      union {
+        uint4 u;
+        bf16 h[8];
+      } v;
+      v.u = make_uint4(0u, 0u, 0u, 0u);
+      if (uy >= 0 && uy < hu && ux >= 0 && ux < hu)
+        v.u = __ldg(reinterpret_cast<const uint4*>(img + ((size_t)(uy / up) * hin + ux / up) * ic));
+      bf16* row = colt + ((size_t)tap * ic + c0) * P + mm;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) row[(size_t)e * P] = v.h[e];
+    }
+  }
+}
+
+// Layer 1 (one channel from the patterns): colT[tap][m - p0], threads along m.
+__global__ void k_im2col_t1(const float* __restrict__ I, float s_in, bf16* __restrict__ colt, int B, int S, int hout,
+                            int p0, int P) {
+  const size_t n = (size_t)9 * P;
+  const int hw = hout * hout, pixels = B * hw;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int m = p0 + (int)(i % P), tap = (int)(i / P);
+    bf16 v = __float2bfloat16_rn(0.f);
+    if (m < pixels) {
+      const int b = m / hw, rem = m % hw, oy = rem / hout, ox = rem % hout;
+      const int y = 2 * oy + tap / 3 - 1, x = 2 * ox + tap % 3 - 1;
+      if (y >= 0 && y < S && x >= 0 && x < S) v = input_value(I, s_in, S, b, y, x);
+    }
+    colt[i] = v;
+  }
+}
+
+// dzT[c][m - p0] = dz[m][c] for m in [p0, p0 + P) (zero past the last pixel), 32 x 32 tiles through
+// shared memory, and the bias gradient: gb[c] += the tile's sum over its pixels.
+__global__ void k_dz_t(const bf16* __restrict__ dz, bf16* __restrict__ dzt, float* __restrict__ gb, int pixels, int C,
+                       int p0, int P) {
+  __shared__ bf16 tile[32][34];
+  __shared__ float colsum[8][32];
+  const int mt = blockIdx.x * 32, ct = blockIdx.y * 32;
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  float acc = 0.f;
+  for (int j = ty; j < 32; j += 8) {
+    const int m = p0 + mt + j, c = ct + tx;
+    const bf16 v = (m < pixels && mt + j < P && c < C) ? dz[(size_t)m * C + c] : __float2bfloat16_rn(0.f);
+    tile[j][tx] = v;
+    acc += __bfloat162float(v);
+  }
+  colsum[ty][tx] = acc;
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    const int c = ct + j, mm = mt + tx;
+    if (c < C && mm < P) dzt[(size_t)c * P + mm] = tile[tx][j];
+  }
+  if (ty == 0 && ct + tx < C) {
+    float t = 0.f;
+#pragma unroll
+    for (int r = 0; r < 8; ++r) t += colsum[r][tx];
+    atomicAdd(gb + ct + tx, t);
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------------
 #define CNN_CHECK(what)                                                  \
@@ -560,30 +698,50 @@ static unsigned blocks_for(size_t n, unsigned cap = 152 * 16) {
 }
 
 template <class LA, class LB, class Epi>
-static int gemm(const LA& la, const LB& lb, int rows, int cols, int K, const Epi& epi, cudaStream_t st,
+static int gemm(const LA& la, const LB& lb, int rows, int cols, int K, const Epi& epi, int* status, cudaStream_t st,
                 int splits = 1) {
+#if PTY_GEMM_LEGACY
   const int kt_all = (K + GB_K - 1) / GB_K;
   if (splits > kt_all) splits = kt_all;
   if (splits < 1) splits = 1;
   const int kt_per = (kt_all + splits - 1) / splits;
   const dim3 grid((cols + GB_N - 1) / GB_N, (rows + GB_M - 1) / GB_M, (kt_all + kt_per - 1) / kt_per);
-  // FP32 accumulation with each 32-wide K tile promoted to a round-to-nearest FP32 sum (the MMA's
-  // own accumulation drifts over long K; see k_gemm_tn)
   k_gemm_tn<bf16, LA, LB, Epi, true><<<grid, GB_THREADS, 0, st>>>(la, lb, kt_all * GB_K, kt_per, epi);
+  (void)status;
   CNN_CHECK("k_gemm_tn");
+#else
+  // tcgen05 tiles of 128 x BN, BN matched to the column count; every 64-wide K block is promoted to
+  // a round-to-nearest FP32 sum (see k_gemm_tc)
+  cudaError_t e;
+  if (cols <= 64) {
+    e = launch_gemm_tc<bf16, 64, true>(la, lb, rows, cols, K, epi, status, st, splits);
+  } else if (cols % 256 == 0) {
+    e = launch_gemm_tc<bf16, 256, true>(la, lb, rows, cols, K, epi, status, st, splits);
+  } else {
+    e = launch_gemm_tc<bf16, 128, true>(la, lb, rows, cols, K, epi, status, st, splits);
+  }
+  if (e != cudaSuccess) {
+    set_error("k_gemm_tc launch failed: %s", cudaGetErrorString(e));
+    return PTY_ECUDA;
+  }
+  note_launch();
+#endif
   return PTY_OK;
 }
 
 struct Buffers {
+  int* status;
   bf16 *wp[5], *wt[5], *act[5], *dz[6];
   float *w6, *p6, *dp6, *du5;
   double* lpart;
+  bf16 *colt, *dzt;
 };
 
 static Buffers carve(const Plan& pl, void* ws) {
   char* base = static_cast<char*>(ws);
   Buffers b;
   memset(&b, 0, sizeof(b));
+  b.status = reinterpret_cast<int*>(base + pl.status);
   for (int l = 0; l < 5; ++l) {
     b.wp[l] = reinterpret_cast<bf16*>(base + pl.wp[l]);
     if (l > 0) b.wt[l] = reinterpret_cast<bf16*>(base + pl.wt[l]);
@@ -596,6 +754,8 @@ static Buffers carve(const Plan& pl, void* ws) {
   b.dp6 = reinterpret_cast<float*>(base + pl.dp6);
   b.du5 = reinterpret_cast<float*>(base + pl.du5);
   b.lpart = reinterpret_cast<double*>(base + pl.lpart);
+  b.colt = reinterpret_cast<bf16*>(base + pl.colt);
+  b.dzt = reinterpret_cast<bf16*>(base + pl.dzt);
   return b;
 }
 
@@ -616,6 +776,10 @@ static int run_forward(const Plan& pl, const Buffers& bu, const float* params, c
     pa.ic[l] = kNet[l].ic;
     pa.oc[l] = kNet[l].oc;
   }
+  if (cudaMemsetAsync(bu.status, 0, sizeof(int), st) != cudaSuccess) {
+    set_error("cudaMemsetAsync failed: %s", cudaGetErrorString(cudaGetLastError()));
+    return PTY_ECUDA;
+  }
   k_pack<<<152 * 4, 256, 0, st>>>(pa);
   CNN_CHECK("k_pack");
   const int B = pl.B;
@@ -627,10 +791,10 @@ static int run_forward(const Plan& pl, const Buffers& bu, const float* params, c
     FwdEpi epi{bu.act[l], params + pl.boff[l], rows, L.oc};
     int rc;
     if (l == 0) {
-      rc = gemm(InputIm2col{I, s_in, pl.S, B, pl.hout[0]}, lb, rows, L.oc, pl.kp[l], epi, st);
+      rc = gemm(InputIm2col{I, s_in, pl.S, B, pl.hout[0]}, lb, rows, L.oc, pl.kp[l], epi, bu.status, st);
     } else {
       rc = gemm(Im2col{bu.act[l - 1], B, pl.hin[l], pl.hu[l], pl.hout[l], L.ic, L.stride, L.up}, lb, rows, L.oc,
-                pl.kp[l], epi, st);
+                pl.kp[l], epi, bu.status, st);
     }
     if (rc) return rc;
   }
@@ -682,24 +846,35 @@ static int run_backward(const Plan& pl, const Buffers& bu, const float* I, float
     const LayerDef& L = kNet[l];
     const int pixels = B * pl.hout[l] * pl.hout[l];
     const int k9 = 9 * L.ic;
-    const int tiles = ((k9 + GB_N - 1) / GB_N) * ((L.oc + GB_M - 1) / GB_M);
-    const int splits = 608 / tiles > 1 ? 608 / tiles : 1;
-    ColRows col{l > 0 ? bu.act[l - 1] : nullptr, l > 0 ? nullptr : I, s_in, B, pl.hin[l], pl.hu[l], pl.hout[l],
-                L.ic, L.stride, L.up};
-    int rc = gemm(DzRows{bu.dz[l], pixels, L.oc}, col, L.oc, k9, pixels, WgradEpi{grad + pl.woff[l], L.oc, k9}, st,
-                  splits);
-    if (rc) return rc;
-    k_bias_grad<<<(unsigned)((pixels + 1023) / 1024), 256, 0, st>>>(bu.dz[l], grad + pl.boff[l], (size_t)pixels,
-                                                                   L.oc, 1024);
-    CNN_CHECK("k_bias_grad");
+    // dW[oc][k] = sum over pixels of dz[m][oc] im2col[m][k], chunk by chunk, both operands
+    // transposed to pixel-contiguous rows first (plain 16-byte loads in the GEMM)
+    const int P = pl.pchunk[l];
+    for (int p0 = 0; p0 < pixels; p0 += P) {
+      if (l == 0) {
+        k_im2col_t1<<<blocks_for((size_t)9 * P), 256, 0, st>>>(I, s_in, bu.colt, B, pl.S, pl.hout[0], p0, P);
+      } else {
+        k_im2col_t<<<blocks_for((size_t)L.ic / 8 * P), 256, 0, st>>>(bu.act[l - 1], bu.colt, B, pl.hin[l], pl.hu[l],
+                                                                     pl.hout[l], L.ic, L.stride, L.up, p0, P);
+      }
+      CNN_CHECK("k_im2col_t");
+      k_dz_t<<<dim3((P + 31) / 32, (L.oc + 31) / 32), dim3(32, 8), 0, st>>>(bu.dz[l], bu.dzt, grad + pl.boff[l], pixels,
+                                                                          L.oc, p0, P);
+      CNN_CHECK("k_dz_t");
+      const int tiles = ((k9 + 127) / 128) * ((L.oc + 127) / 128);
+      const int splits = 2 * 152 / tiles > 1 ? 2 * 152 / tiles : 1;
+      int rc = gemm(PlainLoader<bf16>{bu.dzt, (size_t)P, L.oc}, PlainLoader<bf16>{bu.colt, (size_t)P, k9}, L.oc, k9,
+                    P, WgradEpi{grad + pl.woff[l], L.oc, k9}, bu.status, st, splits);
+      if (rc) return rc;
+    }
     if (l == 0) break;
     const int rows = B * pl.hu[l] * pl.hu[l];
     DgradGather ga{bu.dz[l], B, pl.hu[l], pl.hout[l], L.oc, L.stride};
     PlainLoader<bf16> wt{bu.wt[l], (size_t)pl.ktp[l], L.ic};
+    int rc;
     if (L.up == 1) {
-      rc = gemm(ga, wt, rows, L.ic, pl.ktp[l], DgradEpi{bu.dz[l - 1], bu.act[l - 1], rows, L.ic}, st);
+      rc = gemm(ga, wt, rows, L.ic, pl.ktp[l], DgradEpi{bu.dz[l - 1], bu.act[l - 1], rows, L.ic}, bu.status, st);
     } else {
-      rc = gemm(ga, wt, rows, L.ic, pl.ktp[l], StoreEpi{bu.du5, rows, L.ic}, st);
+      rc = gemm(ga, wt, rows, L.ic, pl.ktp[l], StoreEpi{bu.du5, rows, L.ic}, bu.status, st);
       if (rc) return rc;
       k_upsample_grad<<<blocks_for((size_t)B * pl.hin[l] * pl.hin[l] * L.ic), 256, 0, st>>>(
           bu.du5, bu.act[l - 1], bu.dz[l - 1], B, pl.hin[l], L.ic, L.up);

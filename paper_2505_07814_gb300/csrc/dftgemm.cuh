@@ -19,6 +19,7 @@
 #include <cuda_fp16.h>
 
 #include "gemm_mma.cuh"
+#include "gemm_tc.cuh"
 #include "pipeline.cuh"
 
 namespace pty {
@@ -343,6 +344,7 @@ struct GemmPass {
     SplitLoader<N, P> ld{src, rows, sc};
     constexpr int K = S::kTerms * 2 * N;
     PlainLoader<H> lb{tables + (size_t)mat * 2 * N * K, (size_t)K, 2 * N};
+#if PTY_GEMM_LEGACY
     const dim3 grid(2 * N / GB_N, rows_pad / GB_M, 1);
     if (transpose) {
       k_gemm_tn<H, SplitLoader<N, P>, PlainLoader<H>, DftEpilogue<N, true>, true>
@@ -351,7 +353,19 @@ struct GemmPass {
       k_gemm_tn<H, SplitLoader<N, P>, PlainLoader<H>, DftEpilogue<N, false>, true>
           <<<grid, GB_THREADS, 0, st>>>(ld, lb, K, K / GB_K, DftEpilogue<N, false>{(float*)dst, rows, sc});
     }
-    PTY_LAUNCH_CHECK("k_gemm_tn", -1);
+#else
+    // one CTA covers all 2N output columns, so every A row is split once per GEMM
+    cudaError_t e = transpose ? launch_gemm_tc<H, 2 * N, PTY_TC_PROMOTE>(ld, lb, rows, 2 * N, K,
+                                                              DftEpilogue<N, true>{(float*)dst, rows, sc}, ws.status, st)
+                              : launch_gemm_tc<H, 2 * N, PTY_TC_PROMOTE>(ld, lb, rows, 2 * N, K,
+                                                              DftEpilogue<N, false>{(float*)dst, rows, sc}, ws.status,
+                                                              st);
+    if (e != cudaSuccess) {
+      set_error("k_gemm_tc launch failed: %s", cudaGetErrorString(e));
+      return PTY_ECUDA;
+    }
+#endif
+    PTY_LAUNCH_CHECK("k_gemm", -1);
     return PTY_OK;
   }
   // natural [w][r][c] -> k-space [w][p1][p0] and back, through ws.tmp

@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 namespace pty {
 
 constexpr int GB_M = 128, GB_N = 128, GB_K = 32, GB_PITCH = 40, GB_THREADS = 256;
@@ -67,6 +69,7 @@ __device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
 // or beyond `rows` read as zero.
 template <class H>
 struct PlainLoader {
+  static constexpr bool kDirect = true;  // src() gives the address: copies may go global -> shared directly
   const H* A;
   size_t ld;
   int rows;
@@ -74,7 +77,30 @@ struct PlainLoader {
     if (r >= rows) return make_uint4(0u, 0u, 0u, 0u);
     return __ldg(reinterpret_cast<const uint4*>(A + (size_t)r * ld + k));
   }
+  // address of the chunk, or nullptr where the loader reads zeros
+  __device__ __forceinline__ const void* src(int r, int k) const {
+    return r < rows ? (const void*)(A + (size_t)r * ld + k) : nullptr;
+  }
+  // cursor for gathers through registers: the chunk's address, stepped along the row
+  struct Cursor {
+    const H* p;
+  };
+  __device__ __forceinline__ Cursor cursor(int r, int k) const {
+    return Cursor{r < rows ? A + (size_t)r * ld + k : nullptr};
+  }
+  __device__ __forceinline__ uint4 load(const Cursor& c) const {
+    return c.p ? __ldg(reinterpret_cast<const uint4*>(c.p)) : make_uint4(0u, 0u, 0u, 0u);
+  }
+  __device__ __forceinline__ void advance(Cursor& c, int dk) const {
+    if (c.p) c.p += dk;
+  }
 };
+
+// Loaders without src() are gathered through registers.
+template <class L, class = void>
+struct loader_direct : std::false_type {};
+template <class L>
+struct loader_direct<L, std::void_t<decltype(L::kDirect)>> : std::bool_constant<L::kDirect> {};
 
 // C[M x N] = A[M x K] * B[N x K]^T, A row m / B row n delivered 8 K-elements at a time by the
 // loaders.  grid = (ceil(N / 128), ceil(M / 128), splits): blockIdx.z takes K tiles
