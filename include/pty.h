@@ -96,7 +96,8 @@ typedef struct {
                       and a remainder (three products; 16 and 22 significant bits, fp16 after a
                       power-of-two rescaling of each batch), PTY_FFT_SPLIT3_BF16 three bf16 pieces
                       (six products, 24 bits).  The split modes keep every slice's checkpoint
-                      (ckpt_stride is ignored) and add 2*B*M*N^2*8 bytes of workspace.  The first
+                      (ckpt_stride is ignored) and add 4*B*M*N^2*8 bytes of workspace
+                      (5*B*M*N^2*8 for three-piece bf16).  The first
                       split call on a device builds its DFT tables and waits for them (not
                       capturable into a CUDA graph). */
 } pty_geom;

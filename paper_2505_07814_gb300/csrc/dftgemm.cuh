@@ -20,6 +20,11 @@
 
 #include "gemm_mma.cuh"
 #include "gemm_tc.cuh"
+
+// column tile of the DFT GEMMs (0: all 2N columns in one CTA)
+#ifndef PTY_DFT_BN
+#define PTY_DFT_BN 0
+#endif
 #include "pipeline.cuh"
 
 namespace pty {
@@ -75,8 +80,8 @@ __device__ __forceinline__ typename S::H split_piece(float x, int q) {
   return h;
 }
 
-// Split DFT matrices B^T[mat][2N][kTerms * 2N] (rows: output real parts, then imaginary parts; K:
-// the split terms, each input real parts then imaginary parts).  mat 0: axis 1 forward (natural c ->
+// Split DFT matrices B^T[mat][2N][kTerms * 2N] (rows: real and imaginary part of output position 0,
+// then of position 1, ...; K: the split terms, each input real parts then imaginary parts).  mat 0: axis 1 forward (natural c ->
 // position p1); 1: axis 0 forward (r -> p0); 2: axis 0 inverse (p0 -> r); 3: axis 1 inverse (p1 -> c).
 template <int N, int P>
 __global__ void k_init_dft_tables(typename SplitType<P>::H* Bt) {
@@ -87,7 +92,7 @@ __global__ void k_init_dft_tables(typename SplitType<P>::H* Bt) {
     const int mat = (int)(i / ((size_t)R * K));
     const int jp = (int)((i / K) % R), kp = (int)(i % K);
     const int t = kp / R, q = kp % R;
-    const int qin = q % N, pin = q / N, jout = jp % N, pout = jp / N;
+    const int qin = q % N, pin = q / N, jout = jp / 2, pout = jp % 2;  // output (re, im) interleaved
     int a, b;
     double sign;
     switch (mat) {
@@ -139,8 +144,9 @@ struct SplitLoader {
   }
 };
 
-// C columns 0..N-1 are real parts, N..2N-1 imaginary parts of output positions; TRANSPOSE stores
-// row a of wave w at position (w, col, a).
+// C column 2c is the real part and 2c + 1 the imaginary part of output position c (the tables
+// interleave them), so each (v0, v1) pair is one complex value; TRANSPOSE stores row a of wave w
+// at position (w, c, a).
 template <int N, bool TRANSPOSE>
 struct DftEpilogue {
   float* out;  // interleaved complex
@@ -149,12 +155,91 @@ struct DftEpilogue {
   __device__ __forceinline__ void operator()(int row, int col, float v0, float v1) const {
     if (row >= M) return;
     const float s = scale ? 1.0f / *scale : 1.0f;
-    const int part = col / N, c = col % N;
+    const int c = col >> 1;
     const int w = row / N, a = row % N;
-    const size_t e0 = TRANSPOSE ? ((size_t)w * N + c) * N + a : (size_t)row * N + c;
-    const size_t e1 = TRANSPOSE ? e0 + N : e0 + 1;
-    out[2 * e0 + part] = v0 * s;
-    out[2 * e1 + part] = v1 * s;
+    const size_t e = TRANSPOSE ? ((size_t)w * N + c) * N + a : (size_t)row * N + c;
+    reinterpret_cast<float2*>(out)[e] = make_float2(v0 * s, v1 * s);
+  }
+};
+
+// Pre-split operands for the tensor-core GEMMs: row r holds, for each piece q, the 2N reals
+// (real parts then imaginary parts) of that piece: Xs[r][q][2N].  A K chunk (term t, position j) is
+// then 16 contiguous bytes, Xs[r][a_piece(t)][j .. j + 7], copied global -> shared directly.
+template <int N, int P>
+struct PiecesLoader {
+  using S = SplitType<P>;
+  using H = typename S::H;
+  static constexpr bool kDirect = true;
+  const H* A;
+  int rows;
+  __device__ __forceinline__ const void* src(int r, int k) const {
+    if (r >= rows) return nullptr;
+    const int t = k / (2 * N), j = k % (2 * N);
+    return A + ((size_t)r * S::kPieces + S::a_piece(t)) * (2 * N) + j;
+  }
+  __device__ __forceinline__ uint4 operator()(int r, int k) const {
+    const void* g = src(r, k);
+    return g ? *reinterpret_cast<const uint4*>(g) : make_uint4(0u, 0u, 0u, 0u);
+  }
+};
+
+// Xs from complex rows X[rows][N] (times the fp16 scale when given): one thread per 8 columns of
+// one row, both parts, every piece.
+template <int N, int P>
+__global__ void k_split(const float2* __restrict__ X, typename SplitType<P>::H* __restrict__ Xs, int rows,
+                        const float* scale) {
+  using S = SplitType<P>;
+  using H = typename S::H;
+  const size_t n = (size_t)rows * (N / 8);
+  const float sc = scale ? *scale : 1.0f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t r = i / (N / 8);
+    const int c0 = 8 * (int)(i % (N / 8));
+    const float4* x = reinterpret_cast<const float4*>(X + r * N + c0);
+    float re[8], im[8];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float4 v = x[e];
+      re[2 * e] = v.x * sc;
+      im[2 * e] = v.y * sc;
+      re[2 * e + 1] = v.z * sc;
+      im[2 * e + 1] = v.w * sc;
+    }
+#pragma unroll
+    for (int q = 0; q < S::kPieces; ++q) {
+      union {
+        uint4 u;
+        H h[8];
+      } a, b;
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        a.h[e] = split_piece<S>(re[e], q);
+        b.h[e] = split_piece<S>(im[e], q);
+      }
+      H* row = Xs + (r * S::kPieces + q) * (2 * N);
+      *reinterpret_cast<uint4*>(row + c0) = a.u;
+      *reinterpret_cast<uint4*>(row + N + c0) = b.u;
+    }
+  }
+}
+
+// First GEMM of a 2D transform, unscaled formats: the result, transposed per wave, goes straight
+// into the pieces of the second GEMM's operand (output row (w, c), position part * N + a).
+template <int N, int P>
+struct DftSplitEpilogue {
+  using S = SplitType<P>;
+  typename S::H* out;
+  int M;
+  __device__ __forceinline__ void put(size_t orow, int j, float v) const {
+#pragma unroll
+    for (int q = 0; q < S::kPieces; ++q) out[(orow * S::kPieces + q) * (2 * N) + j] = split_piece<S>(v, q);
+  }
+  __device__ __forceinline__ void operator()(int row, int col, float v0, float v1) const {
+    if (row >= M) return;
+    const int c = col >> 1;  // (v0, v1) = (re, im) of output position c
+    const int w = row / N, a = row % N;
+    put((size_t)w * N + c, a, v0);
+    put((size_t)w * N + c, N + a, v1);
   }
 };
 
@@ -327,24 +412,32 @@ struct GemmPass {
   explicit GemmPass(const Problem& p) : base(p), pb(p), ws(p.ws), st(p.stream) {}
 
   // out = rows of `src` times split DFT matrix `mat`; TRANSPOSE stores each wave transposed
+  // fp16 batch scale of `src` into ws.gscal (returns the device scale pointer)
+  int fp16_scale(const float2* src, const float** sc) {
+    const int rows = pb.B * pb.M * N;
+    unsigned* amax = reinterpret_cast<unsigned*>(ws.gscal);
+    float* scale = reinterpret_cast<float*>(ws.gscal) + 1;
+    if (cudaMemsetAsync(amax, 0, sizeof(unsigned), st) != cudaSuccess) return base.memset_failed();
+    k_absmax<<<152 * 4, 256, 0, st>>>(reinterpret_cast<const float*>(src), (size_t)rows * N * 2, amax);
+    PTY_LAUNCH_CHECK("k_absmax", -1);
+    k_pow2_scale<<<1, 1, 0, st>>>(amax, scale);
+    PTY_LAUNCH_CHECK("k_pow2_scale", -1);
+    *sc = scale;
+    return PTY_OK;
+  }
+#if PTY_GEMM_LEGACY
+  // out = rows of `src` times split DFT matrix `mat`; TRANSPOSE stores each wave transposed
   int gemm(int mat, const float2* src, float2* dst, bool transpose) {
     const int rows = pb.B * pb.M * N;
     const int rows_pad = (rows + GB_M - 1) / GB_M * GB_M;
     const float* sc = nullptr;
     if (S::kScale) {
-      unsigned* amax = reinterpret_cast<unsigned*>(ws.gscal);
-      float* scale = reinterpret_cast<float*>(ws.gscal) + 1;
-      if (cudaMemsetAsync(amax, 0, sizeof(unsigned), st) != cudaSuccess) return base.memset_failed();
-      k_absmax<<<152 * 4, 256, 0, st>>>(reinterpret_cast<const float*>(src), (size_t)rows * N * 2, amax);
-      PTY_LAUNCH_CHECK("k_absmax", -1);
-      k_pow2_scale<<<1, 1, 0, st>>>(amax, scale);
-      PTY_LAUNCH_CHECK("k_pow2_scale", -1);
-      sc = scale;
+      int rc = fp16_scale(src, &sc);
+      if (rc) return rc;
     }
     SplitLoader<N, P> ld{src, rows, sc};
     constexpr int K = S::kTerms * 2 * N;
     PlainLoader<H> lb{tables + (size_t)mat * 2 * N * K, (size_t)K, 2 * N};
-#if PTY_GEMM_LEGACY
     const dim3 grid(2 * N / GB_N, rows_pad / GB_M, 1);
     if (transpose) {
       k_gemm_tn<H, SplitLoader<N, P>, PlainLoader<H>, DftEpilogue<N, true>, true>
@@ -353,30 +446,62 @@ struct GemmPass {
       k_gemm_tn<H, SplitLoader<N, P>, PlainLoader<H>, DftEpilogue<N, false>, true>
           <<<grid, GB_THREADS, 0, st>>>(ld, lb, K, K / GB_K, DftEpilogue<N, false>{(float*)dst, rows, sc});
     }
+    PTY_LAUNCH_CHECK("k_gemm_tn", -1);
+    return PTY_OK;
+  }
+  int transform(int mat_a, int mat_b) {
+    int rc = gemm(mat_a, ws.wave, ws.tmp, true);
+    return rc ? rc : gemm(mat_b, ws.tmp, ws.wave, false);
+  }
 #else
-    // one CTA covers all 2N output columns, so every A row is split once per GEMM
-    cudaError_t e = transpose ? launch_gemm_tc<H, 2 * N, PTY_TC_PROMOTE>(ld, lb, rows, 2 * N, K,
-                                                              DftEpilogue<N, true>{(float*)dst, rows, sc}, ws.status, st)
-                              : launch_gemm_tc<H, 2 * N, PTY_TC_PROMOTE>(ld, lb, rows, 2 * N, K,
-                                                              DftEpilogue<N, false>{(float*)dst, rows, sc}, ws.status,
-                                                              st);
+  // Tensor-core form: the wave is split once into pieces (k_split), the first GEMM writes its
+  // transposed result either as pieces of the second GEMM's operand (bf16 formats) or, for fp16,
+  // in FP32 to be rescaled and split again; both operands reach shared memory by cp.async.
+  template <class Epi>
+  int gemm_tc(int mat, const H* a_pieces, const Epi& epi) {
+    const int rows = pb.B * pb.M * N;
+    constexpr int K = S::kTerms * 2 * N;
+    PiecesLoader<N, P> la{a_pieces, rows};
+    PlainLoader<H> lb{tables + (size_t)mat * 2 * N * K, (size_t)K, 2 * N};
+    constexpr int BN = PTY_DFT_BN > 0 && PTY_DFT_BN < 2 * N ? PTY_DFT_BN : 2 * N;
+    const cudaError_t e = launch_gemm_tc<H, BN, PTY_TC_PROMOTE>(la, lb, rows, 2 * N, K, epi, ws.status, st);
     if (e != cudaSuccess) {
       set_error("k_gemm_tc launch failed: %s", cudaGetErrorString(e));
       return PTY_ECUDA;
     }
-#endif
-    PTY_LAUNCH_CHECK("k_gemm", -1);
+    PTY_LAUNCH_CHECK("k_gemm_tc", -1);
     return PTY_OK;
   }
-  // natural [w][r][c] -> k-space [w][p1][p0] and back, through ws.tmp
-  int dft2() {
-    int rc = gemm(0, ws.wave, ws.tmp, true);
-    return rc ? rc : gemm(1, ws.tmp, ws.wave, false);
+  int split(const float2* src, H* dst, const float* sc) {
+    const int rows = pb.B * pb.M * N;
+    const size_t n = (size_t)rows * (N / 8);
+    const unsigned blocks = (unsigned)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
+    k_split<N, P><<<blocks, 256, 0, st>>>(src, dst, rows, sc);
+    PTY_LAUNCH_CHECK("k_split", -1);
+    return PTY_OK;
   }
-  int idft2() {
-    int rc = gemm(2, ws.wave, ws.tmp, true);
-    return rc ? rc : gemm(3, ws.tmp, ws.wave, false);
+  int transform(int mat_a, int mat_b) {
+    const int rows = pb.B * pb.M * N;
+    H* pa = reinterpret_cast<H*>(ws.pieces0);
+    H* pb_ = reinterpret_cast<H*>(ws.pieces1);
+    const float* sc = nullptr;
+    int rc;
+    if (S::kScale) {
+      if ((rc = fp16_scale(ws.wave, &sc))) return rc;
+      if ((rc = split(ws.wave, pa, sc))) return rc;
+      if ((rc = gemm_tc(mat_a, pa, DftEpilogue<N, true>{(float*)ws.tmp, rows, sc}))) return rc;
+      if ((rc = fp16_scale(ws.tmp, &sc))) return rc;
+      if ((rc = split(ws.tmp, pb_, sc))) return rc;
+    } else {
+      if ((rc = split(ws.wave, pa, nullptr))) return rc;
+      if ((rc = gemm_tc(mat_a, pa, DftSplitEpilogue<N, P>{pb_, rows}))) return rc;
+    }
+    return gemm_tc(mat_b, pb_, DftEpilogue<N, false>{(float*)ws.wave, rows, sc});
   }
+#endif
+  // natural [w][r][c] -> k-space [w][p1][p0] and back
+  int dft2() { return transform(0, 1); }
+  int idft2() { return transform(2, 3); }
   template <int ST>
   int stage(const FwdArgs& fa, const AdjArgs& aa, int sl, int prof) {
     StageArgs g{fa, aa, ws.wave, sl};

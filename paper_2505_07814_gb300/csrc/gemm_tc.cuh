@@ -203,18 +203,22 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<BN>::MINB)
     }
   };
 
-  constexpr bool kDirectB = loader_direct<LoadB>::value;
-  uint4 ra[A_CHUNKS];
+  // Loaders with src() (plain matrices) are copied global -> shared with cp.async; the others are
+  // gathered through registers.
+  constexpr bool kDirectA = loader_direct<LoadA>::value, kDirectB = loader_direct<LoadB>::value;
+  [[maybe_unused]] uint4 ra[kDirectA ? 1 : A_CHUNKS];
   [[maybe_unused]] uint4 rb[kDirectB ? 1 : B_CHUNKS];
   // chunk c of a tile -> k group c / rows, row c % rows: a warp writes 32 rows of one k group
   // (four conflict-free 128-byte wavefronts).  A thread's rows are the same in every block, so its
   // loader cursors are set up once and advanced by 64 per block.
-  typename CursorOf<LoadA>::T ca[A_CHUNKS];
+  [[maybe_unused]] typename CursorOf<LoadA>::T ca[kDirectA ? 1 : A_CHUNKS];
   [[maybe_unused]] typename CursorOf<LoadB>::T cb[kDirectB ? 1 : B_CHUNKS];
+  if constexpr (!kDirectA) {
 #pragma unroll
-  for (int h = 0; h < A_CHUNKS; ++h) {
-    const int c = tid + h * TC_THREADS;
-    ca[h] = cur_make(la, m0 + c % TC_BM, kb0 * TC_BK + 8 * (c / TC_BM));
+    for (int h = 0; h < A_CHUNKS; ++h) {
+      const int c = tid + h * TC_THREADS;
+      ca[h] = cur_make(la, m0 + c % TC_BM, kb0 * TC_BK + 8 * (c / TC_BM));
+    }
   }
   if constexpr (!kDirectB) {
 #pragma unroll
@@ -223,12 +227,14 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<BN>::MINB)
       cb[h] = cur_make(lb, n0 + c % BN, kb0 * TC_BK + 8 * (c / BN));
     }
   }
-  auto fetch = [&](int q) {  // the next block's A (and register-path B) chunks into registers
+  auto fetch = [&](int q) {  // the next block's register-path chunks
     (void)q;
+    if constexpr (!kDirectA) {
 #pragma unroll
-    for (int h = 0; h < A_CHUNKS; ++h) {
-      ra[h] = cur_load(la, ca[h]);
-      cur_advance(la, ca[h], TC_BK);
+      for (int h = 0; h < A_CHUNKS; ++h) {
+        ra[h] = cur_load(la, ca[h]);
+        cur_advance(la, ca[h], TC_BK);
+      }
     }
     if constexpr (!kDirectB) {
 #pragma unroll
@@ -238,28 +244,44 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<BN>::MINB)
       }
     }
   };
-  auto copy_b = [&](int q) {  // direct B: asynchronous global -> shared copies (zero-filled rows)
-    if constexpr (kDirectB) {
-      unsigned char* sb = base + (q % TC_STAGES) * STAGE + A_BYTES;
+  // direct operands: asynchronous global -> shared copies of block q (zero-filled past the rows)
+  auto copy_direct = [&](int q) {
+    if constexpr (kDirectA || kDirectB) {
+      unsigned char* st = base + (q % TC_STAGES) * STAGE;
       const int k0 = (kb0 + q) * TC_BK;
+      if constexpr (kDirectA) {
 #pragma unroll
-      for (int h = 0; h < B_CHUNKS; ++h) {
-        const int c = tid + h * TC_THREADS, r = c % BN, kg = c / BN;
-        const void* g = lb.src(n0 + r, k0 + 8 * kg);
-        const uint32_t d = tc_smem_u32(sb + (r >> 3) * TC_SBO + kg * TC_LBO + (r & 7) * 16);
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(g ? g : (const void*)lb.A),
-                     "r"(g ? 16 : 0)
-                     : "memory");
+        for (int h = 0; h < A_CHUNKS; ++h) {
+          const int c = tid + h * TC_THREADS, r = c % TC_BM, kg = c / TC_BM;
+          const void* g = la.src(m0 + r, k0 + 8 * kg);
+          const uint32_t d = tc_smem_u32(st + (r >> 3) * TC_SBO + kg * TC_LBO + (r & 7) * 16);
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(g ? g : (const void*)la.A),
+                       "r"(g ? 16 : 0)
+                       : "memory");
+        }
+      }
+      if constexpr (kDirectB) {
+#pragma unroll
+        for (int h = 0; h < B_CHUNKS; ++h) {
+          const int c = tid + h * TC_THREADS, r = c % BN, kg = c / BN;
+          const void* g = lb.src(n0 + r, k0 + 8 * kg);
+          const uint32_t d = tc_smem_u32(st + A_BYTES + (r >> 3) * TC_SBO + kg * TC_LBO + (r & 7) * 16);
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(g ? g : (const void*)lb.A),
+                       "r"(g ? 16 : 0)
+                       : "memory");
+        }
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
   };
-  auto stash = [&](int q) {  // registers -> the block's stage
+  auto stash = [&](int q) {  // register-path chunks -> the block's stage
     unsigned char* sa = base + (q % TC_STAGES) * STAGE;
+    if constexpr (!kDirectA) {
 #pragma unroll
-    for (int h = 0; h < A_CHUNKS; ++h) {
-      const int c = tid + h * TC_THREADS, r = c % TC_BM, kg = c / TC_BM;
-      *reinterpret_cast<uint4*>(sa + (r >> 3) * TC_SBO + kg * TC_LBO + (r & 7) * 16) = ra[h];
+      for (int h = 0; h < A_CHUNKS; ++h) {
+        const int c = tid + h * TC_THREADS, r = c % TC_BM, kg = c / TC_BM;
+        *reinterpret_cast<uint4*>(sa + (r >> 3) * TC_SBO + kg * TC_LBO + (r & 7) * 16) = ra[h];
+      }
     }
     if constexpr (!kDirectB) {
       unsigned char* sb = sa + A_BYTES;
@@ -271,10 +293,12 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<BN>::MINB)
     }
   };
 
-  if (nkb > 0) {
-    fetch(0);
-    copy_b(0);
-  }
+  // direct copies run D = STAGES - 1 blocks ahead of the MMAs
+  constexpr int D = TC_STAGES - 1;
+  if (nkb > 0) fetch(0);
+#pragma unroll
+  for (int d = 0; d < D; ++d)
+    if (d < nkb) copy_direct(d);
   for (int q = 0; q < nkb; ++q) {
     const int s = q % TC_STAGES;
     unsigned char* sa = base + s * STAGE;
@@ -283,7 +307,13 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<BN>::MINB)
     // practice, by the promotion or the direct-B copy of an earlier iteration)
     bool mine = q < TC_STAGES || wait_block(q - TC_STAGES);
     if (mine) stash(q);
-    if constexpr (kDirectB) asm volatile("cp.async.wait_all;" ::: "memory");
+    if constexpr (kDirectA || kDirectB) {  // block q's copies landed (newer ones may still fly)
+      if (D >= 2 && q + 1 < nkb) {
+        asm volatile("cp.async.wait_group 1;" ::: "memory");
+      } else {
+        asm volatile("cp.async.wait_all;" ::: "memory");
+      }
+    }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     ok = __syncthreads_and(ok && mine) != 0;
@@ -307,26 +337,25 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<BN>::MINB)
                        tc_smem_u32(bars + s))
                    : "memory");
     }
-    // next block's loads go out now and land while the tensor cores work and block q - 1 is promoted
-    if (q + 1 < nkb) {
-      fetch(q + 1);
-      if constexpr (kDirectB) {
-        // its stage was last read by block q + 1 - STAGES
-        if (q + 1 >= TC_STAGES) mine = wait_block(q + 1 - TC_STAGES);
-        if (mine) copy_b(q + 1);
-      }
-    }
+    // the next block's register-path loads go out now and land while the tensor cores work
+    if (q + 1 < nkb) fetch(q + 1);
     if constexpr (PROMOTE) {
       if (q > 0) {
         // block q - 1's region is refilled by block q + 1, issued only after the next barrier
-        ok = __syncthreads_and(wait_block(q - 1) && mine) != 0;
+        ok = __syncthreads_and(wait_block(q - 1)) != 0;
         if (!ok) break;
         promote(q - 1);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       }
-    } else {
-      ok = ok && mine;
     }
+    // direct copies of block q + D go to the stage block q - 1 read (finished once promoted)
+    if constexpr (kDirectA || kDirectB) {
+      if (q + D < nkb) {
+        if (!PROMOTE && q >= 1) mine = wait_block(q - 1);
+        if (mine) copy_direct(q + D);
+      }
+    }
+    if constexpr (!PROMOTE) ok = ok && mine;
   }
   if (nkb > 0 && ok) {
     ok = __syncthreads_and(wait_block(nkb - 1)) != 0;

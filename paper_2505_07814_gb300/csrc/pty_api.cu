@@ -102,6 +102,9 @@ size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspac
     w.wave = (float2*)take(sizeof(float2) * waves * NN);
     w.tmp = (float2*)take(sizeof(float2) * waves * NN);
     w.gscal = (float*)take(sizeof(float) * 4);
+    const size_t pieces = g.fft_impl == PTY_FFT_SPLIT3_BF16 ? 3 : 2;
+    w.pieces0 = take(2 * pieces * 2 * waves * NN);
+    w.pieces1 = take(2 * pieces * 2 * waves * NN);
   }
   if (out) *out = w;
   return off;

@@ -32,6 +32,8 @@ struct Workspace {
   float2* wave;    // [B][M][N*N]     current wave of every (position, mode)
   float2* tmp;     // [B][M][N*N]     half-transformed waves (transposed per wave)
   float* gscal;    // [4]             fp16 batch scaling: {max |x| bits, scale, -, -}
+  void* pieces0;   // [B][M][N][pieces][2N] 16-bit split operands of the tensor-core GEMMs
+  void* pieces1;   // (the same, for the second GEMM of a 2D transform)
 };
 
 // MODE_FORWARD: patterns only.  MODE_FORWARD_SAVE: patterns, keeping in the workspace what a later
