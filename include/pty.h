@@ -159,6 +159,20 @@ int pty_backward(const pty_geom* geom, int B, const int32_t* idx, const float* a
                  float* g_pos, float* g_tilt, float* g_dz, int accumulate, void* ws, size_t ws_bytes,
                  void* stream);
 
+/* Object constraints applied after an optimiser step (Sec. "Physical constraints": positivity,
+ * real-space depth regularization).  Each is relaxed: x <- x + r (C(x) - x) with r in [0, 1]
+ * (r = 1: the plain constraint, r = 0: off).  Order: the depth blur of amp and of phase (a
+ * Gaussian of standard deviation rz_sigma slices along the slice axis, truncated at 4 sigma and
+ * renormalised at the top and bottom of the volume), then clipping negative phase to zero. */
+typedef struct {
+  float phase_positivity; /* relaxation of the phase >= 0 clip, 0 = off */
+  float rz_sigma;         /* depth-blur standard deviation in slices, 0 = off (Nz <= 128 when on) */
+  float rz_relax;         /* relaxation of the depth blur */
+} pty_constraints;
+
+/* Applies `c` in place to amp and phase [Nz][H][W] (device pointers) on `stream`. */
+int pty_constrain(const pty_geom* geom, float* amp, float* phase, const pty_constraints* c, void* stream);
+
 /* One Adam step on the parameters in place using the gradients already in g_* (pty_adam state).
  * step is the 1-based Adam step count used for bias correction. */
 int pty_adam_update(const pty_geom* geom, float* amp, float* phase, float* probe, float* pos,

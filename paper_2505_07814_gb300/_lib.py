@@ -36,7 +36,7 @@ EXPORTS = ("pty_workspace_size", "pty_forward", "pty_loss_grad", "pty_adam_updat
            "pty_status", "pty_last_error", "pty_supported_sizes", "pty_launch_count", "pty_profile_enable",
            "pty_profile_read", "pty_loss_grad_noalloc", "pty_forward_save", "pty_backward",
            "pty_cnn_param_count", "pty_cnn_workspace_size", "pty_cnn_forward", "pty_cnn_loss_grad", "pty_cnn_adam",
-           "pty_cnn_train_step", "pty_cnn_targets", "pty_cnn_stitch", "pty_cnn_stitch_finish", "pty_cnn_read_state")
+           "pty_cnn_train_step", "pty_cnn_targets", "pty_cnn_stitch", "pty_cnn_stitch_finish", "pty_cnn_read_state", "pty_constrain")
 PROF_STAGES = ("prepare_object", "probe_spectrum", "forward", "loss", "loss_finalize", "adjoint", "object_grad",
                "probe_grad", "scalar_grad")
 
@@ -54,6 +54,10 @@ class pty_adam(ctypes.Structure):
                                                "m_pos", "v_pos", "m_tilt", "v_tilt", "m_dz", "v_dz")] + \
                [(n, ctypes.c_float) for n in ("lr_amp", "lr_phase", "lr_probe", "lr_pos", "lr_tilt", "lr_dz",
                                               "beta1", "beta2", "eps")]
+
+
+class pty_constraints(ctypes.Structure):
+    _fields_ = [("phase_positivity", ctypes.c_float), ("rz_sigma", ctypes.c_float), ("rz_relax", ctypes.c_float)]
 
 
 class PtyError(RuntimeError):
@@ -127,6 +131,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pty_cnn_stitch_finish.restype = I
     lib.pty_cnn_read_state.argtypes = [I, I, P, SZ, I, I, P, P]
     lib.pty_cnn_read_state.restype = I
+    lib.pty_constrain.argtypes = [G, P, P, ctypes.POINTER(pty_constraints), P]
+    lib.pty_constrain.restype = I
     _lib = lib
     return lib
 
@@ -256,3 +262,7 @@ def pty_cnn_stitch_finish(Nz, H, W, num, den, amp, phase, stream):
 
 def pty_cnn_read_state(S, B, ws, ws_bytes, layer, what, out, stream):
     _check(load().pty_cnn_read_state(S, B, ws, ws_bytes, layer, what, out, stream))
+
+
+def pty_constrain(geom, amp, phase, c: pty_constraints, stream):
+    _check(load().pty_constrain(ctypes.byref(geom), amp, phase, ctypes.byref(c), stream))

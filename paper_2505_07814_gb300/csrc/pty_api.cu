@@ -234,6 +234,43 @@ static int dispatch(const Problem& pb) {
 }
 
 // ---------------------------------------------------------------------------------------------
+// Object constraints (pty_constrain): one thread per (row, column) of the object walks its Nz
+// slices in registers: depth blur of amp and phase, then the relaxed phase positivity clip.
+// ---------------------------------------------------------------------------------------------
+constexpr int kMaxBlurSlices = 128;
+
+__global__ void k_constrain(float* __restrict__ amp, float* __restrict__ phase, int Nz, size_t plane, float sigma,
+                            float rz_relax, float pos_relax) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < plane; i += (size_t)gridDim.x * blockDim.x) {
+    if (sigma > 0.f) {
+      const int R = (int)ceilf(4.0f * sigma);
+      for (int which = 0; which < 2; ++which) {
+        float* x = which ? phase : amp;
+        float v[kMaxBlurSlices];
+        for (int s = 0; s < Nz; ++s) v[s] = x[(size_t)s * plane + i];
+        for (int s = 0; s < Nz; ++s) {
+          float num = 0.f, den = 0.f;
+          const int t0 = s - R > 0 ? s - R : 0, t1 = s + R < Nz - 1 ? s + R : Nz - 1;
+          for (int t = t0; t <= t1; ++t) {
+            const float d = (float)(t - s) / sigma;
+            const float w = expf(-0.5f * d * d);
+            num = fmaf(w, v[t], num);
+            den += w;
+          }
+          x[(size_t)s * plane + i] = v[s] + rz_relax * (num / den - v[s]);
+        }
+      }
+    }
+    if (pos_relax > 0.f) {
+      for (int s = 0; s < Nz; ++s) {
+        const float p = phase[(size_t)s * plane + i];
+        if (p < 0.f) phase[(size_t)s * plane + i] = p - pos_relax * p;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
 // Adam (PyTorch semantics), one launch over every enabled parameter.
 // ---------------------------------------------------------------------------------------------
 struct AdamSeg {
@@ -351,6 +388,31 @@ int pty_backward(const pty_geom* geom, int B, const int32_t* idx, const float* a
   pb.g_dz = g_dz;
   pb.accumulate = accumulate ? 1 : 0;
   return dispatch(pb);
+}
+
+int pty_constrain(const pty_geom* geom, float* amp, float* phase, const pty_constraints* c, void* stream) {
+  int rc = validate_geom(geom);
+  if (rc) return rc;
+  REQUIRE(c && amp && phase, "NULL argument");
+  REQUIRE(aligned(amp, 4) && aligned(phase, 4), "float arrays must be 4-byte aligned");
+  REQUIRE(c->phase_positivity >= 0.f && c->phase_positivity <= 1.f, "phase_positivity %g outside [0, 1]",
+          c->phase_positivity);
+  REQUIRE(c->rz_relax >= 0.f && c->rz_relax <= 1.f, "rz_relax %g outside [0, 1]", c->rz_relax);
+  REQUIRE(c->rz_sigma >= 0.f && isfinite(c->rz_sigma), "rz_sigma %g must be finite and >= 0", c->rz_sigma);
+  const bool blur = c->rz_sigma > 0.f && c->rz_relax > 0.f;
+  REQUIRE(!blur || geom->Nz <= kMaxBlurSlices, "the depth blur supports Nz <= %d", kMaxBlurSlices);
+  if (!blur && c->phase_positivity == 0.f) return PTY_OK;
+  const size_t plane = (size_t)geom->H * geom->W;
+  const unsigned blocks = (unsigned)((plane + 255) / 256 < 152 * 16 ? (plane + 255) / 256 : 152 * 16);
+  k_constrain<<<blocks, 256, 0, (cudaStream_t)stream>>>(amp, phase, geom->Nz, plane, blur ? c->rz_sigma : 0.f,
+                                                        c->rz_relax, c->phase_positivity);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("k_constrain launch failed: %s", cudaGetErrorString(e));
+    return PTY_ECUDA;
+  }
+  note_launch();
+  return PTY_OK;
 }
 
 int pty_adam_update(const pty_geom* geom, float* amp, float* phase, float* probe, float* pos, float* tilt,

@@ -221,6 +221,17 @@ def step(pt: Ptycho, params: Params, grads: Params, adam: Adam, idx, I_meas: tor
     return pt.loss
 
 
+def constrain(pt: Ptycho, params: Params, phase_positivity: float = 0.0, rz_sigma: float = 0.0,
+              rz_relax: float = 1.0):
+    """Object constraints after an optimiser step (pty_constrain): relaxed depth blur of amp and
+    phase along the slices, then the relaxed phase >= 0 clip; in place on params.amp / params.phase."""
+    g = pt.geom
+    nobj = g.Nz * g.H * g.W
+    c = _lib.pty_constraints(float(phase_positivity), float(rz_sigma), float(rz_relax))
+    _lib.pty_constrain(pt.cg, _ptr(params.amp, torch.float32, nobj, "amp"),
+                       _ptr(params.phase, torch.float32, nobj, "phase"), c, pt._stream())
+
+
 class _ForwardModel(torch.autograd.Function):
     """I = f(amp, phase, probe, pos, tilt, dz) for one batch, differentiated by the library's adjoint."""
 
