@@ -1,5 +1,6 @@
 """FP64 oracle of the object constraints applied after each optimiser step (Sec. "Physical
-constraints": "Positivity and sparsity", "Real-space depth regularization").
+constraints": "Positivity and sparsity", and the r_z filter of "Real-space depth regularization",
+Eq. 13).
 
 TEST INFRASTRUCTURE ONLY: imported by tests/ alone.
 

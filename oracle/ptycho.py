@@ -15,6 +15,8 @@ exactly what the paper's forward model defines (PtyRAD, arXiv 2505.07814):
 * Eq. 3  multislice exit wave, propagator between slices           -> `exit_wave`
 * Eq. 4  adaptive Fresnel propagator with local tilt               -> `propagator`
 * Eq. 5, 6  Gaussian / Poisson negative log-likelihood losses      -> `loss_value`, `loss_grad_I`
+* the PACBED and sparsity terms of the weighted total loss
+  (Sec. "Loss functions", Eq. 7-9)                                 -> `pacbed_*`, `sparse_*`
 * the derivative of the loss with respect to all six parameters
   (object amplitude and phase, probe, positions, tilts, dz),
   written out by hand as the adjoint of each step                  -> `loss_and_grad`
@@ -31,7 +33,12 @@ Readings where the paper is silent (each also listed in the design notes):
       of the batch; eps = 1e-6 sits inside the log, added to I_model^p;
   R7  where I_model = 0 and p < 1, dI^p/dI is taken as 0;
   R8  complex gradients follow dL/dRe + i dL/dIm; amp/phase gradients are real;
-  R9  one object mode.
+  R9  one object mode;
+  R10 total loss = (Eq. 5 or 6) + w_pacbed L_PACBED + w_sparse L_sparse (the weights of Eq. 9 with
+      the chosen likelihood at weight 1); L_PACBED raises the batch-mean patterns to p_pacbed
+      (default 0.5) and normalises by <I_meas^p_pacbed>_{D,B}; L_sparse averages |phase|^p_sparse
+      (default 1) over every slice of every batch position's N x N patch (a pixel reached by two
+      positions counts twice); sign(0) = 0 and |x|^(p - 1) = 0 at x = 0 for p < 1.
 
 Array conventions: row-major, axis 0 = rows, axis 1 = columns; k_a = fftfreq(N, dx) in 1/angstrom;
 positions and tilts are (axis-0, axis-1) pairs; the probe is [M][N][N]; the object amplitude and
@@ -60,6 +67,10 @@ class Geometry:
     p: float | None = None  # exponent on the patterns; default 1 (Poisson) / 0.5 (Gaussian)
     eps: float = 1e-6
     global_tilt: bool = False  # one tilt for all positions instead of one per position
+    w_pacbed: float = 0.0  # weight of the PACBED term (reading R10)
+    p_pacbed: float | None = None  # its exponent, default 0.5
+    w_sparse: float = 0.0  # weight of the phase sparsity term
+    p_sparse: float | None = None  # its exponent, default 1
 
     @property
     def power(self) -> float:
@@ -211,6 +222,56 @@ def loss_grad_I(geom, I_model, I_meas):
     raise ValueError(geom.loss)
 
 
+def pacbed_value(geom, I_model, I_meas):
+    """L_PACBED: the batch-mean patterns (position-averaged CBED) compared like Eq. 5."""
+    p = 0.5 if geom.p_pacbed is None else float(geom.p_pacbed)
+    d = _pow(I_model.mean(axis=0), p) - _pow(I_meas.mean(axis=0), p)
+    return np.sqrt(np.mean(d ** 2)) / np.mean(_pow(I_meas, p))
+
+
+def pacbed_grad_I(geom, I_model, I_meas):
+    """dL_PACBED / dI_model: the same for every pattern of the batch (each enters the mean 1/B)."""
+    p = 0.5 if geom.p_pacbed is None else float(geom.p_pacbed)
+    B = I_model.shape[0]
+    A = I_model.mean(axis=0)
+    d = _pow(A, p) - _pow(I_meas.mean(axis=0), p)
+    ms = np.mean(d ** 2)
+    if ms == 0.0:
+        return np.zeros_like(I_model)
+    g = d / (d.size * np.sqrt(ms)) / np.mean(_pow(I_meas, p)) * _dpow(A, p) / B
+    return np.broadcast_to(g, I_model.shape).copy()
+
+
+def _patches(phase, corners, N):
+    return [np.asarray(phase, dtype=np.float64)[:, r0:r0 + N, r1:r1 + N] for r0, r1 in corners]
+
+
+def sparse_value(geom, phase, corners):
+    """L_sparse = <|phase|^p>^(1/p) over the batch's patches (reading R10)."""
+    p = 1.0 if geom.p_sparse is None else float(geom.p_sparse)
+    v = np.concatenate([np.abs(x).ravel() for x in _patches(phase, corners, geom.N)])
+    return float(np.mean(v ** p) ** (1.0 / p))
+
+
+def sparse_grad_phase(geom, phase, corners):
+    p = 1.0 if geom.p_sparse is None else float(geom.p_sparse)
+    N = geom.N
+    pats = _patches(phase, corners, N)
+    n = sum(x.size for x in pats)
+    S = sum(float(np.sum(np.abs(x) ** p)) for x in pats)
+    g = np.zeros(np.shape(phase))
+    if S == 0.0:
+        return g
+    scale = (S / n) ** (1.0 / p - 1.0) / n
+    for (r0, r1), x in zip(corners, pats):
+        a = np.abs(x)
+        w = np.zeros_like(a)
+        nz = a > 0
+        w[nz] = a[nz] ** (p - 1.0)
+        g[:, r0:r0 + N, r1:r1 + N] += scale * w * np.sign(x)
+    return g
+
+
 # ----------------------------------------------------------------------------------------------
 # Loss and gradients of all six parameters (hand-written adjoint of every step above)
 # ----------------------------------------------------------------------------------------------
@@ -273,6 +334,9 @@ def loss_and_grad(geom, amp, phase, probe, pos, tilt, dz, I_meas, idx):
     Imeas_b = np.stack([np.asarray(I_meas[j], dtype=np.float64) for j in idx])
     loss = loss_value(geom, I_model, Imeas_b)
     dLdI = loss_grad_I(geom, I_model, Imeas_b)
+    if geom.w_pacbed:
+        loss += geom.w_pacbed * pacbed_value(geom, I_model, Imeas_b)
+        dLdI = dLdI + geom.w_pacbed * pacbed_grad_I(geom, I_model, Imeas_b)
 
     # ---------------- adjoint ----------------
     gT = np.zeros_like(T)
@@ -322,5 +386,9 @@ def loss_and_grad(geom, amp, phase, probe, pos, tilt, dz, I_meas, idx):
     # T = amp e^{i phase}:  dL/damp = Re(conj(e^{i phase}) gT),  dL/dphase = Re(conj(i T) gT)
     g_amp = np.real(np.conj(np.exp(1j * phase)) * gT)
     g_phase = np.real(np.conj(1j * T) * gT)
+    if geom.w_sparse:
+        corners = [tuple(crop_index(pos[j])[0]) for j in idx]
+        loss += geom.w_sparse * sparse_value(geom, phase, corners)
+        g_phase = g_phase + geom.w_sparse * sparse_grad_phase(geom, phase, corners)
     return Gradients(loss=float(loss), I_model=I_model, amp=g_amp, phase=g_phase, probe=g_probe,
                      pos=g_pos, tilt=g_tilt, dz=float(g_dz))
