@@ -100,6 +100,13 @@ typedef struct {
                       (5*B*M*N^2*8 for three-piece bf16).  The first
                       split call on a device builds its DFT tables and waits for them (not
                       capturable into a CUDA graph). */
+  float w_pacbed;  /* weight of the PACBED term (Eq. 7) added to the loss of pty_loss_grad / pty_step:
+                      the batch-mean modelled pattern against the batch-mean measured one, compared
+                      like Eq. 5 with exponent p_pacbed (<= 0: 0.5); 0 = off */
+  float p_pacbed;
+  float w_sparse;  /* weight of the phase-sparsity term (Eq. 8): <|phase|^p_sparse>^(1/p_sparse) over
+                      every slice of every batch position's N x N patch (p_sparse <= 0: 1); 0 = off */
+  float p_sparse;
 } pty_geom;
 
 enum { PTY_FFT_FP32 = 0, PTY_FFT_SPLIT_BF16 = 1, PTY_FFT_SPLIT_FP16 = 2, PTY_FFT_SPLIT3_BF16 = 3 };

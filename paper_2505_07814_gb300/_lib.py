@@ -46,7 +46,8 @@ class pty_geom(ctypes.Structure):
                 ("W", ctypes.c_int), ("Ntot", ctypes.c_int), ("dx", ctypes.c_float),
                 ("lambda_", ctypes.c_float), ("loss", ctypes.c_int), ("p", ctypes.c_float),
                 ("eps", ctypes.c_float), ("grad_mask", ctypes.c_int), ("global_tilt", ctypes.c_int),
-                ("ckpt_stride", ctypes.c_int), ("fft_impl", ctypes.c_int)]
+                ("ckpt_stride", ctypes.c_int), ("fft_impl", ctypes.c_int), ("w_pacbed", ctypes.c_float),
+                ("p_pacbed", ctypes.c_float), ("w_sparse", ctypes.c_float), ("p_sparse", ctypes.c_float)]
 
 
 class pty_adam(ctypes.Structure):

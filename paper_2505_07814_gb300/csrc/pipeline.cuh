@@ -551,7 +551,19 @@ struct LossArgs {
   float* I_model;
   float* u;
   double* lpart;
+  // PACBED term (nullptr when off): batch sums of I_model and I_meas in k-space order, and the
+  // per-pattern sums of I_meas^pac_p
+  float* pac;
+  double* pacpart;
+  float pac_p;
 };
+
+// x^p for x >= 0 (0 for x <= 0 when p != 1), with the common exponents exact.
+__device__ __forceinline__ float pow_nn(float x, float p) {
+  if (p == 1.0f) return x;
+  if (x <= 0.f) return 0.f;
+  return p == 0.5f ? sqrtf(x) : powf(x, p);
+}
 
 template <int N>
 __host__ __device__ constexpr size_t loss_smem_bytes() {
@@ -626,7 +638,7 @@ __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
   __syncthreads();
   const float* Id = a.I_meas ? a.I_meas + (size_t)checked_index(a.idx, b, a.Ntot, a.status) * NN : nullptr;
   const float p = a.p;
-  float sd = 0.f, st = 0.f;
+  float sd = 0.f, st = 0.f, sp = 0.f;
   for (int q = tid; q < NN; q += T) {
     const int k0 = (q / N + N / 2) & (N - 1), k1 = (q % N + N / 2) & (N - 1);
     const int l = kpos1<N>(k1) * RS + kpos0<N>(k0);  // staging row p1, column p0 (global p1 * N + p0)
@@ -639,6 +651,12 @@ __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
       sd += Dp;
       st += term;
       L[l] = u;
+      if (a.pac) {
+        const int e = kpos1<N>(k1) * N + kpos0<N>(k0);
+        atomicAdd(a.pac + e, I);
+        atomicAdd(a.pac + NN + e, d);
+        sp += pow_nn(d, a.pac_p);
+      }
     }
   }
   __syncthreads();
@@ -653,6 +671,12 @@ __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
       a.lpart[2 * b + 1] = y;
     }
   }
+  if (a.pac) {
+    __syncthreads();
+    double x = sp, y = 0.0;
+    block_sum2<T>(x, y, red);
+    if (tid == 0) a.pacpart[b] = x;
+  }
 }
 
 // The same without shared-memory staging (the N = 256 staging area would not fit): walks the
@@ -665,7 +689,7 @@ __global__ void __launch_bounds__(T) k_loss_gather(LossArgs a) {
   const int b = blockIdx.x, tid = threadIdx.x;
   const float* Im = a.Imode + (size_t)b * a.M * NN;
   const float* Id = a.I_meas ? a.I_meas + (size_t)checked_index(a.idx, b, a.Ntot, a.status) * NN : nullptr;
-  float sd = 0.f, st = 0.f;
+  float sd = 0.f, st = 0.f, sp = 0.f;
   for (int e = tid; e < NN; e += T) {  // e = p1 * N + p0
     float I = 0.f;
     for (int m = 0; m < a.M; ++m) I += Im[(size_t)m * NN + e];
@@ -674,10 +698,16 @@ __global__ void __launch_bounds__(T) k_loss_gather(LossArgs a) {
     if (a.I_model) a.I_model[(size_t)b * NN + q] = I;
     if (Id) {
       float term, u, Dp;
-      loss_pixel(I, Id[q], a.p, a.eps, a.loss, &term, &Dp, &u);
+      const float d = Id[q];
+      loss_pixel(I, d, a.p, a.eps, a.loss, &term, &Dp, &u);
       sd += Dp;
       st += term;
       a.u[(size_t)b * NN + e] = u;
+      if (a.pac) {
+        atomicAdd(a.pac + e, I);
+        atomicAdd(a.pac + NN + e, d);
+        sp += pow_nn(d, a.pac_p);
+      }
     }
   }
   if (a.lpart) {
@@ -687,6 +717,49 @@ __global__ void __launch_bounds__(T) k_loss_gather(LossArgs a) {
       a.lpart[2 * b] = x;
       a.lpart[2 * b + 1] = y;
     }
+  }
+  if (a.pac) {
+    __syncthreads();
+    double x = sp, y = 0.0;
+    block_sum2<T>(x, y, red);
+    if (tid == 0) a.pacpart[b] = x;
+  }
+}
+
+// PACBED term (Eq. 7) of one batch, one CTA of 1024 threads: the batch-mean patterns A and C from
+// the sums, d = A^p - C^p, the loss w sqrt(<d^2>) / <I_meas^p> added to *loss_out, and the
+// derivative w d p A^(p-1) / (<I_meas^p> N^2 B sqrt(<d^2>)), the same for every pattern, written to
+// pac[2 N^2 ..] (k-space order) for the adjoint.
+template <int N>
+__global__ void __launch_bounds__(1024) k_pacbed(float* __restrict__ pac, const double* __restrict__ pacpart, int B,
+                                                 float p, float w, double* loss_out, double* scal, int* status) {
+  constexpr int NN = N * N;
+  __shared__ double red[64];
+  __shared__ double sh[2];
+  const int tid = threadIdx.x;
+  const float inv_b = 1.0f / (float)B;
+  double m2 = 0.0, z = 0.0;
+  for (int e = tid; e < NN; e += 1024) {
+    const float d = pow_nn(pac[e] * inv_b, p) - pow_nn(pac[NN + e] * inv_b, p);
+    m2 += (double)d * d;
+  }
+  for (int b = tid; b < B; b += 1024) z += pacpart[b];
+  block_sum2<1024>(m2, z, red);
+  if (tid == 0) {
+    const double ms = m2 / NN, Z = z / ((double)NN * B);
+    const double L = sqrt(ms) / Z;
+    if (!isfinite(L)) atomicOr(status, PTY_ENONFINITE);
+    sh[0] = ms > 0.0 && Z > 0.0 ? (double)w / (Z * NN * B * sqrt(ms)) : 0.0;
+    scal[2] = L;
+    if (loss_out) *loss_out += (double)w * L;
+  }
+  __syncthreads();
+  const float c = (float)sh[0];
+  for (int e = tid; e < NN; e += 1024) {
+    const float A = pac[e] * inv_b;
+    const float d = pow_nn(A, p) - pow_nn(pac[NN + e] * inv_b, p);
+    const float dpow = p == 1.0f ? 1.0f : (A > 0.f ? p * powf(A, p - 1.0f) : 0.f);
+    pac[2 * NN + e] = c * d * dpow;
   }
 }
 
@@ -740,6 +813,7 @@ struct AdjArgs {
   float2* gT;
   float2* gPhat;
   double* spart;  // [wave][5], accumulated over the segments of one pass
+  const float* pacg;  // PACBED dL/dI [N*N] (k-space) or nullptr
   int* status;
   // slices [s0, s1) of this launch; the adjoint wave is carried between launches in gstate
   int s0, s1;
@@ -761,6 +835,8 @@ struct FarGradLoad {
   const float* u;
   const float2* Psi;
   float gs;
+  const float* pg = nullptr;  // PACBED dL/dI (the same for every pattern), or nullptr
+  float gp = 0.f;             // its factor 2 / N
   template <int K>
   __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     float2 p[K];
@@ -769,10 +845,11 @@ struct FarGradLoad {
     for (int k = 0; k < K; ++k) {
       const int e = kidx<N>(r0 + k * rs, c0 + k * cs);
       p[k] = ld_ro(Psi + e);
-      w[k] = ld_ro(u + e);
+      w[k] = gs * ld_ro(u + e);
+      if (pg) w[k] = fmaf(gp, ld_ro(pg + e), w[k]);
     }
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = cscale(p[k], gs * w[k]);
+    for (int k = 0; k < K; ++k) v[k] = cscale(p[k], w[k]);
   }
 };
 // transmission of slice s backwards: dL/dT += conj(psi_in) g (scatter-add), g <- conj(T) g
@@ -911,7 +988,8 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   if (a.s1 == a.Nz) {
     // g_psi = F_ortho^-1[2 dL/dI Psi] = (1/N) unnormalised inverse of 2 dL/dI Psi; its column step
     // is fused with the last slice's transmission below (same step structure as the forward kernel).
-    FarGradLoad<N> farg{a.u + (size_t)b * NN, a.Psi + (size_t)bm * NN, (float)(2.0 * a.scal[0] / N)};
+    FarGradLoad<N> farg{a.u + (size_t)b * NN, a.Psi + (size_t)bm * NN, (float)(2.0 * a.scal[0] / N), a.pacg,
+                        2.0f / N};
     F::row_inv(s, tw, farg);
     F::block_inv(s, tw);
   } else {
@@ -983,6 +1061,68 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   if (a.s0 > 0) {  // hand the adjoint wave to the launch of the previous segment
     float2* g = a.gstate + (size_t)bm * NN + (size_t)F::rank() * F::ROWS * N;
     for (int e = tid; e < F::ROWS * N; e += T) g[e] = s[(e / N) * RS + e % N];
+  }
+}
+
+// ---------------------------------------------------------------------------------------------
+// Phase-sparsity term (Eq. 8): <|phase|^p>^(1/p) over every slice of every batch position's patch
+// ---------------------------------------------------------------------------------------------
+// one CTA per (position, slice): the patch's sum of |phase|^p (FP64)
+template <int N, int T>
+__global__ void __launch_bounds__(T) k_sparse_sum(const float* __restrict__ phase, const float* __restrict__ pos,
+                                                  const int32_t* __restrict__ idx, int Ntot, int H, int W, int Nz,
+                                                  float p, double* __restrict__ part, int* status) {
+  __shared__ double red[2 * (T / 32)];
+  const int b = blockIdx.x / Nz, sl = blockIdx.x % Nz;
+  const int j = checked_index(idx, b, Ntot, status);
+  int i0, i1;
+  float d0, d1;
+  patch_corner<N>(pos, j, H, W, &i0, &i1, &d0, &d1, status);
+  const float* ph = phase + (size_t)sl * H * W + (size_t)i0 * W + i1;
+  double acc = 0.0;
+  for (int e = threadIdx.x; e < N * N; e += T) acc += pow_nn(fabsf(ph[(size_t)(e / N) * W + e % N]), p);
+  double y = 0.0;
+  block_sum2<T>(acc, y, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = acc;
+}
+
+// the term (added to *loss_out) and the gradient factor (S/n)^(1/p - 1) / n into scal[3]
+static __global__ void k_sparse_finalize(const double* __restrict__ part, int nparts, double n, float p, float w,
+                                         double* loss_out, double* scal, int* status) {
+  __shared__ double red[16];
+  double x = 0.0, y = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) x += part[i];
+  block_sum2<256>(x, y, red);
+  if (threadIdx.x == 0) {
+    const double mean = x / n;
+    const double L = mean > 0.0 ? pow(mean, 1.0 / p) : 0.0;
+    if (!isfinite(L)) atomicOr(status, PTY_ENONFINITE);
+    scal[3] = mean > 0.0 ? pow(mean, 1.0 / p - 1.0) / n : 0.0;
+    if (loss_out) *loss_out += (double)w * L;
+  }
+}
+
+// dL/dphase += w scal[3] |phase|^(p - 1) sign(phase) at every patch pixel (float atomics: a pixel
+// reached by several positions collects each)
+template <int N, int T>
+__global__ void __launch_bounds__(T) k_sparse_grad(const float* __restrict__ phase, const float* __restrict__ pos,
+                                                   const int32_t* __restrict__ idx, int Ntot, int H, int W, int Nz,
+                                                   float p, float w, const double* __restrict__ scal,
+                                                   float* __restrict__ g_phase, int* status) {
+  const int b = blockIdx.x / Nz, sl = blockIdx.x % Nz;
+  const int j = checked_index(idx, b, Ntot, status);
+  int i0, i1;
+  float d0, d1;
+  patch_corner<N>(pos, j, H, W, &i0, &i1, &d0, &d1, status);
+  const size_t base = (size_t)sl * H * W + (size_t)i0 * W + i1;
+  const float c = w * (float)scal[3];
+  for (int e = threadIdx.x; e < N * N; e += T) {
+    const size_t o = base + (size_t)(e / N) * W + e % N;
+    const float x = phase[o], a = fabsf(x);
+    if (a > 0.f) {
+      const float wp = p == 1.0f ? 1.0f : powf(a, p - 1.0f);
+      atomicAdd(g_phase + o, copysignf(c * wp, x));
+    }
   }
 }
 
@@ -1243,6 +1383,11 @@ struct Pass {
     la.I_model = pb.I_model;
     la.u = I_meas ? ws.u : nullptr;
     la.lpart = I_meas ? ws.lpart : nullptr;
+    const bool pac = I_meas && pb.w_pac > 0.f && ws.pac;
+    la.pac = pac ? ws.pac : nullptr;
+    la.pacpart = pac ? ws.pacpart : nullptr;
+    la.pac_p = pb.p_pac;
+    if (pac && cudaMemsetAsync(ws.pac, 0, sizeof(float) * 2 * NN, st) != cudaSuccess) return memset_failed();
     if constexpr (N == 256) {
       k_loss_gather<N, T><<<pb.B, T, 0, st>>>(la);
     } else {
@@ -1252,6 +1397,11 @@ struct Pass {
     if (I_meas) {
       k_loss_finalize<<<1, 256, 0, st>>>(ws.lpart, pb.B, pb.loss, (double)pb.B * NN, ws.scal, pb.loss_out, ws.status);
       PTY_LAUNCH_CHECK("k_loss_finalize", 4);
+      if (pac) {
+        k_pacbed<N><<<1, 1024, 0, st>>>(ws.pac, ws.pacpart, pb.B, pb.p_pac, pb.w_pac, pb.loss_out, ws.scal,
+                                        ws.status);
+        PTY_LAUNCH_CHECK("k_pacbed", -1);
+      }
     }
     return PTY_OK;
   }
@@ -1298,6 +1448,7 @@ struct Pass {
     aa.gT = ws.gT;
     aa.gPhat = ws.gPhat;
     aa.spart = ws.spart;
+    aa.pacg = (pb.mode == MODE_GRAD && pb.w_pac > 0.f && ws.pac) ? ws.pac + 2 * NN : nullptr;
     aa.status = ws.status;
     aa.gstate = ws.gstate;
     return aa;
@@ -1358,7 +1509,8 @@ struct Pass {
     return PTY_OK;
   }
 
-  // dL/damp, dL/dphase, dL/dprobe and the scalar gradients from the accumulators.
+  // dL/damp, dL/dphase, dL/dprobe and the scalar gradients from the accumulators; then the
+  // phase-sparsity term of the loss and its gradient.
   int finalize() {
     const int gm = pb.grad_mask;
     const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
@@ -1366,6 +1518,23 @@ struct Pass {
       k_object_grad<<<object_blocks(), 256, 0, st>>>(pb.amp, pb.phase, ws.gT, (gm & PTY_GRAD_AMP) ? pb.g_amp : nullptr,
                                                      (gm & PTY_GRAD_PHASE) ? pb.g_phase : nullptr, pb.accumulate, nobj);
       PTY_LAUNCH_CHECK("k_object_grad", 6);
+    }
+    if (pb.mode == MODE_GRAD && pb.w_sp > 0.f && ws.sppart && pb.B > 0) {
+      const unsigned patches = (unsigned)(pb.B * pb.Nz);
+      k_sparse_sum<N, 256><<<patches, 256, 0, st>>>(pb.phase, pb.pos, pb.idx, pb.Ntot, pb.H, pb.W, pb.Nz, pb.p_sp,
+                                                    ws.sppart, ws.status);
+      PTY_LAUNCH_CHECK("k_sparse_sum", -1);
+      k_sparse_finalize<<<1, 256, 0, st>>>(ws.sppart, (int)patches, (double)patches * NN, pb.p_sp, pb.w_sp,
+                                           pb.loss_out, ws.scal, ws.status);
+      PTY_LAUNCH_CHECK("k_sparse_finalize", -1);
+      if ((gm & PTY_GRAD_PHASE) && pb.g_phase) {
+        if (!want_obj && !pb.accumulate &&
+            cudaMemsetAsync(pb.g_phase, 0, sizeof(float) * nobj, st) != cudaSuccess)
+          return memset_failed();
+        k_sparse_grad<N, 256><<<patches, 256, 0, st>>>(pb.phase, pb.pos, pb.idx, pb.Ntot, pb.H, pb.W, pb.Nz, pb.p_sp,
+                                                       pb.w_sp, ws.scal, pb.g_phase, ws.status);
+        PTY_LAUNCH_CHECK("k_sparse_grad", -1);
+      }
     }
     if (want_probe) {
       PTY_LAUNCH_RC(launch_waves<C>(k_probe_grad<N, T>, pb.M, T, probe_smem(), st, (const float2*)ws.gPhat,

@@ -97,6 +97,11 @@ size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspac
     if (want_obj) w.gT = (float2*)take(sizeof(float2) * nobj);
     if (want_probe) w.gPhat = (float2*)take(sizeof(float2) * g.M * NN);
     w.spart = (double*)take(sizeof(double) * 5 * (waves > 0 ? waves : 1));
+    if (g.w_pacbed > 0.f) {
+      w.pac = (float*)take(sizeof(float) * 3 * NN);
+      w.pacpart = (double*)take(sizeof(double) * (size_t)(B > 0 ? B : 1));
+    }
+    if (g.w_sparse > 0.f) w.sppart = (double*)take(sizeof(double) * (size_t)(B > 0 ? B : 1) * g.Nz);
   }
   if (g.fft_impl != PTY_FFT_FP32) {
     w.wave = (float2*)take(sizeof(float2) * waves * NN);
@@ -144,6 +149,11 @@ static int validate_geom(const pty_geom* g) {
   }
   if (g->fft_impl != PTY_FFT_FP32 && g->N != 64 && g->N != 128) {
     set_error("split-precision DFTs support N = 64 and 128, not %d", g->N);
+    return PTY_EINVAL;
+  }
+  if (!(g->w_pacbed >= 0.f) || !(g->w_sparse >= 0.f) || !isfinite(g->w_pacbed) || !isfinite(g->w_sparse) ||
+      !isfinite(g->p_pacbed) || !isfinite(g->p_sparse)) {
+    set_error("w_pacbed, w_sparse must be finite and >= 0, p_pacbed, p_sparse finite");
     return PTY_EINVAL;
   }
   if (g->ckpt_stride < 0) {
@@ -204,6 +214,10 @@ static int prepare(const pty_geom* g, int B, int mode, const int32_t* idx, const
   pb->mode = mode;
   pb->kstride = effective_stride(*g);
   pb->fft_impl = g->fft_impl;
+  pb->w_pac = g->w_pacbed;
+  pb->p_pac = g->p_pacbed > 0.f ? g->p_pacbed : 0.5f;
+  pb->w_sp = g->w_sparse;
+  pb->p_sp = g->p_sparse > 0.f ? g->p_sparse : 1.0f;
   pb->idx = idx;
   pb->amp = amp;
   pb->phase = phase;

@@ -32,6 +32,10 @@ struct Workspace {
   float2* wave;    // [B][M][N*N]     current wave of every (position, mode)
   float2* tmp;     // [B][M][N*N]     half-transformed waves (transposed per wave)
   float* gscal;    // [4]             fp16 batch scaling: {max |x| bits, scale, -, -}
+  // extra loss terms (when their weights are non-zero)
+  float* pac;      // [3][N*N]        sum over the batch of I_model, of I_meas (k-space), PACBED dL/dI
+  double* pacpart; // [B]             per-pattern sums of I_meas^p_pacbed
+  double* sppart;  // [B][Nz]         per-patch sums of |phase|^p_sparse
   void* pieces0;   // [B][M][N][pieces][2N] 16-bit split operands of the tensor-core GEMMs
   void* pieces1;   // (the same, for the second GEMM of a 2D transform)
 };
@@ -49,6 +53,7 @@ struct Problem {
   int grad_mask, global_tilt, accumulate, mode;
   int kstride;  // slices per recompute segment (1: every slice's checkpoint is stored)
   int fft_impl;  // PTY_FFT_*
+  float w_pac, p_pac, w_sp, p_sp;  // extra loss terms (weights 0 = off), exponents resolved
   const int32_t* idx;
   const float *amp, *phase, *pos, *tilt, *dz;
   const float2* probe;

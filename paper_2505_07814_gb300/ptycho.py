@@ -37,6 +37,11 @@ class Geometry:
     # per-slice DFTs: "fp32" shared-memory FFT; split-precision tensor-core GEMMs "bf16" / "fp16"
     # (hi + lo pieces, three products) or "bf16x3" (three bf16 pieces, six products)
     fft: str = "fp32"
+    # extra loss terms (Eq. 7-9): PACBED and phase sparsity, weight 0 = off, exponent <= 0 = default
+    w_pacbed: float = 0.0
+    p_pacbed: float = 0.0
+    w_sparse: float = 0.0
+    p_sparse: float = 0.0
 
     @property
     def grad_mask(self) -> int:
@@ -48,7 +53,8 @@ class Geometry:
     def c(self) -> _lib.pty_geom:
         return _lib.pty_geom(self.N, self.M, self.Nz, self.H, self.W, self.Ntot, self.dx, self.lam,
                              LOSS[self.loss], self.p, self.eps, self.grad_mask, int(self.global_tilt),
-                             int(self.ckpt_stride), FFT_IMPL[self.fft])
+                             int(self.ckpt_stride), FFT_IMPL[self.fft], float(self.w_pacbed), float(self.p_pacbed),
+                             float(self.w_sparse), float(self.p_sparse))
 
     def checkpoint_bytes(self, B: int) -> int:
         """Bytes the adjoint's forward record takes for a batch of B positions (see ckpt_stride)."""
