@@ -347,6 +347,41 @@ def run_nmse(args):
     print(json.dumps(line), flush=True)
 
 
+def run_constrain(args, w, geom, params, flush, torch, Ptycho):
+    """pty_constrain on the workload's object: depth blur (sigma 1 slice) + positivity, HBM-bound
+    (amp and phase read and written once)."""
+    from paper_2505_07814_gb300.ptycho import constrain
+    pt = Ptycho(geom, 1)
+    for _ in range(args.warmup):
+        constrain(pt, params, phase_positivity=1.0, rz_sigma=1.0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    total = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        e0.record()
+        constrain(pt, params, phase_positivity=1.0, rz_sigma=1.0)
+        e1.record()
+        e1.synchronize()
+        total += e0.elapsed_time(e1)
+    ms = total / args.steps
+    nbytes = 2 * 2 * 4 * w.Nz * w.H * w.W
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak = json.load(fh).get("hbm_gbs")
+    except (OSError, ValueError):
+        pass
+    peak = peak or 6800.0
+    gbs = nbytes / (ms / 1e3) / 1e9
+    print(json.dumps({"metric": "object constraints (depth blur + positivity) per call", "value": ms, "unit": "ms",
+                      "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
+                      "config": {"workload": WORKLOADS[args.workload][0], "object": [w.Nz, w.H, w.W],
+                                 "rz_sigma": 1.0, "phase_positivity": 1.0},
+                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                                   "bytes": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}), flush=True)
+
+
 def cnn_flops(S=128, train=True):
     """Algorithmic flops of the learned initialiser per pattern: 2 x MACs of the six 3x3
     convolutions at their output resolutions (nearest upsampling counted on the upsampled grid);
@@ -441,6 +476,10 @@ def main():
     ap.add_argument("--nmse-epochs", type=int, default=8)
     ap.add_argument("--nmse-split", default="bf16,fp16", help="split-precision forms to time from the flat start")
     ap.add_argument("--cnn", action="store_true", help="learned-initialiser training / inference throughput")
+    ap.add_argument("--w-pacbed", type=float, default=0.0, help="weight of the PACBED loss term (Eq. 7)")
+    ap.add_argument("--w-sparse", type=float, default=0.0, help="weight of the phase-sparsity loss term (Eq. 8)")
+    ap.add_argument("--constrain", action="store_true",
+                    help="time pty_constrain (depth blur + positivity) on the workload's object instead")
     args = ap.parse_args()
     if args.cnn:
         run_cnn(args)
@@ -493,10 +532,13 @@ def main():
 
     def geometry(stride):
         return Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, Ntot=w.Ntot, dx=w.dx, lam=w.lam, loss="poisson",
-                        ckpt_stride=stride, fft=args.fft)
+                        ckpt_stride=stride, fft=args.fft, w_pacbed=args.w_pacbed, w_sparse=args.w_sparse)
 
     if args.sweep_ckpt:
         sweep_ckpt(args, w, geometry, params, I_meas, idx_t, flush, dev, torch, Ptycho)
+        return
+    if args.constrain:
+        run_constrain(args, w, geometry(1), params, flush, torch, Ptycho)
         return
     geom = geometry(args.ckpt_stride)
     pt = Ptycho(geom, B, device=dev)
@@ -612,7 +654,7 @@ def main():
                 "data": "synthetic",
                 "config": {"workload": "%s, batch %d" % (WORKLOADS[args.workload][0], B), "N": w.N, "M": w.M,
                            "Nz": w.Nz, "positions": w.Ntot, "batch": B, "ckpt_stride": args.ckpt_stride,
-                           "fft": args.fft,
+                           "fft": args.fft, "w_pacbed": args.w_pacbed, "w_sparse": args.w_sparse,
                            "checkpoint_bytes": geom.checkpoint_bytes(B),
                            "object": [w.Nz, w.H, w.W], "loss": "poisson", "grads": "amp,phase,probe,pos,tilt,dz",
                            "batches": "contiguous raster blocks", "start": "flat object (amp 1, phase U[0,1e-8])",

@@ -21,11 +21,16 @@ def _setup(Nz, H, W, seed=0):
     return Ptycho(geom, 1), params, amp.astype(np.float64), phase.astype(np.float64)
 
 
-@pytest.mark.parametrize("Nz,pos,sigma,relax", [(7, 1.0, 1.3, 0.6), (20, 0.5, 2.0, 1.0), (8, 1.0, 0.0, 1.0),
-                                               (1, 1.0, 1.0, 1.0), (5, 0.0, 0.7, 0.3)])
-def test_constrain_matches_oracle(Nz, pos, sigma, relax):
+# 70 x 90 takes the float4 path over 12 full tiles and a ragged one; 71 x 90 (plane not a multiple
+# of 4) the scalar path; Nz = 128 the largest depth, with more than 48 KB of shared memory per CTA.
+@pytest.mark.parametrize("Nz,H,W,pos,sigma,relax", [(7, 70, 90, 1.0, 1.3, 0.6), (20, 70, 90, 0.5, 2.0, 1.0),
+                                                   (8, 70, 90, 1.0, 0.0, 1.0), (1, 70, 90, 1.0, 1.0, 1.0),
+                                                   (5, 70, 90, 0.0, 0.7, 0.3), (6, 71, 90, 1.0, 1.1, 0.8),
+                                                   (3, 71, 90, 0.7, 0.0, 1.0), (128, 70, 90, 1.0, 3.0, 1.0),
+                                                   (40, 65, 66, 0.0, 30.0, 1.0)])
+def test_constrain_matches_oracle(Nz, H, W, pos, sigma, relax):
     from paper_2505_07814_gb300.ptycho import constrain
-    pt, params, amp, phase = _setup(Nz, 70, 90)
+    pt, params, amp, phase = _setup(Nz, H, W)
     constrain(pt, params, phase_positivity=pos, rz_sigma=sigma, rz_relax=relax)
     torch.cuda.synchronize()
     ra, rp = K.constrain(amp, phase, pos, sigma, relax)
