@@ -166,19 +166,42 @@ int pty_backward(const pty_geom* geom, int B, const int32_t* idx, const float* a
                  float* g_pos, float* g_tilt, float* g_dz, int accumulate, void* ws, size_t ws_bytes,
                  void* stream);
 
-/* Object constraints applied after an optimiser step (Sec. "Physical constraints": positivity,
- * real-space depth regularization).  Each is relaxed: x <- x + r (C(x) - x) with r in [0, 1]
- * (r = 1: the plain constraint, r = 0: off).  Order: the depth blur of amp and of phase (a
- * Gaussian of standard deviation rz_sigma slices along the slice axis, truncated at 4 sigma and
- * renormalised at the top and bottom of the volume), then clipping negative phase to zero. */
+/* Constraints applied after an optimiser step (Sec. "Physical constraints").  Each object
+ * constraint is relaxed: x <- x + r (C(x) - x) with r in [0, 1] (r = 1: the plain constraint,
+ * r = 0: off).  Order: probe orthogonalisation; then, on the object, the k_z filter, the depth blur,
+ * then clipping negative phase to zero.
+ *   k_z filter (Eq. 10-12): amp and phase are each filtered through the periodic 3D DFT of the
+ *     Nz x H x W object by W_a(k) = (1 - (2/pi) atan(beta^2 k_z^2 / (k_x^2 + k_y^2 + 1e-3)))
+ *     exp(-alpha (k_x^2 + k_y^2)), k in cycles per angstrom (pixel size dx, slice spacing dz).
+ *     On when kz_relax > 0 and beta or alpha > 0.  H, W <= 8192, Nz <= 128.
+ *   depth blur (Eq. 13): a Gaussian of standard deviation rz_sigma slices along the slice axis,
+ *     truncated at 4 sigma and renormalised at the top and bottom of the volume.  Nz <= 128.
+ *   probe orthogonalisation (mixed-state probe): the M modes (rows of an M x N^2 matrix A) become
+ *     the eigenmodes of their density matrix, Q = U^H A with A A^H = U diag(lambda) U^H, ordered by
+ *     decreasing power lambda, each column of U turned so its largest-magnitude entry is real
+ *     positive.  Not relaxed.  M <= 32. */
 typedef struct {
   float phase_positivity; /* relaxation of the phase >= 0 clip, 0 = off */
-  float rz_sigma;         /* depth-blur standard deviation in slices, 0 = off (Nz <= 128 when on) */
+  float rz_sigma;         /* depth-blur standard deviation in slices, 0 = off */
   float rz_relax;         /* relaxation of the depth blur */
+  float kz_beta;          /* strength beta of the k_z filter (dimensionless) */
+  float kz_alpha;         /* lateral Gaussian alpha of the k_z filter, square angstrom */
+  float kz_relax;         /* relaxation of the k_z filter, 0 = off */
+  int probe_orthogonalize; /* nonzero: orthogonalise the probe modes */
 } pty_constraints;
 
-/* Applies `c` in place to amp and phase [Nz][H][W] (device pointers) on `stream`. */
-int pty_constrain(const pty_geom* geom, float* amp, float* phase, const pty_constraints* c, void* stream);
+/* Bytes of device workspace pty_constrain needs for `c` (0 when only the blur and the clip are
+ * on, or on invalid arguments): the k_z filter's complex volume (8 Nz H W bytes) and the
+ * orthogonalisation's Gram partials and eigenvectors. */
+size_t pty_constrain_workspace_size(const pty_geom* geom, const pty_constraints* c);
+
+/* Applies `c` in place on `stream`: amp, phase [Nz][H][W] float, probe [M][N][N] complex64 (real,
+ * imaginary interleaved), dz the device scalar of the slice spacing (read by the k_z filter only).
+ * Pointers that `c` does not use may be NULL.  ws: device workspace of at least
+ * pty_constrain_workspace_size bytes, 256-byte aligned (NULL when that is 0).  Returns PTY_EINVAL
+ * on bad arguments or sizes, PTY_ECUDA on a launch failure; no host synchronisation. */
+int pty_constrain(const pty_geom* geom, float* amp, float* phase, float* probe, const float* dz,
+                  const pty_constraints* c, void* ws, size_t ws_bytes, void* stream);
 
 /* One Adam step on the parameters in place using the gradients already in g_* (pty_adam state).
  * step is the 1-based Adam step count used for bias correction. */

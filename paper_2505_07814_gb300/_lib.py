@@ -36,7 +36,8 @@ EXPORTS = ("pty_workspace_size", "pty_forward", "pty_loss_grad", "pty_adam_updat
            "pty_status", "pty_last_error", "pty_supported_sizes", "pty_launch_count", "pty_profile_enable",
            "pty_profile_read", "pty_loss_grad_noalloc", "pty_forward_save", "pty_backward",
            "pty_cnn_param_count", "pty_cnn_workspace_size", "pty_cnn_forward", "pty_cnn_loss_grad", "pty_cnn_adam",
-           "pty_cnn_train_step", "pty_cnn_targets", "pty_cnn_stitch", "pty_cnn_stitch_finish", "pty_cnn_read_state", "pty_constrain")
+           "pty_cnn_train_step", "pty_cnn_targets", "pty_cnn_stitch", "pty_cnn_stitch_finish", "pty_cnn_read_state", "pty_constrain",
+           "pty_constrain_workspace_size")
 PROF_STAGES = ("prepare_object", "probe_spectrum", "forward", "loss", "loss_finalize", "adjoint", "object_grad",
                "probe_grad", "scalar_grad")
 
@@ -58,7 +59,9 @@ class pty_adam(ctypes.Structure):
 
 
 class pty_constraints(ctypes.Structure):
-    _fields_ = [("phase_positivity", ctypes.c_float), ("rz_sigma", ctypes.c_float), ("rz_relax", ctypes.c_float)]
+    _fields_ = [("phase_positivity", ctypes.c_float), ("rz_sigma", ctypes.c_float), ("rz_relax", ctypes.c_float),
+                ("kz_beta", ctypes.c_float), ("kz_alpha", ctypes.c_float), ("kz_relax", ctypes.c_float),
+                ("probe_orthogonalize", ctypes.c_int)]
 
 
 class PtyError(RuntimeError):
@@ -132,8 +135,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pty_cnn_stitch_finish.restype = I
     lib.pty_cnn_read_state.argtypes = [I, I, P, SZ, I, I, P, P]
     lib.pty_cnn_read_state.restype = I
-    lib.pty_constrain.argtypes = [G, P, P, ctypes.POINTER(pty_constraints), P]
+    lib.pty_constrain.argtypes = [G, P, P, P, P, ctypes.POINTER(pty_constraints), P, SZ, P]
     lib.pty_constrain.restype = I
+    lib.pty_constrain_workspace_size.argtypes = [G, ctypes.POINTER(pty_constraints)]
+    lib.pty_constrain_workspace_size.restype = SZ
     _lib = lib
     return lib
 
@@ -265,5 +270,9 @@ def pty_cnn_read_state(S, B, ws, ws_bytes, layer, what, out, stream):
     _check(load().pty_cnn_read_state(S, B, ws, ws_bytes, layer, what, out, stream))
 
 
-def pty_constrain(geom, amp, phase, c: pty_constraints, stream):
-    _check(load().pty_constrain(ctypes.byref(geom), amp, phase, ctypes.byref(c), stream))
+def pty_constrain_workspace_size(geom, c: pty_constraints) -> int:
+    return load().pty_constrain_workspace_size(ctypes.byref(geom), ctypes.byref(c))
+
+
+def pty_constrain(geom, amp, phase, probe, dz, c: pty_constraints, ws, ws_bytes: int, stream):
+    _check(load().pty_constrain(ctypes.byref(geom), amp, phase, probe, dz, ctypes.byref(c), ws, ws_bytes, stream))

@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpty.so")
-SOURCES = ["pty_api.cu", "pty_n64.cu", "pty_n128.cu", "pty_n256.cu", "cnn.cu"]
+SOURCES = ["pty_api.cu", "pty_n64.cu", "pty_n128.cu", "pty_n256.cu", "cnn.cu", "constraints.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -117,7 +117,7 @@ size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspac
 
 static bool supported_N(int N) { return N == 64 || N == 128 || N == 256; }
 
-static int validate_geom(const pty_geom* g) {
+int validate_geom(const pty_geom* g) {
   if (!g) {
     set_error("geometry is NULL");
     return PTY_EINVAL;
@@ -167,15 +167,6 @@ static int validate_geom(const pty_geom* g) {
   return PTY_OK;
 }
 
-static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
-
-#define REQUIRE(cond, ...)     \
-  do {                         \
-    if (!(cond)) {             \
-      set_error(__VA_ARGS__);  \
-      return PTY_EINVAL;       \
-    }                          \
-  } while (0)
 
 static int prepare(const pty_geom* g, int B, int mode, const int32_t* idx, const float* amp, const float* phase,
                    const float* probe, const float* pos, const float* tilt, const float* dz, void* ws,
@@ -245,125 +236,6 @@ static int dispatch(const Problem& pb) {
     case 256: return run_pipeline<256>(pb);
     default: set_error("N = %d not supported", pb.N); return PTY_EINVAL;
   }
-}
-
-// ---------------------------------------------------------------------------------------------
-// Object constraints (pty_constrain).  One CTA per (tile of T x V pixels of the plane, array):
-// cp.async copies the tile's Nz slices to shared memory (each element is read from HBM once),
-// each thread blurs its V pixel columns along depth with the Gaussian taps held in shared memory
-// and writes every output once; the phase CTAs apply the relaxed positivity clip on the way out.
-// HBM-bound: 8 bytes per element and array.
-// ---------------------------------------------------------------------------------------------
-constexpr int kMaxBlurSlices = 128;
-constexpr int kConstrainSmem = 200 * 1024;
-
-template <int V>
-__global__ void k_constrain(float* __restrict__ x0, float* __restrict__ x1, int Nz, size_t plane, float sigma, int R,
-                            float rz_relax, float pos_relax) {
-  extern __shared__ __align__(16) unsigned char c_smem[];
-  float* taps = reinterpret_cast<float*>(c_smem);  // w(d) = exp(-d^2 / (2 sigma^2)), d = 0 .. R
-  float* rden = taps + kMaxBlurSlices;             // 1 / (sum of slice s's taps inside the volume)
-  float* tile = rden + kMaxBlurSlices;             // [Nz][T * V]
-  float* x = blockIdx.y ? x1 : x0;
-  const float clip = x == x1 ? pos_relax : 0.f;  // x1 is the phase
-  const int T = blockDim.x, tid = threadIdx.x;
-  const size_t p = (blockIdx.x * (size_t)T + tid) * V;
-  const bool in = p < plane;  // V = 4 needs plane % 4 == 0, so the whole vector is inside
-
-  if (!(sigma > 0.f)) {  // positivity alone
-    if (in) {
-      for (int s = 0; s < Nz; ++s) {
-        float* q = x + (size_t)s * plane + p;
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          const float y = q[v];
-          if (y < 0.f) q[v] = y - clip * y;
-        }
-      }
-    }
-    return;
-  }
-  for (int s = 0; s < Nz; ++s) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(tile + ((size_t)s * T + tid) * V);
-    const float* g = x + (size_t)s * plane + (in ? p : 0);
-    if (V == 4)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(g), "r"(in ? 16 : 0) : "memory");
-    else
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(g), "r"(in ? 4 : 0) : "memory");
-  }
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  for (int d = tid; d <= R; d += T) {
-    const float u = (float)d / sigma;
-    taps[d] = expf(-0.5f * u * u);
-  }
-  __syncthreads();
-  for (int s = tid; s < Nz; s += T) {
-    const int t0 = s - R > 0 ? s - R : 0, t1 = s + R < Nz - 1 ? s + R : Nz - 1;
-    float den = 0.f;
-    for (int t = t0; t <= t1; ++t) den += taps[t > s ? t - s : s - t];
-    rden[s] = 1.f / den;
-  }
-  asm volatile("cp.async.wait_all;" ::: "memory");
-  __syncthreads();
-  if (!in) return;
-  for (int s = 0; s < Nz; ++s) {
-    const int t0 = s - R > 0 ? s - R : 0, t1 = s + R < Nz - 1 ? s + R : Nz - 1;
-    float acc[V], v0[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) acc[v] = 0.f;
-    for (int t = t0; t <= t1; ++t) {
-      const float w = taps[t > s ? t - s : s - t];
-      const float* src = tile + ((size_t)t * T + tid) * V;
-      if constexpr (V == 4) {
-        const float4 q = *reinterpret_cast<const float4*>(src);
-        acc[0] = fmaf(w, q.x, acc[0]);
-        acc[1] = fmaf(w, q.y, acc[1]);
-        acc[2] = fmaf(w, q.z, acc[2]);
-        acc[3] = fmaf(w, q.w, acc[3]);
-      } else {
-        acc[0] = fmaf(w, src[0], acc[0]);
-      }
-    }
-    const float* own = tile + ((size_t)s * T + tid) * V;
-#pragma unroll
-    for (int v = 0; v < V; ++v) {
-      v0[v] = own[v];
-      float y = v0[v] + rz_relax * (acc[v] * rden[s] - v0[v]);
-      if (y < 0.f) y -= clip * y;
-      acc[v] = y;
-    }
-    float* dst = x + (size_t)s * plane + p;
-    if constexpr (V == 4)
-      *reinterpret_cast<float4*>(dst) = make_float4(acc[0], acc[1], acc[2], acc[3]);
-    else
-      dst[0] = acc[0];
-  }
-}
-
-template <int V>
-static int launch_constrain(float* amp, float* phase, int Nz, size_t plane, float sigma, float rz_relax,
-                            float pos_relax, cudaStream_t st) {
-  const bool blur = sigma > 0.f;
-  int T = 128;
-  size_t smem = 0;
-  if (blur) {
-    const size_t fixed = 2 * kMaxBlurSlices * sizeof(float);
-    T = (int)((kConstrainSmem - fixed) / ((size_t)Nz * V * sizeof(float)));
-    T = T >= 128 ? 128 : T / 32 * 32;
-    smem = fixed + (size_t)Nz * T * V * sizeof(float);
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(k_constrain<V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
-      set_error("cudaFuncSetAttribute(k_constrain) failed: %s", cudaGetErrorString(cudaGetLastError()));
-      return PTY_ECUDA;
-    }
-  }
-  const int R0 = (int)ceilf(4.0f * sigma);
-  const int R = blur ? (R0 < Nz - 1 ? R0 : Nz - 1) : 0;
-  const size_t per = (size_t)T * V;
-  const dim3 grid((unsigned)((plane + per - 1) / per), blur ? 2 : 1);
-  // without the blur only the phase is touched: the single row of CTAs takes x1 = phase as x0
-  k_constrain<V><<<grid, T, smem, st>>>(blur ? amp : phase, phase, Nz, plane, sigma, R, rz_relax, pos_relax);
-  return PTY_OK;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -484,35 +356,6 @@ int pty_backward(const pty_geom* geom, int B, const int32_t* idx, const float* a
   pb.g_dz = g_dz;
   pb.accumulate = accumulate ? 1 : 0;
   return dispatch(pb);
-}
-
-int pty_constrain(const pty_geom* geom, float* amp, float* phase, const pty_constraints* c, void* stream) {
-  int rc = validate_geom(geom);
-  if (rc) return rc;
-  REQUIRE(c && amp && phase, "NULL argument");
-  REQUIRE(aligned(amp, 4) && aligned(phase, 4), "float arrays must be 4-byte aligned");
-  REQUIRE(c->phase_positivity >= 0.f && c->phase_positivity <= 1.f, "phase_positivity %g outside [0, 1]",
-          c->phase_positivity);
-  REQUIRE(c->rz_relax >= 0.f && c->rz_relax <= 1.f, "rz_relax %g outside [0, 1]", c->rz_relax);
-  REQUIRE(c->rz_sigma >= 0.f && isfinite(c->rz_sigma), "rz_sigma %g must be finite and >= 0", c->rz_sigma);
-  const bool blur = c->rz_sigma > 0.f && c->rz_relax > 0.f;
-  REQUIRE(!blur || geom->Nz <= kMaxBlurSlices, "the depth blur supports Nz <= %d", kMaxBlurSlices);
-  if (!blur && c->phase_positivity == 0.f) return PTY_OK;
-  const size_t plane = (size_t)geom->H * geom->W;
-  const bool vec = plane % 4 == 0 && aligned(amp, 16) && aligned(phase, 16);
-  const float sigma = blur ? c->rz_sigma : 0.f;
-  rc = vec ? launch_constrain<4>(amp, phase, geom->Nz, plane, sigma, c->rz_relax, c->phase_positivity,
-                                 (cudaStream_t)stream)
-           : launch_constrain<1>(amp, phase, geom->Nz, plane, sigma, c->rz_relax, c->phase_positivity,
-                                 (cudaStream_t)stream);
-  if (rc) return rc;
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    set_error("k_constrain launch failed: %s", cudaGetErrorString(e));
-    return PTY_ECUDA;
-  }
-  note_launch();
-  return PTY_OK;
 }
 
 int pty_adam_update(const pty_geom* geom, float* amp, float* phase, float* probe, float* pos, float* tilt,

@@ -81,6 +81,18 @@ template <int N, int P>
 int run_pipeline_gemm(const Problem& pb);
 
 void set_error(const char* fmt, ...);
+// Checks the fields of a geometry every entry point shares; PTY_OK or PTY_EINVAL (message set).
+int validate_geom(const pty_geom* g);
+
+inline bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+#define REQUIRE(cond, ...)     \
+  do {                         \
+    if (!(cond)) {             \
+      set_error(__VA_ARGS__);  \
+      return PTY_EINVAL;       \
+    }                          \
+  } while (0)
 
 // Diagnostics: launch counter and optional per-stage event timing (pty_profile_*).
 void note_launch();

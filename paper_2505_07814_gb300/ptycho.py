@@ -228,14 +228,25 @@ def step(pt: Ptycho, params: Params, grads: Params, adam: Adam, idx, I_meas: tor
 
 
 def constrain(pt: Ptycho, params: Params, phase_positivity: float = 0.0, rz_sigma: float = 0.0,
-              rz_relax: float = 1.0):
-    """Object constraints after an optimiser step (pty_constrain): relaxed depth blur of amp and
-    phase along the slices, then the relaxed phase >= 0 clip; in place on params.amp / params.phase."""
+              rz_relax: float = 1.0, kz_beta: float = 0.0, kz_alpha: float = 0.0, kz_relax: float = 0.0,
+              orthogonalize_probe: bool = False):
+    """Constraints after an optimiser step (pty_constrain), in place on params: probe-mode
+    orthogonalisation; then on amp / phase the relaxed k_z filter (Eq. 10-12), the relaxed depth
+    blur along the slices (Eq. 13) and the relaxed phase >= 0 clip."""
     g = pt.geom
     nobj = g.Nz * g.H * g.W
-    c = _lib.pty_constraints(float(phase_positivity), float(rz_sigma), float(rz_relax))
+    c = _lib.pty_constraints(float(phase_positivity), float(rz_sigma), float(rz_relax), float(kz_beta),
+                             float(kz_alpha), float(kz_relax), int(bool(orthogonalize_probe)))
+    need = _lib.pty_constrain_workspace_size(pt.cg, c)
+    ws = getattr(pt, "_constrain_ws", None)
+    if need and (ws is None or ws.numel() < need):
+        ws = torch.empty(need, dtype=torch.uint8, device=pt.device)
+        pt._constrain_ws = ws
     _lib.pty_constrain(pt.cg, _ptr(params.amp, torch.float32, nobj, "amp"),
-                       _ptr(params.phase, torch.float32, nobj, "phase"), c, pt._stream())
+                       _ptr(params.phase, torch.float32, nobj, "phase"),
+                       _ptr(params.probe, torch.complex64, g.M * g.N * g.N, "probe"),
+                       _ptr(params.dz, torch.float32, 1, "dz"), c, ws.data_ptr() if need else None, need,
+                       pt._stream())
 
 
 class _ForwardModel(torch.autograd.Function):
