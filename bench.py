@@ -347,39 +347,50 @@ def run_nmse(args):
     print(json.dumps(line), flush=True)
 
 
+CONSTRAIN_KINDS = {
+    # kind: (pty_constrain settings, description, HBM bytes per object voxel as designed or None)
+    "blur": (dict(phase_positivity=1.0, rz_sigma=1.0), "depth blur (sigma 1 slice) + positivity", 16),
+    # five passes: x (amp, phase -> z), y, depth columns, y, x (z, amp, phase -> amp, phase)
+    "kz": (dict(kz_beta=1.0, kz_alpha=0.01, kz_relax=1.0), "k_z filter (beta 1, alpha 0.01 A^2)", 88),
+    "ortho": (dict(orthogonalize_probe=True), "probe-mode orthogonalisation", None),
+}
+
+
 def run_constrain(args, w, geom, params, flush, torch, Ptycho):
-    """pty_constrain on the workload's object: depth blur (sigma 1 slice) + positivity, HBM-bound
-    (amp and phase read and written once)."""
+    """pty_constrain on the workload's object or probe; the object constraints are HBM-bound."""
     from paper_2505_07814_gb300.ptycho import constrain
+    kw, what, per_voxel = CONSTRAIN_KINDS[args.constrain]
     pt = Ptycho(geom, 1)
     for _ in range(args.warmup):
-        constrain(pt, params, phase_positivity=1.0, rz_sigma=1.0)
+        constrain(pt, params, **kw)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     total = 0.0
     for _ in range(args.steps):
         flush.zero_()
         e0.record()
-        constrain(pt, params, phase_positivity=1.0, rz_sigma=1.0)
+        constrain(pt, params, **kw)
         e1.record()
         e1.synchronize()
         total += e0.elapsed_time(e1)
     ms = total / args.steps
-    nbytes = 2 * 2 * 4 * w.Nz * w.H * w.W
-    peak = None
-    try:
-        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-            peak = json.load(fh).get("hbm_gbs")
-    except (OSError, ValueError):
-        pass
-    peak = peak or 6800.0
-    gbs = nbytes / (ms / 1e3) / 1e9
-    print(json.dumps({"metric": "object constraints (depth blur + positivity) per call", "value": ms, "unit": "ms",
-                      "higher_is_better": False, "steps": args.steps, "warmup": args.warmup,
-                      "config": {"workload": WORKLOADS[args.workload][0], "object": [w.Nz, w.H, w.W],
-                                 "rz_sigma": 1.0, "phase_positivity": 1.0},
-                      "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                                   "bytes": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}}), flush=True)
+    line = {"metric": "%s per call" % what, "value": ms, "unit": "ms", "higher_is_better": False,
+            "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": WORKLOADS[args.workload][0], "object": [w.Nz, w.H, w.W], "modes": w.M, "N": w.N,
+                       **{k: (float(v) if not isinstance(v, bool) else v) for k, v in kw.items()}}}
+    if per_voxel:
+        peak = None
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                peak = json.load(fh).get("hbm_gbs")
+        except (OSError, ValueError):
+            pass
+        peak = peak or 6800.0
+        nbytes = per_voxel * w.Nz * w.H * w.W
+        gbs = nbytes / (ms / 1e3) / 1e9
+        line["roofline"] = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                            "bytes": nbytes, "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    print(json.dumps(line), flush=True)
 
 
 def cnn_flops(S=128, train=True):
@@ -478,8 +489,8 @@ def main():
     ap.add_argument("--cnn", action="store_true", help="learned-initialiser training / inference throughput")
     ap.add_argument("--w-pacbed", type=float, default=0.0, help="weight of the PACBED loss term (Eq. 7)")
     ap.add_argument("--w-sparse", type=float, default=0.0, help="weight of the phase-sparsity loss term (Eq. 8)")
-    ap.add_argument("--constrain", action="store_true",
-                    help="time pty_constrain (depth blur + positivity) on the workload's object instead")
+    ap.add_argument("--constrain", nargs="?", const="blur", default=None, choices=sorted(CONSTRAIN_KINDS),
+                    help="time one kind of pty_constrain on the workload's object / probe instead")
     args = ap.parse_args()
     if args.cnn:
         run_cnn(args)
