@@ -277,6 +277,47 @@ def sweep_ckpt(args, w, geometry, params, I_meas, idx_t, flush, dev, torch, Ptyc
         torch.cuda.empty_cache()
 
 
+def sweep_shape(args, w, amp0, phase0, I_meas, idx_t, flush, dev, torch, Geometry, Params, Ptycho):
+    """Step time against batch size, probe modes and slices on the multislice workload (the shape of
+    the paper's Fig. 3b-d): one JSON line per point.  Extra modes are the workload's modes scaled by
+    1/2 per repeat, extra slices repeat its slices; values do not change the work."""
+    import numpy as np
+    f32 = dict(dtype=torch.float32, device=dev)
+    points = [("batch", B, w.M, w.Nz) for B in (64, 128, 256, 512)]
+    points += [("modes", 256, M, w.Nz) for M in (1, 2, 4, 6, 8, 12)]
+    points += [("slices", 256, w.M, Nz) for Nz in (1, 2, 4, 8, 12, 16)]
+    for axis, B, M, Nz in points:
+        probe = np.stack([w.probe[m % w.M] * 0.5 ** (m // w.M) for m in range(M)])
+        amp = np.stack([amp0[s % w.Nz] for s in range(Nz)])
+        phase = np.stack([phase0[s % w.Nz] for s in range(Nz)])
+        params = Params(amp=torch.tensor(amp, **f32), phase=torch.tensor(phase, **f32),
+                        probe=torch.tensor(probe, dtype=torch.complex64, device=dev), pos=torch.tensor(w.pos, **f32),
+                        tilt=torch.tensor(w.tilt, **f32), dz=torch.tensor([w.dz], **f32))
+        geom = Geometry(N=w.N, M=M, Nz=Nz, H=w.H, W=w.W, Ntot=w.Ntot, dx=w.dx, lam=w.lam, loss="poisson")
+        pt = Ptycho(geom, B, device=dev)
+        grads = params.zeros_like()
+        idx = [t[:B] for t in idx_t]
+        for k in range(args.warmup):
+            pt.loss_grad(params, idx[k % len(idx)], I_meas, grads=grads)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ms = 0.0
+        for k in range(args.steps):
+            flush.zero_()
+            ev[0].record()
+            pt.loss_grad(params, idx[k % len(idx)], I_meas, grads=grads)
+            ev[1].record()
+            ev[1].synchronize()
+            ms += ev[0].elapsed_time(ev[1])
+        assert pt.status() == 0
+        ms /= args.steps
+        print(json.dumps({"sweep": axis, "workload": WORKLOADS[args.workload][0], "batch": B, "modes": M,
+                          "slices": Nz, "ms_per_step": ms, "updates_per_s": B * M * Nz / (ms / 1e3),
+                          "s_per_pass": ms / 1e3 * (w.Ntot / B)}), flush=True)
+        del pt, grads, params
+        torch.cuda.empty_cache()
+
+
 def run_nmse(args):
     """Time to object NMSE <= target on the multislice workload (object seed 1234, measured counts
     simulated by the forward model): the flat start (Sec. "Preprocessing and initialization") with
@@ -478,6 +519,8 @@ def main():
     ap.add_argument("--fft", default="fp32", choices=["fp32", "bf16", "fp16", "bf16x3"],
                     help="per-slice DFTs: FP32 shared-memory FFT or split-precision tensor-core GEMMs")
     ap.add_argument("--sweep-ckpt", default="", help="comma-separated strides: print one timing line per stride")
+    ap.add_argument("--sweep-shape", action="store_true",
+                    help="step time against batch size, probe modes and slices (one line per point)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -550,6 +593,9 @@ def main():
         return
     if args.constrain:
         run_constrain(args, w, geometry(1), params, flush, torch, Ptycho)
+        return
+    if args.sweep_shape:
+        sweep_shape(args, w, amp0, phase0, I_meas, idx_t, flush, dev, torch, Geometry, Params, Ptycho)
         return
     geom = geometry(args.ckpt_stride)
     pt = Ptycho(geom, B, device=dev)

@@ -33,7 +33,8 @@ Readings where the paper is silent (each also listed in the design notes):
       of the batch; eps = 1e-6 sits inside the log, added to I_model^p;
   R7  where I_model = 0 and p < 1, dI^p/dI is taken as 0;
   R8  complex gradients follow dL/dRe + i dL/dIm; amp/phase gradients are real;
-  R9  one object mode;
+  R9  K object modes (Eq. 2): the pattern sums |F[psi]|^2 over every (probe mode, object mode)
+      pair, with no weights between the object modes; the paper's reconstructions use K = 1;
   R10 total loss = (Eq. 5 or 6) + w_pacbed L_PACBED + w_sparse L_sparse (the weights of Eq. 9 with
       the chosen likelihood at weight 1); L_PACBED raises the batch-mean patterns to p_pacbed
       (default 0.5) and normalises by <I_meas^p_pacbed>_{D,B}; L_sparse averages |phase|^p_sparse
@@ -42,7 +43,8 @@ Readings where the paper is silent (each also listed in the design notes):
 
 Array conventions: row-major, axis 0 = rows, axis 1 = columns; k_a = fftfreq(N, dx) in 1/angstrom;
 positions and tilts are (axis-0, axis-1) pairs; the probe is [M][N][N]; the object amplitude and
-phase are [Nz][H][W]; measured patterns are [Ntot][N][N], DC-centred.
+phase are [Nz][H][W] (one object mode) or [K][Nz][H][W]; measured patterns are [Ntot][N][N],
+DC-centred.
 """
 from __future__ import annotations
 
@@ -71,6 +73,7 @@ class Geometry:
     p_pacbed: float | None = None  # its exponent, default 0.5
     w_sparse: float = 0.0  # weight of the phase sparsity term
     p_sparse: float | None = None  # its exponent, default 1
+    K: int = 1  # object modes (reading R9)
 
     @property
     def power(self) -> float:
@@ -159,19 +162,26 @@ def tilt_of(geom, tilt, j):
     return np.asarray(tilt if geom.global_tilt else tilt[j], dtype=np.float64).reshape(2)
 
 
+def object_modes(geom, x):
+    """The object array as [K][Nz][H][W] (a single mode may be passed as [Nz][H][W])."""
+    x = np.asarray(x)
+    return x.reshape((geom.K, geom.Nz) + x.shape[-2:])
+
+
 def model_patterns(geom, amp, phase, probe, pos, tilt, dz, idx):
-    """Eq. 1-2 for the scan positions idx: I_j = fftshift(sum_m |F_ortho[psi_j^(m)]|^2), [B][N][N]."""
+    """Eq. 1-2 for the scan positions idx: I_j = fftshift(sum_m sum_n |F_ortho[psi_j^(m)(n)]|^2),
+    [B][N][N] (probe modes m, object modes n)."""
     N = geom.N
-    T = transmission(amp, phase)
+    T = transmission(object_modes(geom, amp), object_modes(geom, phase))
     out = np.zeros((len(idx), N, N))
     for b, j in enumerate(idx):
         r, dr = crop_index(pos[j])
-        Oj = object_patch(T, r, N)
         Mj = propagator(N, geom.dx, geom.lam, dz, tilt_of(geom, tilt, j))
         I = np.zeros((N, N))
         for m in range(geom.M):
             Pj = shift_operator(probe[m], dr)
-            I += np.abs(far_field(exit_wave(Pj, Oj, Mj))) ** 2
+            for n in range(geom.K):
+                I += np.abs(far_field(exit_wave(Pj, object_patch(T[n], r, N), Mj))) ** 2
         out[b] = np.fft.fftshift(I)
     return out
 
@@ -243,7 +253,9 @@ def pacbed_grad_I(geom, I_model, I_meas):
 
 
 def _patches(phase, corners, N):
-    return [np.asarray(phase, dtype=np.float64)[:, r0:r0 + N, r1:r1 + N] for r0, r1 in corners]
+    """Every position's N x N window of every slice (of every object mode, when phase is 4D)."""
+    ph = np.asarray(phase, dtype=np.float64)
+    return [ph[..., r0:r0 + N, r1:r1 + N] for r0, r1 in corners]
 
 
 def sparse_value(geom, phase, corners):
@@ -268,7 +280,7 @@ def sparse_grad_phase(geom, phase, corners):
         w = np.zeros_like(a)
         nz = a > 0
         w[nz] = a[nz] ** (p - 1.0)
-        g[:, r0:r0 + N, r1:r1 + N] += scale * w * np.sign(x)
+        g[..., r0:r0 + N, r1:r1 + N] += scale * w * np.sign(x)
     return g
 
 
@@ -280,8 +292,8 @@ def sparse_grad_phase(geom, phase, corners):
 class Gradients:
     loss: float
     I_model: np.ndarray  # [B][N][N] DC-centred
-    amp: np.ndarray  # [Nz][H][W]
-    phase: np.ndarray  # [Nz][H][W]
+    amp: np.ndarray  # shape of the amp argument
+    phase: np.ndarray  # shape of the phase argument
     probe: np.ndarray  # [M][N][N] complex, dL/dRe + i dL/dIm
     pos: np.ndarray  # [Ntot][2]
     tilt: np.ndarray  # [Ntot][2] (or [2] with global tilt)
@@ -294,10 +306,12 @@ def loss_and_grad(geom, amp, phase, probe, pos, tilt, dz, I_meas, idx):
     I_meas is indexed by scan position ([Ntot][N][N], DC-centred).  Gradient arrays cover the
     whole parameter (zeros where the batch does not reach).
     """
-    N, M, Nz = geom.N, geom.M, geom.Nz
+    N, M, Nz, K = geom.N, geom.M, geom.Nz, geom.K
     idx = list(idx)
     B = len(idx)
-    T = transmission(amp, phase)
+    amp_shape = np.shape(amp)
+    amp, phase = object_modes(geom, amp), object_modes(geom, phase)
+    T = transmission(amp, phase)  # [K][Nz][H][W]
     k0, k1 = freqs(N, geom.dx)
     f = np.fft.fftfreq(N)
     f0, f1 = np.meshgrid(f, f, indexing="ij")
@@ -308,26 +322,27 @@ def loss_and_grad(geom, amp, phase, probe, pos, tilt, dz, I_meas, idx):
     I_model = np.zeros((B, N, N))
     for b, j in enumerate(idx):
         r, dr = crop_index(pos[j])
-        Oj = object_patch(T, r, N)
         th = tilt_of(geom, tilt, j)
         Mj = propagator(N, geom.dx, geom.lam, dz, th)
         R = shift_ramp(N, dr)
-        per_mode = []
+        per_mode = []  # [(m, n)] for probe mode m, object mode n
         I = np.zeros((N, N))
         for m in range(M):
-            psi = idft2(Phat[m] * R)  # shifted probe P_j
-            psi_in, vhat = [], []
-            for s in range(Nz):
-                psi_in.append(psi)
-                u = Oj[s] * psi
-                if s < Nz - 1:
-                    vhat.append(Mj * dft2(u))
-                    psi = idft2(vhat[-1])
-                else:
-                    psi = u
-            Psi = far_field(psi)
-            I += np.abs(Psi) ** 2
-            per_mode.append((psi_in, vhat, Psi))
+            for n in range(K):
+                Oj = object_patch(T[n], r, N)
+                psi = idft2(Phat[m] * R)  # shifted probe P_j
+                psi_in, vhat = [], []
+                for s in range(Nz):
+                    psi_in.append(psi)
+                    u = Oj[s] * psi
+                    if s < Nz - 1:
+                        vhat.append(Mj * dft2(u))
+                        psi = idft2(vhat[-1])
+                    else:
+                        psi = u
+                Psi = far_field(psi)
+                I += np.abs(Psi) ** 2
+                per_mode.append((m, n, psi_in, vhat, Psi))
         I_model[b] = np.fft.fftshift(I)
         records.append((j, r, dr, th, Mj, R, per_mode))
 
@@ -345,7 +360,6 @@ def loss_and_grad(geom, amp, phase, probe, pos, tilt, dz, I_meas, idx):
     g_tilt = np.zeros_like(np.asarray(tilt, dtype=np.float64))
     g_dz = 0.0
     for b, (j, r, dr, th, Mj, R, per_mode) in enumerate(records):
-        Oj = object_patch(T, r, N)
         w = np.fft.ifftshift(dLdI[b])  # back to DFT order
         # dM/d(dz) / M and dM/d(theta_a) / M
         c_dz = 1j * (-np.pi * geom.lam * (k0 ** 2 + k1 ** 2)
@@ -353,13 +367,13 @@ def loss_and_grad(geom, amp, phase, probe, pos, tilt, dz, I_meas, idx):
         c_t0 = 2j * np.pi * dz * k0 / np.cos(th[0]) ** 2
         c_t1 = 2j * np.pi * dz * k1 / np.cos(th[1]) ** 2
         gth = np.zeros(2)
-        for m in range(M):
-            psi_in, vhat, Psi = per_mode[m]
+        for m, n, psi_in, vhat, Psi in per_mode:
+            Oj = object_patch(T[n], r, N)
             # I = |Psi|^2 -> g_Psi = 2 dL/dI Psi ; Psi = F_ortho psi -> g_psi = F_ortho^H g_Psi
             g = np.fft.ifft2(2.0 * w * Psi, norm="ortho")
             for s in range(Nz - 1, -1, -1):
                 # u_s = O_s psi_in_s
-                gT[s, r[0]:r[0] + N, r[1]:r[1] + N] += np.conj(psi_in[s]) * g
+                gT[n, s, r[0]:r[0] + N, r[1]:r[1] + N] += np.conj(psi_in[s]) * g
                 g = np.conj(Oj[s]) * g
                 if s > 0:
                     # psi_in_s = F^-1[vhat], F^-1 = (1/N^2) F^H  ->  g_vhat = F[g] / N^2
@@ -390,5 +404,6 @@ def loss_and_grad(geom, amp, phase, probe, pos, tilt, dz, I_meas, idx):
         corners = [tuple(crop_index(pos[j])[0]) for j in idx]
         loss += geom.w_sparse * sparse_value(geom, phase, corners)
         g_phase = g_phase + geom.w_sparse * sparse_grad_phase(geom, phase, corners)
+    g_amp, g_phase = g_amp.reshape(amp_shape), g_phase.reshape(amp_shape)
     return Gradients(loss=float(loss), I_model=I_model, amp=g_amp, phase=g_phase, probe=g_probe,
                      pos=g_pos, tilt=g_tilt, dz=float(g_dz))
