@@ -107,6 +107,11 @@ typedef struct {
   float w_sparse;  /* weight of the phase-sparsity term (Eq. 8): <|phase|^p_sparse>^(1/p_sparse) over
                       every slice of every batch position's N x N patch (p_sparse <= 0: 1); 0 = off */
   float p_sparse;
+  int obj_modes;   /* object modes K of the mixed-state object (Eq. 2), 0 or 1: a single object.  The
+                      object arrays (amp, phase and their gradients and Adam moments) are
+                      [K][Nz][H][W]; every pattern sums the intensities of all M x K (probe mode,
+                      object mode) pairs; the sparsity term covers every mode's patches.  The
+                      workspace's per-wave arrays grow by K. */
 } pty_geom;
 
 enum { PTY_FFT_FP32 = 0, PTY_FFT_SPLIT_BF16 = 1, PTY_FFT_SPLIT_FP16 = 2, PTY_FFT_SPLIT3_BF16 = 3 };
@@ -127,7 +132,8 @@ typedef struct {
  * named in geom->grad_mask).  0 on invalid geometry (see pty_last_error()). */
 size_t pty_workspace_size(const pty_geom* geom, int B);
 
-/* Forward model, Eq. 1-4: I_model[b] = fftshift( sum_m |F_ortho[psi_{idx[b]}^(m)]|^2 ), [B][N][N].
+/* Forward model, Eq. 1-4: I_model[b] = fftshift( sum_m sum_n |F_ortho[psi_{idx[b]}^(m)(n)]|^2 ), [B][N][N]
+ * (probe modes m, object modes n).
  * Reads amp, phase, probe, pos, tilt, dz; writes I_model.  ws must hold pty_workspace_size(). */
 int pty_forward(const pty_geom* geom, int B, const int32_t* idx, const float* amp,
                 const float* phase, const float* probe, const float* pos, const float* tilt,
@@ -169,7 +175,7 @@ int pty_backward(const pty_geom* geom, int B, const int32_t* idx, const float* a
 /* Constraints applied after an optimiser step (Sec. "Physical constraints").  Each object
  * constraint is relaxed: x <- x + r (C(x) - x) with r in [0, 1] (r = 1: the plain constraint,
  * r = 0: off).  Order: probe orthogonalisation; then, on the object, the k_z filter, the depth blur,
- * then clipping negative phase to zero.
+ * then clipping negative phase to zero (each object mode on its own).
  *   k_z filter (Eq. 10-12): amp and phase are each filtered through the periodic 3D DFT of the
  *     Nz x H x W object by W_a(k) = (1 - (2/pi) atan(beta^2 k_z^2 / (k_x^2 + k_y^2 + 1e-3)))
  *     exp(-alpha (k_x^2 + k_y^2)), k in cycles per angstrom (pixel size dx, slice spacing dz).

@@ -48,7 +48,8 @@ class pty_geom(ctypes.Structure):
                 ("lambda_", ctypes.c_float), ("loss", ctypes.c_int), ("p", ctypes.c_float),
                 ("eps", ctypes.c_float), ("grad_mask", ctypes.c_int), ("global_tilt", ctypes.c_int),
                 ("ckpt_stride", ctypes.c_int), ("fft_impl", ctypes.c_int), ("w_pacbed", ctypes.c_float),
-                ("p_pacbed", ctypes.c_float), ("w_sparse", ctypes.c_float), ("p_sparse", ctypes.c_float)]
+                ("p_pacbed", ctypes.c_float), ("w_sparse", ctypes.c_float), ("p_sparse", ctypes.c_float),
+                ("obj_modes", ctypes.c_int)]
 
 
 class pty_adam(ctypes.Structure):

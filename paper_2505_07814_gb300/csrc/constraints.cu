@@ -666,15 +666,20 @@ int pty_constrain(const pty_geom* geom, float* amp, float* phase, float* probe, 
   cudaStream_t st = (cudaStream_t)stream;
   char* w = static_cast<char*>(ws);
   if (ortho && geom->M > 1 && (rc = run_orthogonalize(geom, probe, L, w, st))) return rc;
-  if (kz && (rc = run_kz_filter(geom, amp, phase, dz, c, reinterpret_cast<float2*>(w + L.z), st))) return rc;
-  if (!blur && c->phase_positivity == 0.f) return PTY_OK;
-  const size_t plane = (size_t)geom->H * geom->W;
-  const bool vec = plane % 4 == 0 && aligned(amp, 16) && aligned(phase, 16);
-  const float sigma = blur ? c->rz_sigma : 0.f;
-  rc = vec ? launch_constrain<4>(amp, phase, geom->Nz, plane, sigma, c->rz_relax, c->phase_positivity, st)
-           : launch_constrain<1>(amp, phase, geom->Nz, plane, sigma, c->rz_relax, c->phase_positivity, st);
-  if (rc) return rc;
-  return launched("k_constrain");
+  const size_t plane = (size_t)geom->H * geom->W, vol = (size_t)geom->Nz * plane;
+  const int Ko = geom->obj_modes > 1 ? geom->obj_modes : 1;
+  for (int n = 0; n < Ko; ++n) {  // each object mode is its own volume (the k_z workspace is reused)
+    float* a = amp ? amp + n * vol : nullptr;
+    float* p = phase ? phase + n * vol : nullptr;
+    if (kz && (rc = run_kz_filter(geom, a, p, dz, c, reinterpret_cast<float2*>(w + L.z), st))) return rc;
+    if (!blur && c->phase_positivity == 0.f) continue;
+    const bool vec = plane % 4 == 0 && aligned(a, 16) && aligned(p, 16);
+    const float sigma = blur ? c->rz_sigma : 0.f;
+    rc = vec ? launch_constrain<4>(a, p, geom->Nz, plane, sigma, c->rz_relax, c->phase_positivity, st)
+             : launch_constrain<1>(a, p, geom->Nz, plane, sigma, c->rz_relax, c->phase_positivity, st);
+    if (rc || (rc = launched("k_constrain"))) return rc;
+  }
+  return PTY_OK;
 }
 
 }  // extern "C"

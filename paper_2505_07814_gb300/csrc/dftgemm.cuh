@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs g) {
   double* red = reinterpret_cast<double*>(f1 + N);
   const FwdArgs& a = g.f;
   const int tid = threadIdx.x, bm = blockIdx.x;
-  const int b = bm / a.M, m = bm % a.M;
+  const int b = bm / (a.M * a.Ko), m = (bm / a.Ko) % a.M;  // waves: (position, probe mode, object mode)
   const int j = checked_index(a.idx, b, a.Ntot, a.status);
   int i0, i1;
   float d0, d1, th0, th1;
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs g) {
     fwd_tables<N>(t0p, t1p, t2p, t3p, d0, d1, th0, th1, dz, a.dx, a.lam);
   }
   __syncthreads();
-  const size_t plane = (size_t)a.H * a.W, patch = (size_t)i0 * a.W + i1;
+  const size_t plane = (size_t)a.H * a.W, patch = (size_t)(bm % a.Ko) * a.Nz * plane + (size_t)i0 * a.W + i1;
   float2* X = g.wave + (size_t)bm * NN;
   const int sl = g.sl;
   float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -415,7 +415,7 @@ struct GemmPass {
   // out = rows of `src` times split DFT matrix `mat`; TRANSPOSE stores each wave transposed
   // fp16 batch scale of `src` into ws.gscal (returns the device scale pointer)
   int fp16_scale(const float2* src, const float** sc) {
-    const int rows = pb.B * pb.M * N;
+    const int rows = pb.B * pb.M * pb.Ko * N;
     unsigned* amax = reinterpret_cast<unsigned*>(ws.gscal);
     float* scale = reinterpret_cast<float*>(ws.gscal) + 1;
     if (cudaMemsetAsync(amax, 0, sizeof(unsigned), st) != cudaSuccess) return base.memset_failed();
@@ -429,7 +429,7 @@ struct GemmPass {
 #if PTY_GEMM_LEGACY
   // out = rows of `src` times split DFT matrix `mat`; TRANSPOSE stores each wave transposed
   int gemm(int mat, const float2* src, float2* dst, bool transpose) {
-    const int rows = pb.B * pb.M * N;
+    const int rows = pb.B * pb.M * pb.Ko * N;
     const int rows_pad = (rows + GB_M - 1) / GB_M * GB_M;
     const float* sc = nullptr;
     if (S::kScale) {
@@ -460,7 +460,7 @@ struct GemmPass {
   // in FP32 to be rescaled and split again; both operands reach shared memory by cp.async.
   template <class Epi>
   int gemm_tc(int mat, const H* a_pieces, const Epi& epi) {
-    const int rows = pb.B * pb.M * N;
+    const int rows = pb.B * pb.M * pb.Ko * N;
     constexpr int K = S::kTerms * 2 * N;
     PiecesLoader<N, P> la{a_pieces, rows};
     PlainLoader<H> lb{tables + (size_t)mat * 2 * N * K, (size_t)K, 2 * N};
@@ -474,7 +474,7 @@ struct GemmPass {
     return PTY_OK;
   }
   int split(const float2* src, H* dst, const float* sc) {
-    const int rows = pb.B * pb.M * N;
+    const int rows = pb.B * pb.M * pb.Ko * N;
     const size_t n = (size_t)rows * (N / 8);
     const unsigned blocks = (unsigned)((n + 255) / 256 < 152 * 16 ? (n + 255) / 256 : 152 * 16);
     k_split<N, P><<<blocks, 256, 0, st>>>(src, dst, rows, sc);
@@ -482,7 +482,7 @@ struct GemmPass {
     return PTY_OK;
   }
   int transform(int mat_a, int mat_b) {
-    const int rows = pb.B * pb.M * N;
+    const int rows = pb.B * pb.M * pb.Ko * N;
     H* pa = reinterpret_cast<H*>(ws.pieces0);
     H* pb_ = reinterpret_cast<H*>(ws.pieces1);
     const float* sc = nullptr;
@@ -506,7 +506,7 @@ struct GemmPass {
   template <int ST>
   int stage(const FwdArgs& fa, const AdjArgs& aa, int sl, int prof) {
     StageArgs g{fa, aa, ws.wave, sl};
-    k_stage<N, ST><<<pb.B * pb.M, 256, stage_smem_bytes<N>(), st>>>(g);
+    k_stage<N, ST><<<pb.B * pb.M * pb.Ko, 256, stage_smem_bytes<N>(), st>>>(g);
     PTY_LAUNCH_CHECK("k_stage", prof);
     return PTY_OK;
   }

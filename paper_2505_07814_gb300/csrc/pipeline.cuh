@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(T) k_probe_spectrum(const float2* __restrict__
 // Forward: one CTA per (batch entry b, mode m)
 // ---------------------------------------------------------------------------------------------
 struct FwdArgs {
-  int M, Nz, H, W, Ntot, global_tilt;
+  int M, Ko, Nz, H, W, Ntot, global_tilt;  // Ko: object modes
   float dx, lam;
   const int32_t* idx;
   const float *pos, *tilt, *dz;
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   float2* pm1 = pm0 + N;  // propagator factor along axis 1
   const int tid = threadIdx.x;
   const int bm = blockIdx.x / F::C;  // wave (position, mode); a cluster of F::C CTAs per wave
-  const int b = bm / a.M, m = bm % a.M;
+  const int b = bm / (a.M * a.Ko), m = (bm / a.Ko) % a.M;  // waves: (position, probe mode, object mode)
   const int j = checked_index(a.idx, b, a.Ntot, a.status);
   int i0, i1;
   float d0, d1, th0, th1;
@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   tilt_of(a.tilt, a.global_tilt, j, &th0, &th1);
   const float dz = a.dz[0];
   const size_t plane = (size_t)a.H * a.W;
-  const float2* Tpatch = a.T + (size_t)i0 * a.W + i1;
+  const float2* Tpatch = a.T + (size_t)(bm % a.Ko) * a.Nz * plane + (size_t)i0 * a.W + i1;
   prefetch_patch<N>(Tpatch, a.W);
 
   build_twiddles<N>(tw);
@@ -485,7 +485,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_recompute(FwdArgs a) {
   float2* pm1 = pm0 + N;
   const int tid = threadIdx.x;
   const int bm = blockIdx.x / F::C;  // wave (position, mode); a cluster of F::C CTAs per wave
-  const int b = bm / a.M, m = bm % a.M;
+  const int b = bm / (a.M * a.Ko), m = (bm / a.Ko) % a.M;  // waves: (position, probe mode, object mode)
   const int j = checked_index(a.idx, b, a.Ntot, a.status);
   int i0, i1;
   float d0, d1, th0, th1;
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_recompute(FwdArgs a) {
   tilt_of(a.tilt, a.global_tilt, j, &th0, &th1);
   const float dz = a.dz[0];
   const size_t plane = (size_t)a.H * a.W;
-  const float2* Tpatch = a.T + (size_t)i0 * a.W + i1;
+  const float2* Tpatch = a.T + (size_t)(bm % a.Ko) * a.Nz * plane + (size_t)i0 * a.W + i1;
   const int K = a.kstride;
   build_twiddles<N>(tw);
   fwd_tables<N>(ra0, ra1, pm0, pm1, d0, d1, th0, th1, dz, a.dx, a.lam);
@@ -796,7 +796,7 @@ static __global__ void k_loss_finalize(const double* __restrict__ lpart, int B, 
 // Adjoint: one CTA per (b, m), slices in reverse.
 // ---------------------------------------------------------------------------------------------
 struct AdjArgs {
-  int M, Nz, H, W, Ntot, global_tilt, grad_mask;
+  int M, Ko, Nz, H, W, Ntot, global_tilt, grad_mask;  // Ko: object modes
   float dx, lam;
   const int32_t* idx;
   const float *pos, *tilt, *dz;
@@ -961,7 +961,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   double* red = reinterpret_cast<double*>(f1 + N);
   const int tid = threadIdx.x, lane = tid & 31;
   const int bm = blockIdx.x / F::C;  // wave (position, mode); a cluster of F::C CTAs per wave
-  const int b = bm / a.M, m = bm % a.M;
+  const int b = bm / (a.M * a.Ko), m = (bm / a.Ko) % a.M;  // waves: (position, probe mode, object mode)
   const int j = checked_index(a.idx, b, a.Ntot, a.status);
   int i0, i1;
   float d0, d1, th0, th1;
@@ -973,7 +973,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   const bool want_pos = (a.grad_mask & PTY_GRAD_POS) != 0;
   const bool want_prop = (a.grad_mask & (PTY_GRAD_DZ | PTY_GRAD_TILT)) != 0 && a.vhat != nullptr;
   const size_t plane = (size_t)a.H * a.W;
-  const size_t patch = (size_t)i0 * a.W + i1;
+  const size_t patch = (size_t)(bm % a.Ko) * a.Nz * plane + (size_t)i0 * a.W + i1;
   // slot pointers relative to slice numbers (ck_base + s * NN is slice s's entering wave, vh_base +
   // (s - 1) * NN the spectrum entering slice s)
   const float2* ck_base = want_obj ? a.ckpt + ((ptrdiff_t)bm * a.ck_per_wave - a.ck_first) * NN : nullptr;
@@ -1312,13 +1312,14 @@ struct Pass {
   }
   static size_t probe_smem() { return sizeof(float2) * ((size_t)wave_rows<N>() * (N + 1) + N); }
   unsigned object_blocks() const {
-    const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
+    const size_t nobj = (size_t)pb.Ko * pb.Nz * pb.H * pb.W;
     return (unsigned)((nobj + 255) / 256 < 152 * 16 ? (nobj + 255) / 256 : 152 * 16);
   }
 
   FwdArgs fwd_args() const {
     FwdArgs fa;
     fa.M = pb.M;
+    fa.Ko = pb.Ko;
     fa.Nz = pb.Nz;
     fa.H = pb.H;
     fa.W = pb.W;
@@ -1346,7 +1347,7 @@ struct Pass {
 
   // T and probe spectra (start of every forward).
   int forward_begin() {
-    const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
+    const size_t nobj = (size_t)pb.Ko * pb.Nz * pb.H * pb.W;
     prof_begin(st);
     k_prepare_object<<<object_blocks(), 256, 0, st>>>(pb.amp, pb.phase, ws.T, nullptr, nobj);
     PTY_LAUNCH_CHECK("k_prepare_object", 0);
@@ -1371,7 +1372,7 @@ struct Pass {
   // Mode sum, and the loss when I_meas is given.
   int loss_phase(const float* I_meas) {
     LossArgs la;
-    la.M = pb.M;
+    la.M = pb.M * pb.Ko;  // waves summed into each pattern
     la.Ntot = pb.Ntot;
     la.status = ws.status;
     la.loss = pb.loss;
@@ -1410,7 +1411,7 @@ struct Pass {
   int forward(const float* I_meas) {
     int rc = forward_begin();
     if (rc || pb.B == 0) return rc;
-    PTY_LAUNCH_RC(launch_waves<C>(k_forward<N, TF>, pb.B * pb.M, TF, fwd_smem_bytes<N>(), st, fwd_args_saved()),
+    PTY_LAUNCH_RC(launch_waves<C>(k_forward<N, TF>, pb.B * pb.M * pb.Ko, TF, fwd_smem_bytes<N>(), st, fwd_args_saved()),
                   "k_forward", 2);
     return loss_phase(I_meas);
   }
@@ -1428,6 +1429,7 @@ struct Pass {
   AdjArgs adj_args() const {
     AdjArgs aa;
     aa.M = pb.M;
+    aa.Ko = pb.Ko;
     aa.Nz = pb.Nz;
     aa.H = pb.H;
     aa.W = pb.W;
@@ -1456,10 +1458,10 @@ struct Pass {
 
   // Zero the accumulators of the adjoint.
   int adjoint_begin() {
-    const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
+    const size_t nobj = (size_t)pb.Ko * pb.Nz * pb.H * pb.W;
     if (want_obj && cudaMemsetAsync(ws.gT, 0, sizeof(float2) * nobj, st) != cudaSuccess) return memset_failed();
     if (want_probe && cudaMemsetAsync(ws.gPhat, 0, sizeof(float2) * pb.M * NN, st) != cudaSuccess) return memset_failed();
-    if (pb.B > 0 && cudaMemsetAsync(ws.spart, 0, sizeof(double) * 5 * pb.B * pb.M, st) != cudaSuccess)
+    if (pb.B > 0 && cudaMemsetAsync(ws.spart, 0, sizeof(double) * 5 * pb.B * pb.M * pb.Ko, st) != cudaSuccess)
       return memset_failed();
     return PTY_OK;
   }
@@ -1477,7 +1479,7 @@ struct Pass {
         aa.vh_per_wave = pb.Nz - 1;
         aa.s0 = 0;
         aa.s1 = pb.Nz;
-        PTY_LAUNCH_RC(launch_waves<C>(k_adjoint<N, TA>, pb.B * pb.M, TA, adj_smem_bytes<N, TA>(), st, aa),
+        PTY_LAUNCH_RC(launch_waves<C>(k_adjoint<N, TA>, pb.B * pb.M * pb.Ko, TA, adj_smem_bytes<N, TA>(), st, aa),
                       "k_adjoint", 5);
       } else {
         for (int q = nseg - 1; q >= 0; --q) {
@@ -1490,7 +1492,7 @@ struct Pass {
             fa.vhat = want_prop ? ws.vhat : nullptr;
             fa.s0 = s0;
             fa.s1 = s1;
-            PTY_LAUNCH_RC(launch_waves<C>(k_recompute<N, TF>, pb.B * pb.M, TF, fwd_smem_bytes<N>(), st, fa),
+            PTY_LAUNCH_RC(launch_waves<C>(k_recompute<N, TF>, pb.B * pb.M * pb.Ko, TF, fwd_smem_bytes<N>(), st, fa),
                           "k_recompute", -1);
           }
           aa.ckpt = ws.ckpt;
@@ -1501,7 +1503,7 @@ struct Pass {
           aa.vh_per_wave = K;
           aa.s0 = s0;
           aa.s1 = s1;
-          PTY_LAUNCH_RC(launch_waves<C>(k_adjoint<N, TA>, pb.B * pb.M, TA, adj_smem_bytes<N, TA>(), st, aa),
+          PTY_LAUNCH_RC(launch_waves<C>(k_adjoint<N, TA>, pb.B * pb.M * pb.Ko, TA, adj_smem_bytes<N, TA>(), st, aa),
                         "k_adjoint", q == 0 ? 5 : -1);
         }
       }
@@ -1513,15 +1515,17 @@ struct Pass {
   // phase-sparsity term of the loss and its gradient.
   int finalize() {
     const int gm = pb.grad_mask;
-    const size_t nobj = (size_t)pb.Nz * pb.H * pb.W;
+    const size_t nobj = (size_t)pb.Ko * pb.Nz * pb.H * pb.W;
     if (want_obj) {
       k_object_grad<<<object_blocks(), 256, 0, st>>>(pb.amp, pb.phase, ws.gT, (gm & PTY_GRAD_AMP) ? pb.g_amp : nullptr,
                                                      (gm & PTY_GRAD_PHASE) ? pb.g_phase : nullptr, pb.accumulate, nobj);
       PTY_LAUNCH_CHECK("k_object_grad", 6);
     }
     if (pb.mode == MODE_GRAD && pb.w_sp > 0.f && ws.sppart && pb.B > 0) {
-      const unsigned patches = (unsigned)(pb.B * pb.Nz);
-      k_sparse_sum<N, 256><<<patches, 256, 0, st>>>(pb.phase, pb.pos, pb.idx, pb.Ntot, pb.H, pb.W, pb.Nz, pb.p_sp,
+      // every object mode's slices count as slices here (the patches of all modes enter the mean)
+      const int nzk = pb.Nz * pb.Ko;
+      const unsigned patches = (unsigned)(pb.B * nzk);
+      k_sparse_sum<N, 256><<<patches, 256, 0, st>>>(pb.phase, pb.pos, pb.idx, pb.Ntot, pb.H, pb.W, nzk, pb.p_sp,
                                                     ws.sppart, ws.status);
       PTY_LAUNCH_CHECK("k_sparse_sum", -1);
       k_sparse_finalize<<<1, 256, 0, st>>>(ws.sppart, (int)patches, (double)patches * NN, pb.p_sp, pb.w_sp,
@@ -1531,7 +1535,7 @@ struct Pass {
         if (!want_obj && !pb.accumulate &&
             cudaMemsetAsync(pb.g_phase, 0, sizeof(float) * nobj, st) != cudaSuccess)
           return memset_failed();
-        k_sparse_grad<N, 256><<<patches, 256, 0, st>>>(pb.phase, pb.pos, pb.idx, pb.Ntot, pb.H, pb.W, pb.Nz, pb.p_sp,
+        k_sparse_grad<N, 256><<<patches, 256, 0, st>>>(pb.phase, pb.pos, pb.idx, pb.Ntot, pb.H, pb.W, nzk, pb.p_sp,
                                                        pb.w_sp, ws.scal, pb.g_phase, ws.status);
         PTY_LAUNCH_CHECK("k_sparse_grad", -1);
       }
@@ -1551,7 +1555,7 @@ struct Pass {
           return memset_failed();
       }
       if (pb.B > 0) {
-        k_scalar_grad<<<1, 256, 0, st>>>(ws.spart, pb.idx, pb.B, pb.M, pb.Ntot, pb.global_tilt, gm, pb.g_pos,
+        k_scalar_grad<<<1, 256, 0, st>>>(ws.spart, pb.idx, pb.B, pb.M * pb.Ko, pb.Ntot, pb.global_tilt, gm, pb.g_pos,
                                          pb.g_tilt, pb.g_dz, pb.accumulate);
         PTY_LAUNCH_CHECK("k_scalar_grad", 8);
       } else if (!pb.accumulate) {

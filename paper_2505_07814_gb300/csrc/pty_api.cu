@@ -60,8 +60,9 @@ int effective_stride(const pty_geom& g) {
 
 size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspace* out) {
   const size_t NN = (size_t)g.N * g.N;
-  const size_t nobj = (size_t)g.Nz * g.H * g.W;
-  const size_t waves = (size_t)B * g.M;
+  const size_t Ko = g.obj_modes > 1 ? (size_t)g.obj_modes : 1;
+  const size_t nobj = Ko * g.Nz * g.H * g.W;
+  const size_t waves = (size_t)B * g.M * Ko;
   const bool grad = mode != MODE_FORWARD;
   const bool want_obj = grad && (g.grad_mask & (PTY_GRAD_AMP | PTY_GRAD_PHASE));
   const bool want_prop = grad && (g.grad_mask & (PTY_GRAD_DZ | PTY_GRAD_TILT)) && g.Nz > 1;
@@ -101,7 +102,7 @@ size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspac
       w.pac = (float*)take(sizeof(float) * 3 * NN);
       w.pacpart = (double*)take(sizeof(double) * (size_t)(B > 0 ? B : 1));
     }
-    if (g.w_sparse > 0.f) w.sppart = (double*)take(sizeof(double) * (size_t)(B > 0 ? B : 1) * g.Nz);
+    if (g.w_sparse > 0.f) w.sppart = (double*)take(sizeof(double) * (size_t)(B > 0 ? B : 1) * g.Nz * Ko);
   }
   if (g.fft_impl != PTY_FFT_FP32) {
     w.wave = (float2*)take(sizeof(float2) * waves * NN);
@@ -160,7 +161,11 @@ int validate_geom(const pty_geom* g) {
     set_error("ckpt_stride %d < 0", g->ckpt_stride);
     return PTY_EINVAL;
   }
-  if ((double)g->Nz * g->H * g->W > 4.0e9) {
+  if (g->obj_modes < 0 || g->obj_modes > 64) {
+    set_error("obj_modes = %d outside 0 .. 64", g->obj_modes);
+    return PTY_EINVAL;
+  }
+  if ((double)(g->obj_modes > 1 ? g->obj_modes : 1) * g->Nz * g->H * g->W > 4.0e9) {
     set_error("object too large");
     return PTY_EINVAL;
   }
@@ -174,7 +179,7 @@ static int prepare(const pty_geom* g, int B, int mode, const int32_t* idx, const
   int rc = validate_geom(g);
   if (rc) return rc;
   REQUIRE(B >= 0, "batch size %d < 0", B);
-  REQUIRE((double)B * g->M < 2.0e9, "batch too large");
+  REQUIRE((double)B * g->M * (g->obj_modes > 1 ? g->obj_modes : 1) < 2.0e9, "batch too large");
   REQUIRE(amp && phase && probe && pos && tilt && dz, "a parameter pointer is NULL");
   REQUIRE(B == 0 || idx, "idx is NULL");
   REQUIRE(B == 0 || g->Ntot >= 1, "a non-empty batch needs Ntot >= 1");
@@ -190,6 +195,7 @@ static int prepare(const pty_geom* g, int B, int mode, const int32_t* idx, const
   memset(pb, 0, sizeof(*pb));
   pb->N = g->N;
   pb->M = g->M;
+  pb->Ko = g->obj_modes > 1 ? g->obj_modes : 1;
   pb->Nz = g->Nz;
   pb->H = g->H;
   pb->W = g->W;
@@ -365,7 +371,7 @@ int pty_adam_update(const pty_geom* geom, float* amp, float* phase, float* probe
   if (rc) return rc;
   REQUIRE(adam, "adam state is NULL");
   REQUIRE(step >= 1, "Adam step count must be >= 1");
-  const size_t nobj = (size_t)geom->Nz * geom->H * geom->W;
+  const size_t nobj = (size_t)(geom->obj_modes > 1 ? geom->obj_modes : 1) * geom->Nz * geom->H * geom->W;
   const size_t nprobe = 2 * (size_t)geom->M * geom->N * geom->N;
   const size_t ntilt = geom->global_tilt ? 2 : 2 * (size_t)geom->Ntot;
   AdamArgs a;

@@ -12,7 +12,7 @@ namespace pty {
 // layout: element p1 * N + p0 holds frequency (kbin(p0), kbin(p1)) along (axis 0, axis 1).
 struct Workspace {
   int* status;     // [1]   device status bits
-  float2* T;       // [Nz][H][W]      transmission amp * exp(i phase)
+  float2* T;       // [Ko][Nz][H][W]  transmission amp * exp(i phase)
   float2* Phat;    // [M][N*N]        probe spectra F[P_m] (k-space layout)
   float2* ckpt;     // [B][M][Nz][N*N] wave entering each slice (natural layout); recompute mode:
                     // [B][M][K][N*N], the current segment's entering waves
@@ -25,7 +25,7 @@ struct Workspace {
   float* u;        // [B][N*N]        dL/dI before the batch normaliser (k-space)
   double* lpart;   // [B][2]          per-pattern loss sums
   double* scal;    // [4]             {dL/dI normaliser, loss, -, -}
-  float2* gT;      // [Nz][H][W]      dL/dT accumulator
+  float2* gT;      // [Ko][Nz][H][W]  dL/dT accumulator
   float2* gPhat;   // [M][N*N]        probe-spectrum gradient accumulator (k-space)
   double* spart;   // [B][M][5]       per-wave {pos0, pos1, tilt0, tilt1, dz} gradient partials
   // split-precision DFT modes only
@@ -35,7 +35,7 @@ struct Workspace {
   // extra loss terms (when their weights are non-zero)
   float* pac;      // [3][N*N]        sum over the batch of I_model, of I_meas (k-space), PACBED dL/dI
   double* pacpart; // [B]             per-pattern sums of I_meas^p_pacbed
-  double* sppart;  // [B][Nz]         per-patch sums of |phase|^p_sparse
+  double* sppart;  // [B][Ko*Nz]      per-patch sums of |phase|^p_sparse
   void* pieces0;   // [B][M][N][pieces][2N] 16-bit split operands of the tensor-core GEMMs
   void* pieces1;   // (the same, for the second GEMM of a 2D transform)
 };
@@ -47,6 +47,7 @@ enum Mode { MODE_FORWARD = 0, MODE_GRAD = 1, MODE_FORWARD_SAVE = 2, MODE_BACKWAR
 
 struct Problem {
   int N, M, Nz, H, W, Ntot, B;
+  int Ko;  // object modes (>= 1); waves are ordered (position, probe mode, object mode)
   float dx, lam;
   int loss;
   float p, eps;

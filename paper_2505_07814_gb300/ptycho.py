@@ -42,6 +42,12 @@ class Geometry:
     p_pacbed: float = 0.0
     w_sparse: float = 0.0
     p_sparse: float = 0.0
+    obj_modes: int = 1  # object modes K (Eq. 2): amp / phase are [K, Nz, H, W] when K > 1
+
+    @property
+    def nobj(self) -> int:
+        """Elements of the amplitude (or phase) array: K x Nz x H x W."""
+        return max(self.obj_modes, 1) * self.Nz * self.H * self.W
 
     @property
     def grad_mask(self) -> int:
@@ -54,11 +60,11 @@ class Geometry:
         return _lib.pty_geom(self.N, self.M, self.Nz, self.H, self.W, self.Ntot, self.dx, self.lam,
                              LOSS[self.loss], self.p, self.eps, self.grad_mask, int(self.global_tilt),
                              int(self.ckpt_stride), FFT_IMPL[self.fft], float(self.w_pacbed), float(self.p_pacbed),
-                             float(self.w_sparse), float(self.p_sparse))
+                             float(self.w_sparse), float(self.p_sparse), int(self.obj_modes))
 
     def checkpoint_bytes(self, B: int) -> int:
         """Bytes the adjoint's forward record takes for a batch of B positions (see ckpt_stride)."""
-        wave = 8 * self.N * self.N * B * self.M
+        wave = 8 * self.N * self.N * B * self.M * max(self.obj_modes, 1)
         if self.ckpt_stride <= 1 or self.fft != "fp32":
             return wave * (2 * self.Nz - 1)
         K = min(self.ckpt_stride, self.Nz)
@@ -67,7 +73,7 @@ class Geometry:
 
 @dataclasses.dataclass
 class Params:
-    """Device tensors: amp/phase float32 [Nz,H,W], probe complex64 [M,N,N], pos float32 [Ntot,2],
+    """Device tensors: amp/phase float32 [Nz,H,W] (or [K,Nz,H,W] with object modes), probe complex64 [M,N,N], pos float32 [Ntot,2],
     tilt float32 [Ntot,2] (or [2]), dz float32 [1]."""
     amp: torch.Tensor
     phase: torch.Tensor
@@ -123,7 +129,7 @@ class Ptycho:
 
     def _param_ptrs(self, p: Params):
         g = self.geom
-        nobj = g.Nz * g.H * g.W
+        nobj = g.nobj
         ntilt = 2 if g.global_tilt else 2 * g.Ntot
         return (_ptr(p.amp, torch.float32, nobj, "amp"), _ptr(p.phase, torch.float32, nobj, "phase"),
                 _ptr(p.probe, torch.complex64, g.M * g.N * g.N, "probe"),
@@ -234,7 +240,7 @@ def constrain(pt: Ptycho, params: Params, phase_positivity: float = 0.0, rz_sigm
     orthogonalisation; then on amp / phase the relaxed k_z filter (Eq. 10-12), the relaxed depth
     blur along the slices (Eq. 13) and the relaxed phase >= 0 clip."""
     g = pt.geom
-    nobj = g.Nz * g.H * g.W
+    nobj = g.nobj
     c = _lib.pty_constraints(float(phase_positivity), float(rz_sigma), float(rz_relax), float(kz_beta),
                              float(kz_alpha), float(kz_relax), int(bool(orthogonalize_probe)))
     need = _lib.pty_constrain_workspace_size(pt.cg, c)
