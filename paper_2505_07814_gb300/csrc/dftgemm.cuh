@@ -333,8 +333,8 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs g) {
       FarStore<N> hk{a.Psi ? a.Psi + (size_t)bm * NN : nullptr, a.Imode + (size_t)bm * NN};
       hk.template operator()<U>(lo, 0, h, STEP, v);
     } else if constexpr (ST == GS_FARGRAD) {
-      FarGradLoad<N> hk{g.a.u + (size_t)b * NN, g.a.Psi + (size_t)bm * NN, (float)(2.0 * g.a.scal[0] / N),
-                        g.a.pacg, 2.0f / N};
+      FarGradLoad<N> hk{g.a.u + (size_t)b * NN, g.a.Psi + (size_t)bm * NN,
+                        g.a.u_scaled ? 1.0f : (float)(2.0 * g.a.scal[0] / N)};
       hk.template operator()<U>(lo, 0, h, STEP, v);
     } else if constexpr (ST == GS_ADJTRANS) {
       const bool obj = (g.a.grad_mask & (PTY_GRAD_AMP | PTY_GRAD_PHASE)) != 0;

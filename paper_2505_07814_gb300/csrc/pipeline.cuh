@@ -368,7 +368,9 @@ struct FarStore {
   }
 };
 
-template <int N, int T>
+// OM: object modes (a.Ko > 1).  The single-mode instantiation folds Ko = 1, so its code is that of a
+// plain (position, probe mode) kernel.
+template <int N, int T, bool OM = false>
 __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   using F = Fft2<N, T>;
   constexpr int RS = F::RS;
@@ -382,7 +384,8 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   float2* pm1 = pm0 + N;  // propagator factor along axis 1
   const int tid = threadIdx.x;
   const int bm = blockIdx.x / F::C;  // wave (position, mode); a cluster of F::C CTAs per wave
-  const int b = bm / (a.M * a.Ko), m = (bm / a.Ko) % a.M;  // waves: (position, probe mode, object mode)
+  const int Ko = OM ? a.Ko : 1;
+  const int b = bm / (a.M * Ko), m = (bm / Ko) % a.M;  // waves: (position, probe mode, object mode)
   const int j = checked_index(a.idx, b, a.Ntot, a.status);
   int i0, i1;
   float d0, d1, th0, th1;
@@ -390,7 +393,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   tilt_of(a.tilt, a.global_tilt, j, &th0, &th1);
   const float dz = a.dz[0];
   const size_t plane = (size_t)a.H * a.W;
-  const float2* Tpatch = a.T + (size_t)(bm % a.Ko) * a.Nz * plane + (size_t)i0 * a.W + i1;
+  const float2* Tpatch = a.T + (OM ? (size_t)(bm % Ko) * a.Nz * plane : 0) + (size_t)i0 * a.W + i1;
   prefetch_patch<N>(Tpatch, a.W);
 
   build_twiddles<N>(tw);
@@ -471,7 +474,7 @@ struct CkptStore {
   }
 };
 
-template <int N, int T>
+template <int N, int T, bool OM = false>
 __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_recompute(FwdArgs a) {
   using F = Fft2<N, T>;
   constexpr int RS = F::RS;
@@ -485,7 +488,8 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_recompute(FwdArgs a) {
   float2* pm1 = pm0 + N;
   const int tid = threadIdx.x;
   const int bm = blockIdx.x / F::C;  // wave (position, mode); a cluster of F::C CTAs per wave
-  const int b = bm / (a.M * a.Ko), m = (bm / a.Ko) % a.M;  // waves: (position, probe mode, object mode)
+  const int Ko = OM ? a.Ko : 1;
+  const int b = bm / (a.M * Ko), m = (bm / Ko) % a.M;  // waves: (position, probe mode, object mode)
   const int j = checked_index(a.idx, b, a.Ntot, a.status);
   int i0, i1;
   float d0, d1, th0, th1;
@@ -493,7 +497,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_recompute(FwdArgs a) {
   tilt_of(a.tilt, a.global_tilt, j, &th0, &th1);
   const float dz = a.dz[0];
   const size_t plane = (size_t)a.H * a.W;
-  const float2* Tpatch = a.T + (size_t)(bm % a.Ko) * a.Nz * plane + (size_t)i0 * a.W + i1;
+  const float2* Tpatch = a.T + (OM ? (size_t)(bm % Ko) * a.Nz * plane : 0) + (size_t)i0 * a.W + i1;
   const int K = a.kstride;
   build_twiddles<N>(tw);
   fwd_tables<N>(ra0, ra1, pm0, pm1, d0, d1, th0, th1, dz, a.dx, a.lam);
@@ -621,7 +625,8 @@ __device__ __forceinline__ void loss_pixel(float I, float d, float p, float eps,
   }
 }
 
-template <int N, int T>
+// PAC: the PACBED sums are on (a.pac != nullptr); the plain instantiation carries none of that work.
+template <int N, int T, bool PAC = false>
 __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
   constexpr int RS = N + 1;
   constexpr int NN = N * N;
@@ -651,7 +656,7 @@ __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
       sd += Dp;
       st += term;
       L[l] = u;
-      if (a.pac) {
+      if (PAC) {
         const int e = kpos1<N>(k1) * N + kpos0<N>(k0);
         atomicAdd(a.pac + e, I);
         atomicAdd(a.pac + NN + e, d);
@@ -671,7 +676,7 @@ __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
       a.lpart[2 * b + 1] = y;
     }
   }
-  if (a.pac) {
+  if (PAC) {
     __syncthreads();
     double x = sp, y = 0.0;
     block_sum2<T>(x, y, red);
@@ -682,7 +687,7 @@ __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
 // The same without shared-memory staging (the N = 256 staging area would not fit): walks the
 // pattern in k-space order (coalesced mode sum and dL/dI), gathering the measured pattern and
 // scattering the modelled one in detector order.
-template <int N, int T>
+template <int N, int T, bool PAC = false>
 __global__ void __launch_bounds__(T) k_loss_gather(LossArgs a) {
   constexpr int NN = N * N;
   __shared__ double red[2 * (T / 32)];
@@ -703,7 +708,7 @@ __global__ void __launch_bounds__(T) k_loss_gather(LossArgs a) {
       sd += Dp;
       st += term;
       a.u[(size_t)b * NN + e] = u;
-      if (a.pac) {
+      if (PAC) {
         atomicAdd(a.pac + e, I);
         atomicAdd(a.pac + NN + e, d);
         sp += pow_nn(d, a.pac_p);
@@ -718,7 +723,7 @@ __global__ void __launch_bounds__(T) k_loss_gather(LossArgs a) {
       a.lpart[2 * b + 1] = y;
     }
   }
-  if (a.pac) {
+  if (PAC) {
     __syncthreads();
     double x = sp, y = 0.0;
     block_sum2<T>(x, y, red);
@@ -761,6 +766,18 @@ __global__ void __launch_bounds__(1024) k_pacbed(float* __restrict__ pac, const 
     const float dpow = p == 1.0f ? 1.0f : (A > 0.f ? p * powf(A, p - 1.0f) : 0.f);
     pac[2 * NN + e] = c * d * dpow;
   }
+}
+
+// The far-field weight of the adjoint with the PACBED term folded in, for every pattern of the
+// batch: u <- 2 (s u + g_pacbed) / N, s the dL/dI normaliser (scal[0]); the adjoint then reads u
+// with gs = 1, so its first transform carries no extra operand.
+template <int N>
+__global__ void k_pacbed_fold(float* __restrict__ u, const float* __restrict__ pacg, const double* __restrict__ scal,
+                              size_t n) {
+  constexpr int NN = N * N;
+  const float gs = (float)(2.0 * scal[0] / N), gp = 2.0f / N;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    u[i] = fmaf(gp, pacg[i % NN], gs * u[i]);
 }
 
 // Batch loss (Eq. 5 / 6) and the normaliser of dL/dI, in FP64, fixed summation order.
@@ -813,7 +830,7 @@ struct AdjArgs {
   float2* gT;
   float2* gPhat;
   double* spart;  // [wave][5], accumulated over the segments of one pass
-  const float* pacg;  // PACBED dL/dI [N*N] (k-space) or nullptr
+  int u_scaled;  // 1: u holds 2 dL/dI / N with the PACBED term folded in (k_pacbed_fold)
   int* status;
   // slices [s0, s1) of this launch; the adjoint wave is carried between launches in gstate
   int s0, s1;
@@ -834,9 +851,7 @@ struct FarGradLoad {
   static constexpr int kChunk = PTY_KG;
   const float* u;
   const float2* Psi;
-  float gs;
-  const float* pg = nullptr;  // PACBED dL/dI (the same for every pattern), or nullptr
-  float gp = 0.f;             // its factor 2 / N
+  float gs;  // 2 x (dL/dI normaliser) / N, or 1 when u already holds the scaled weight
   template <int K>
   __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     float2 p[K];
@@ -845,11 +860,10 @@ struct FarGradLoad {
     for (int k = 0; k < K; ++k) {
       const int e = kidx<N>(r0 + k * rs, c0 + k * cs);
       p[k] = ld_ro(Psi + e);
-      w[k] = gs * ld_ro(u + e);
-      if (pg) w[k] = fmaf(gp, ld_ro(pg + e), w[k]);
+      w[k] = ld_ro(u + e);
     }
 #pragma unroll
-    for (int k = 0; k < K; ++k) v[k] = cscale(p[k], w[k]);
+    for (int k = 0; k < K; ++k) v[k] = cscale(p[k], gs * w[k]);
   }
 };
 // transmission of slice s backwards: dL/dT += conj(psi_in) g (scatter-add), g <- conj(T) g
@@ -940,7 +954,7 @@ struct ProbeStore {
   }
 };
 
-template <int N, int T>
+template <int N, int T, bool OM = false>
 __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   using F = Fft2<N, T>;
   constexpr int RS = F::RS;
@@ -961,7 +975,8 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   double* red = reinterpret_cast<double*>(f1 + N);
   const int tid = threadIdx.x, lane = tid & 31;
   const int bm = blockIdx.x / F::C;  // wave (position, mode); a cluster of F::C CTAs per wave
-  const int b = bm / (a.M * a.Ko), m = (bm / a.Ko) % a.M;  // waves: (position, probe mode, object mode)
+  const int Ko = OM ? a.Ko : 1;
+  const int b = bm / (a.M * Ko), m = (bm / Ko) % a.M;  // waves: (position, probe mode, object mode)
   const int j = checked_index(a.idx, b, a.Ntot, a.status);
   int i0, i1;
   float d0, d1, th0, th1;
@@ -973,7 +988,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   const bool want_pos = (a.grad_mask & PTY_GRAD_POS) != 0;
   const bool want_prop = (a.grad_mask & (PTY_GRAD_DZ | PTY_GRAD_TILT)) != 0 && a.vhat != nullptr;
   const size_t plane = (size_t)a.H * a.W;
-  const size_t patch = (size_t)(bm % a.Ko) * a.Nz * plane + (size_t)i0 * a.W + i1;
+  const size_t patch = (OM ? (size_t)(bm % Ko) * a.Nz * plane : 0) + (size_t)i0 * a.W + i1;
   // slot pointers relative to slice numbers (ck_base + s * NN is slice s's entering wave, vh_base +
   // (s - 1) * NN the spectrum entering slice s)
   const float2* ck_base = want_obj ? a.ckpt + ((ptrdiff_t)bm * a.ck_per_wave - a.ck_first) * NN : nullptr;
@@ -988,8 +1003,8 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   if (a.s1 == a.Nz) {
     // g_psi = F_ortho^-1[2 dL/dI Psi] = (1/N) unnormalised inverse of 2 dL/dI Psi; its column step
     // is fused with the last slice's transmission below (same step structure as the forward kernel).
-    FarGradLoad<N> farg{a.u + (size_t)b * NN, a.Psi + (size_t)bm * NN, (float)(2.0 * a.scal[0] / N), a.pacg,
-                        2.0f / N};
+    FarGradLoad<N> farg{a.u + (size_t)b * NN, a.Psi + (size_t)bm * NN,
+                        a.u_scaled ? 1.0f : (float)(2.0 * a.scal[0] / N)};
     F::row_inv(s, tw, farg);
     F::block_inv(s, tw);
   } else {
@@ -1289,19 +1304,26 @@ struct Pass {
     nseg = (pb.Nz + K - 1) / K;
   }
 
+  // the fused kernels for this problem's object-mode count
+  auto fwd_kernel() const { return pb.Ko > 1 ? k_forward<N, TF, true> : k_forward<N, TF, false>; }
+  auto recompute_kernel() const { return pb.Ko > 1 ? k_recompute<N, TF, true> : k_recompute<N, TF, false>; }
+  auto adj_kernel() const { return pb.Ko > 1 ? k_adjoint<N, TA, true> : k_adjoint<N, TA, false>; }
+
   int set_attributes() {
-    bool ok = cudaFuncSetAttribute(k_forward<N, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    bool ok = cudaFuncSetAttribute(fwd_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)fwd_smem_bytes<N>()) == cudaSuccess &&
-              cudaFuncSetAttribute(k_recompute<N, TF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+              cudaFuncSetAttribute(recompute_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)fwd_smem_bytes<N>()) == cudaSuccess &&
-              cudaFuncSetAttribute(k_adjoint<N, TA>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+              cudaFuncSetAttribute(adj_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)adj_smem_bytes<N, TA>()) == cudaSuccess &&
               cudaFuncSetAttribute(k_probe_spectrum<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)probe_smem()) == cudaSuccess &&
               cudaFuncSetAttribute(k_probe_grad<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)probe_smem()) == cudaSuccess;
     if constexpr (N != 256) {
-      ok = ok && cudaFuncSetAttribute(k_loss<N, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      ok = ok && cudaFuncSetAttribute(k_loss<N, T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)loss_smem_bytes<N>()) == cudaSuccess;
+      ok = ok && cudaFuncSetAttribute(k_loss<N, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)loss_smem_bytes<N>()) == cudaSuccess;
     }
     if (!ok) {
@@ -1390,9 +1412,9 @@ struct Pass {
     la.pac_p = pb.p_pac;
     if (pac && cudaMemsetAsync(ws.pac, 0, sizeof(float) * 2 * NN, st) != cudaSuccess) return memset_failed();
     if constexpr (N == 256) {
-      k_loss_gather<N, T><<<pb.B, T, 0, st>>>(la);
+      (pac ? k_loss_gather<N, T, true> : k_loss_gather<N, T, false>)<<<pb.B, T, 0, st>>>(la);
     } else {
-      k_loss<N, T><<<pb.B, T, loss_smem_bytes<N>(), st>>>(la);
+      (pac ? k_loss<N, T, true> : k_loss<N, T, false>)<<<pb.B, T, loss_smem_bytes<N>(), st>>>(la);
     }
     PTY_LAUNCH_CHECK("k_loss", 3);
     if (I_meas) {
@@ -1402,6 +1424,12 @@ struct Pass {
         k_pacbed<N><<<1, 1024, 0, st>>>(ws.pac, ws.pacpart, pb.B, pb.p_pac, pb.w_pac, pb.loss_out, ws.scal,
                                         ws.status);
         PTY_LAUNCH_CHECK("k_pacbed", -1);
+        if (pb.mode == MODE_GRAD) {
+          const size_t n = (size_t)pb.B * NN;
+          k_pacbed_fold<N><<<(unsigned)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8), 256, 0, st>>>(
+              ws.u, ws.pac + 2 * NN, ws.scal, n);
+          PTY_LAUNCH_CHECK("k_pacbed_fold", -1);
+        }
       }
     }
     return PTY_OK;
@@ -1411,7 +1439,7 @@ struct Pass {
   int forward(const float* I_meas) {
     int rc = forward_begin();
     if (rc || pb.B == 0) return rc;
-    PTY_LAUNCH_RC(launch_waves<C>(k_forward<N, TF>, pb.B * pb.M * pb.Ko, TF, fwd_smem_bytes<N>(), st, fwd_args_saved()),
+    PTY_LAUNCH_RC(launch_waves<C>(fwd_kernel(), pb.B * pb.M * pb.Ko, TF, fwd_smem_bytes<N>(), st, fwd_args_saved()),
                   "k_forward", 2);
     return loss_phase(I_meas);
   }
@@ -1450,7 +1478,7 @@ struct Pass {
     aa.gT = ws.gT;
     aa.gPhat = ws.gPhat;
     aa.spart = ws.spart;
-    aa.pacg = (pb.mode == MODE_GRAD && pb.w_pac > 0.f && ws.pac) ? ws.pac + 2 * NN : nullptr;
+    aa.u_scaled = (pb.mode == MODE_GRAD && pb.w_pac > 0.f && ws.pac) ? 1 : 0;
     aa.status = ws.status;
     aa.gstate = ws.gstate;
     return aa;
@@ -1479,7 +1507,7 @@ struct Pass {
         aa.vh_per_wave = pb.Nz - 1;
         aa.s0 = 0;
         aa.s1 = pb.Nz;
-        PTY_LAUNCH_RC(launch_waves<C>(k_adjoint<N, TA>, pb.B * pb.M * pb.Ko, TA, adj_smem_bytes<N, TA>(), st, aa),
+        PTY_LAUNCH_RC(launch_waves<C>(adj_kernel(), pb.B * pb.M * pb.Ko, TA, adj_smem_bytes<N, TA>(), st, aa),
                       "k_adjoint", 5);
       } else {
         for (int q = nseg - 1; q >= 0; --q) {
@@ -1492,7 +1520,7 @@ struct Pass {
             fa.vhat = want_prop ? ws.vhat : nullptr;
             fa.s0 = s0;
             fa.s1 = s1;
-            PTY_LAUNCH_RC(launch_waves<C>(k_recompute<N, TF>, pb.B * pb.M * pb.Ko, TF, fwd_smem_bytes<N>(), st, fa),
+            PTY_LAUNCH_RC(launch_waves<C>(recompute_kernel(), pb.B * pb.M * pb.Ko, TF, fwd_smem_bytes<N>(), st, fa),
                           "k_recompute", -1);
           }
           aa.ckpt = ws.ckpt;
@@ -1503,7 +1531,7 @@ struct Pass {
           aa.vh_per_wave = K;
           aa.s0 = s0;
           aa.s1 = s1;
-          PTY_LAUNCH_RC(launch_waves<C>(k_adjoint<N, TA>, pb.B * pb.M * pb.Ko, TA, adj_smem_bytes<N, TA>(), st, aa),
+          PTY_LAUNCH_RC(launch_waves<C>(adj_kernel(), pb.B * pb.M * pb.Ko, TA, adj_smem_bytes<N, TA>(), st, aa),
                         "k_adjoint", q == 0 ? 5 : -1);
         }
       }
