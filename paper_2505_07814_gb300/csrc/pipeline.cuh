@@ -1080,22 +1080,60 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Phase-sparsity term (Eq. 8): <|phase|^p>^(1/p) over every slice of every batch position's patch
+// Phase-sparsity term (Eq. 8): <|phase|^p>^(1/p) over every slice of every batch position's patch.
+// With c(y, x) the number of batch patches that contain pixel (y, x), the sum over patches is the
+// sum over pixels of c |phase|^p and the gradient of a pixel is c times a patch's, so the term is
+// one pass over the object with no atomics on it: patch rows mark +1 / -1 at their column ends in
+// a row-difference array (2 int atomics per patch row), a warp-per-row scan turns the marks into c.
 // ---------------------------------------------------------------------------------------------
-// one CTA per (position, slice): the patch's sum of |phase|^p (FP64)
-template <int N, int T>
-__global__ void __launch_bounds__(T) k_sparse_sum(const float* __restrict__ phase, const float* __restrict__ pos,
-                                                  const int32_t* __restrict__ idx, int Ntot, int H, int W, int Nz,
-                                                  float p, double* __restrict__ part, int* status) {
-  __shared__ double red[2 * (T / 32)];
-  const int b = blockIdx.x / Nz, sl = blockIdx.x % Nz;
-  const int j = checked_index(idx, b, Ntot, status);
+constexpr int kSparseBlocks = 152 * 8;  // CTAs of the sum pass (its FP64 partials)
+
+// one CTA per batch position, one thread per patch row
+template <int N>
+__global__ void __launch_bounds__(N) k_cover_marks(const float* __restrict__ pos, const int32_t* __restrict__ idx,
+                                                   int Ntot, int H, int W, int* __restrict__ D, int* status) {
+  const int j = checked_index(idx, blockIdx.x, Ntot, status);
   int i0, i1;
   float d0, d1;
-  patch_corner<N>(pos, j, H, W, &i0, &i1, &d0, &d1, status);
-  const float* ph = phase + (size_t)sl * H * W + (size_t)i0 * W + i1;
+  patch_corner<N>(pos, j, H, W, &i0, &i1, &d0, &d1, status);  // clamped inside the object
+  int* row = D + (size_t)(i0 + threadIdx.x) * (W + 1);
+  atomicAdd(row + i1, 1);
+  atomicAdd(row + i1 + N, -1);
+}
+
+// c(y, x) = inclusive prefix sum of the marks along row y; one warp per row, in place
+static __global__ void k_cover_scan(int* __restrict__ D, int H, int W) {
+  const int lane = threadIdx.x & 31;
+  const int y = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (y >= H) return;
+  int* row = D + (size_t)y * (W + 1);
+  int carry = 0;
+  for (int x0 = 0; x0 < W; x0 += 32) {
+    const int x = x0 + lane;
+    int v = x < W ? row[x] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += u;
+    }
+    v += carry;
+    if (x < W) row[x] = v;
+    carry = __shfl_sync(0xffffffffu, v, 31);
+  }
+}
+
+// FP64 partials of sum over every slice of c |phase|^p
+template <int T>
+__global__ void __launch_bounds__(T) k_sparse_sum(const float* __restrict__ phase, const int* __restrict__ C,
+                                                  int H, int W, size_t n, float p, double* __restrict__ part) {
+  __shared__ double red[2 * (T / 32)];
+  const size_t plane = (size_t)H * W;
   double acc = 0.0;
-  for (int e = threadIdx.x; e < N * N; e += T) acc += pow_nn(fabsf(ph[(size_t)(e / N) * W + e % N]), p);
+  for (size_t i = blockIdx.x * (size_t)T + threadIdx.x; i < n; i += (size_t)gridDim.x * T) {
+    const size_t q = i % plane;
+    const int c = C[(q / W) * (W + 1) + q % W];
+    if (c) acc += (double)c * pow_nn(fabsf(phase[i]), p);
+  }
   double y = 0.0;
   block_sum2<T>(acc, y, red);
   if (threadIdx.x == 0) part[blockIdx.x] = acc;
@@ -1117,26 +1155,19 @@ static __global__ void k_sparse_finalize(const double* __restrict__ part, int np
   }
 }
 
-// dL/dphase += w scal[3] |phase|^(p - 1) sign(phase) at every patch pixel (float atomics: a pixel
-// reached by several positions collects each)
-template <int N, int T>
-__global__ void __launch_bounds__(T) k_sparse_grad(const float* __restrict__ phase, const float* __restrict__ pos,
-                                                   const int32_t* __restrict__ idx, int Ntot, int H, int W, int Nz,
-                                                   float p, float w, const double* __restrict__ scal,
-                                                   float* __restrict__ g_phase, int* status) {
-  const int b = blockIdx.x / Nz, sl = blockIdx.x % Nz;
-  const int j = checked_index(idx, b, Ntot, status);
-  int i0, i1;
-  float d0, d1;
-  patch_corner<N>(pos, j, H, W, &i0, &i1, &d0, &d1, status);
-  const size_t base = (size_t)sl * H * W + (size_t)i0 * W + i1;
-  const float c = w * (float)scal[3];
-  for (int e = threadIdx.x; e < N * N; e += T) {
-    const size_t o = base + (size_t)(e / N) * W + e % N;
-    const float x = phase[o], a = fabsf(x);
-    if (a > 0.f) {
+// dL/dphase += w scal[3] c |phase|^(p - 1) sign(phase) at every pixel (c = patches containing it)
+static __global__ void k_sparse_grad(const float* __restrict__ phase, const int* __restrict__ C, int H, int W,
+                                     size_t n, float p, float w, const double* __restrict__ scal,
+                                     float* __restrict__ g_phase) {
+  const size_t plane = (size_t)H * W;
+  const float f = w * (float)scal[3];
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t q = i % plane;
+    const int c = C[(q / W) * (W + 1) + q % W];
+    const float x = phase[i], a = fabsf(x);
+    if (c && a > 0.f) {
       const float wp = p == 1.0f ? 1.0f : powf(a, p - 1.0f);
-      atomicAdd(g_phase + o, copysignf(c * wp, x));
+      g_phase[i] += copysignf(f * (float)c * wp, x);
     }
   }
 }
@@ -1550,21 +1581,25 @@ struct Pass {
       PTY_LAUNCH_CHECK("k_object_grad", 6);
     }
     if (pb.mode == MODE_GRAD && pb.w_sp > 0.f && ws.sppart && pb.B > 0) {
-      // every object mode's slices count as slices here (the patches of all modes enter the mean)
-      const int nzk = pb.Nz * pb.Ko;
-      const unsigned patches = (unsigned)(pb.B * nzk);
-      k_sparse_sum<N, 256><<<patches, 256, 0, st>>>(pb.phase, pb.pos, pb.idx, pb.Ntot, pb.H, pb.W, nzk, pb.p_sp,
-                                                    ws.sppart, ws.status);
+      // coverage count of the batch's patches, then one pass over every slice of every object mode
+      if (cudaMemsetAsync(ws.cover, 0, sizeof(int) * (size_t)pb.H * (pb.W + 1), st) != cudaSuccess)
+        return memset_failed();
+      k_cover_marks<N><<<pb.B, N, 0, st>>>(pb.pos, pb.idx, pb.Ntot, pb.H, pb.W, ws.cover, ws.status);
+      PTY_LAUNCH_CHECK("k_cover_marks", -1);
+      k_cover_scan<<<(unsigned)((pb.H + 7) / 8), 256, 0, st>>>(ws.cover, pb.H, pb.W);
+      PTY_LAUNCH_CHECK("k_cover_scan", -1);
+      const double patch_pixels = (double)pb.B * pb.Ko * pb.Nz * NN;  // the mean's denominator
+      k_sparse_sum<256><<<kSparseBlocks, 256, 0, st>>>(pb.phase, ws.cover, pb.H, pb.W, nobj, pb.p_sp, ws.sppart);
       PTY_LAUNCH_CHECK("k_sparse_sum", -1);
-      k_sparse_finalize<<<1, 256, 0, st>>>(ws.sppart, (int)patches, (double)patches * NN, pb.p_sp, pb.w_sp,
-                                           pb.loss_out, ws.scal, ws.status);
+      k_sparse_finalize<<<1, 256, 0, st>>>(ws.sppart, kSparseBlocks, patch_pixels, pb.p_sp, pb.w_sp, pb.loss_out,
+                                           ws.scal, ws.status);
       PTY_LAUNCH_CHECK("k_sparse_finalize", -1);
       if ((gm & PTY_GRAD_PHASE) && pb.g_phase) {
         if (!want_obj && !pb.accumulate &&
             cudaMemsetAsync(pb.g_phase, 0, sizeof(float) * nobj, st) != cudaSuccess)
           return memset_failed();
-        k_sparse_grad<N, 256><<<patches, 256, 0, st>>>(pb.phase, pb.pos, pb.idx, pb.Ntot, pb.H, pb.W, nzk, pb.p_sp,
-                                                       pb.w_sp, ws.scal, pb.g_phase, ws.status);
+        k_sparse_grad<<<object_blocks(), 256, 0, st>>>(pb.phase, ws.cover, pb.H, pb.W, nobj, pb.p_sp, pb.w_sp,
+                                                       ws.scal, pb.g_phase);
         PTY_LAUNCH_CHECK("k_sparse_grad", -1);
       }
     }

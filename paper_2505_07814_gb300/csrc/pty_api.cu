@@ -102,7 +102,10 @@ size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspac
       w.pac = (float*)take(sizeof(float) * 3 * NN);
       w.pacpart = (double*)take(sizeof(double) * (size_t)(B > 0 ? B : 1));
     }
-    if (g.w_sparse > 0.f) w.sppart = (double*)take(sizeof(double) * (size_t)(B > 0 ? B : 1) * g.Nz * Ko);
+    if (g.w_sparse > 0.f) {
+      w.sppart = (double*)take(sizeof(double) * 152 * 8);
+      w.cover = (int*)take(sizeof(int) * (size_t)g.H * (g.W + 1));
+    }
   }
   if (g.fft_impl != PTY_FFT_FP32) {
     w.wave = (float2*)take(sizeof(float2) * waves * NN);

@@ -35,7 +35,8 @@ struct Workspace {
   // extra loss terms (when their weights are non-zero)
   float* pac;      // [3][N*N]        sum over the batch of I_model, of I_meas (k-space), PACBED dL/dI
   double* pacpart; // [B]             per-pattern sums of I_meas^p_pacbed
-  double* sppart;  // [B][Ko*Nz]      per-patch sums of |phase|^p_sparse
+  double* sppart;  // [152*8]         partial sums of c |phase|^p_sparse (sparsity term)
+  int* cover;      // [H][W+1]        patch coverage count c of the batch (sparsity term)
   void* pieces0;   // [B][M][N][pieces][2N] 16-bit split operands of the tensor-core GEMMs
   void* pieces1;   // (the same, for the second GEMM of a 2D transform)
 };
