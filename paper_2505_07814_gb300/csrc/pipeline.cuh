@@ -656,10 +656,9 @@ __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
       sd += Dp;
       st += term;
       L[l] = u;
-      if (PAC) {
-        const int e = kpos1<N>(k1) * N + kpos0<N>(k0);
-        atomicAdd(a.pac + e, I);
-        atomicAdd(a.pac + NN + e, d);
+      if (PAC) {  // sums in detector order: a warp's atomics land on consecutive addresses
+        atomicAdd(a.pac + q, I);
+        atomicAdd(a.pac + NN + q, d);
         sp += pow_nn(d, a.pac_p);
       }
     }
@@ -734,7 +733,8 @@ __global__ void __launch_bounds__(T) k_loss_gather(LossArgs a) {
 // PACBED term (Eq. 7) of one batch, one CTA of 1024 threads: the batch-mean patterns A and C from
 // the sums, d = A^p - C^p, the loss w sqrt(<d^2>) / <I_meas^p> added to *loss_out, and the
 // derivative w d p A^(p-1) / (<I_meas^p> N^2 B sqrt(<d^2>)), the same for every pattern, written to
-// pac[2 N^2 ..] (k-space order) for the adjoint.
+// pac[2 N^2 ..] (k-space order) for the adjoint.  The sums are in the order of the loss kernel's
+// loop: detector order (k_loss, N <= 128) or k-space order (k_loss_gather, N = 256).
 template <int N>
 __global__ void __launch_bounds__(1024) k_pacbed(float* __restrict__ pac, const double* __restrict__ pacpart, int B,
                                                  float p, float w, double* loss_out, double* scal, int* status) {
@@ -764,7 +764,12 @@ __global__ void __launch_bounds__(1024) k_pacbed(float* __restrict__ pac, const 
     const float A = pac[e] * inv_b;
     const float d = pow_nn(A, p) - pow_nn(pac[NN + e] * inv_b, p);
     const float dpow = p == 1.0f ? 1.0f : (A > 0.f ? p * powf(A, p - 1.0f) : 0.f);
-    pac[2 * NN + e] = c * d * dpow;
+    int ek = e;  // k-space position of sum element e
+    if constexpr (N != 256) {
+      const int k0 = (e / N + N / 2) & (N - 1), k1 = (e % N + N / 2) & (N - 1);
+      ek = kpos1<N>(k1) * N + kpos0<N>(k0);
+    }
+    pac[2 * NN + ek] = c * d * dpow;
   }
 }
 
