@@ -39,6 +39,25 @@
 #ifndef PTY_FWD_SPLIT_COL
 #define PTY_FWD_SPLIT_COL 0
 #endif
+// Adjoint L2 prefetch plan (cp.async.bulk.prefetch.L2 of whole 128 KB blocks).  0: at the start of
+// slice s, the checkpoint of slice s - 1 and the spectrum of the next slice's propagation.  1: at
+// the start of slice s the spectrum its own propagation reads, after its transmission step the
+// checkpoint the next slice reads.  2: only before the slice loop.  3: none.  Measured on the
+// multislice workload (N = 128, M = 6, Nz = 8, 512 positions): adjoint 4.13 / 4.07 / 3.74 / 3.69
+// ms; the bulk prefetches cost more than the load latency they hide, so none is the default.
+#ifndef PTY_ADJ_PF
+#define PTY_ADJ_PF 3
+#endif
+// 1: the forward prefetches the next slice's transmission patch to L2 (measured: 2.496 ms with,
+// 2.490 ms without on the same workload)
+#ifndef PTY_FWD_PF
+#define PTY_FWD_PF 0
+#endif
+// 1: the adjoint reads checkpoints and spectra with evict-first (streaming) loads, so they do not
+// displace the transmission and its gradient accumulator from L2 (adjoint 3.685 -> 3.655 ms)
+#ifndef PTY_ADJ_LDCS
+#define PTY_ADJ_LDCS 1
+#endif
 #ifndef PTY_KS
 #define PTY_KS 4
 #endif
@@ -226,6 +245,15 @@ __device__ __forceinline__ float ld_ro(const float* p) {
   return v;
 }
 
+// Checkpoints and spectra the adjoint reads exactly once
+__device__ __forceinline__ float2 ld_once(const float2* p) {
+#if PTY_ADJ_LDCS
+  return __ldcs(p);
+#else
+  return ld_ro(p);
+#endif
+}
+
 // L2 prefetch of a byte range (rounded out to 16-byte boundaries).
 __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
   const uintptr_t a = (uintptr_t)p & ~(uintptr_t)15;
@@ -394,7 +422,9 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   const float dz = a.dz[0];
   const size_t plane = (size_t)a.H * a.W;
   const float2* Tpatch = a.T + (OM ? (size_t)(bm % Ko) * a.Nz * plane : 0) + (size_t)i0 * a.W + i1;
+#if PTY_FWD_PF
   prefetch_patch<N>(Tpatch, a.W);
+#endif
 
   build_twiddles<N>(tw);
   fwd_tables<N>(ra0, ra1, pm0, pm1, d0, d1, th0, th1, dz, a.dx, a.lam);
@@ -408,7 +438,9 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   F::row_inv(s, tw, shift);
   F::block_inv(s, tw);
   for (int sl = 0; sl < a.Nz; ++sl) {
+#if PTY_FWD_PF
     if (sl + 1 < a.Nz) prefetch_patch<N>(Tpatch + (sl + 1) * plane, a.W);
+#endif
     TransLoad<N> trans{Tpatch + sl * plane, a.W, a.ckpt ? a.ckpt + ((size_t)bm * a.Nz + sl) * NN : nullptr};
 #if PTY_FWD_SPLIT_COL
     NoHook none;
@@ -887,7 +919,7 @@ struct AdjTransLoad {
     for (int k = 0; k < K; ++k) {
       const int r = r0 + k * rs, c = c0 + k * cs;
       t[k] = ld_ro(Ts + (size_t)r * W + c);
-      if (ck) ps[k] = ld_ro(ck + r * N + c);
+      if (ck) ps[k] = ld_once(ck + r * N + c);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -911,7 +943,7 @@ struct AdjPropStore {
     if (vh) {
       float2 x[K];
 #pragma unroll
-      for (int k = 0; k < K; ++k) x[k] = ld_ro(vh + kidx<N>(r0 + k * rs, c0 + k * cs));
+      for (int k = 0; k < K; ++k) x[k] = ld_once(vh + kidx<N>(r0 + k * rs, c0 + k * cs));
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int r = r0 + k * rs, c = c0 + k * cs;
@@ -998,8 +1030,10 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   // (s - 1) * NN the spectrum entering slice s)
   const float2* ck_base = want_obj ? a.ckpt + ((ptrdiff_t)bm * a.ck_per_wave - a.ck_first) * NN : nullptr;
   const float2* vh_base = want_prop ? a.vhat + ((ptrdiff_t)bm * a.vh_per_wave - a.vh_first) * NN : nullptr;
+#if PTY_ADJ_PF < 3
   if (want_obj) prefetch_block<N>(ck_base + (size_t)(a.s1 - 1) * NN);
   if (want_prop && a.s1 - 1 > a.s0 - 1 && a.s1 >= 2) prefetch_block<N>(vh_base + (size_t)(a.s1 - 2) * NN);
+#endif
 
   build_twiddles<N>(tw);
   adj_tables<N>(cm0, cm1, cr0, cr1, e0, e1, c0, c1, f0, f1, d0, d1, th0, th1, dz, a.dx, a.lam);
@@ -1021,8 +1055,12 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   float gdz = 0.f, gt0 = 0.f, gt1 = 0.f, gp0 = 0.f, gp1 = 0.f;
   NoHook none;
   for (int sl = a.s1 - 1; sl >= a.s0; --sl) {
+#if PTY_ADJ_PF == 0
     if (sl - 1 >= a.s0 && want_obj) prefetch_block<N>(ck_base + (size_t)(sl - 1) * NN);
     if (sl - 2 >= a.s0 - 1 && sl >= 2 && want_prop) prefetch_block<N>(vh_base + (size_t)(sl - 2) * NN);
+#elif PTY_ADJ_PF == 1
+    if (sl >= 1 && sl < a.s1 - 1 && want_prop) prefetch_block<N>(vh_base + (size_t)(sl - 1) * NN);
+#endif
     AdjTransLoad<N> trans{a.T + sl * plane + patch, a.gT + sl * plane + patch,
                           want_obj ? ck_base + (size_t)sl * NN : nullptr, a.W};
     if (sl > 0 || want_probe || want_pos) {  // (sl > 0: propagate back into slice sl - 1)
@@ -1035,6 +1073,9 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
       F::col_fwd(s, tw, none);
 #else
       F::template col_inv_fwd<true>(s, tw, trans);
+#endif
+#if PTY_ADJ_PF == 1
+      if (sl - 1 >= a.s0 && want_obj) prefetch_block<N>(ck_base + (size_t)(sl - 1) * NN);
 #endif
       F::block_fwd(s, tw);
       if (sl > 0) {
