@@ -662,38 +662,72 @@ def main():
                     "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; fp16 taken equal)"}
     stages = {k: v / max(ncalls, 1) for k, v in stage_ms.items()}
 
-    # end to end through the public API from pinned host buffers
-    host = {n: getattr(params, n).cpu().pin_memory() for n in ("amp", "phase", "probe", "pos", "tilt", "dz")}
+    # end to end through the public API from pinned host buffers: every step copies its inputs in
+    # (every parameter and the batch's measured patterns) and every gradient and the loss out.  The
+    # copies run on a second stream into double buffers, so that step k + 1's inputs and step k's
+    # outputs move while the next step computes; the timed region spans all e_steps steps, with the
+    # L2 flush before each step timed separately and taken out.
+    names = ("amp", "phase", "probe", "pos", "tilt", "dz")
+    host = {n: getattr(params, n).cpu().pin_memory() for n in names}
     h_rows = torch.tensor(I_rows).pin_memory()
-    h_grads = {n: torch.empty_like(getattr(grads, n), device="cpu").pin_memory()
-               for n in ("amp", "phase", "probe", "pos", "tilt", "dz")}
-    h_loss = torch.empty(1, dtype=torch.float64).pin_memory()
+    h_grads = [{n: torch.empty_like(getattr(grads, n), device="cpu").pin_memory() for n in names} for _ in range(2)]
+    h_loss = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
+    d_params = [params, params.zeros_like()]
+    d_grads = [grads, params.zeros_like()]
+    d_meas = [I_meas, torch.zeros_like(I_meas)]
+    d_loss = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in range(2)]
+    comp = torch.cuda.current_stream(dev)
+    cs = torch.cuda.Stream(device=dev)
+    in_ready, comp_done, out_done = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
     e_steps = min(args.e2e_steps, args.steps)
-    h2d = d2h = 0
+    h2d = sum(host[n].numel() * host[n].element_size() for n in names)
+    h2d += sum((hi - lo) * w.N * w.N * 4 for lo, hi in row_runs(idx_h[0]))
+    d2h = sum(h_grads[0][n].numel() * h_grads[0][n].element_size() for n in names) + 8
+
+    def issue_inputs(k):
+        j = k % 2
+        if k >= 2:
+            cs.wait_event(comp_done[j])  # step k - 2 is done with buffer j
+        with torch.cuda.stream(cs):
+            for n in names:
+                getattr(d_params[j], n).copy_(host[n], non_blocking=True)
+            for lo, hi in row_runs(idx_h[k % 8]):  # the measured patterns this batch reads
+                r0 = row_of[lo]
+                d_meas[j][lo:hi].copy_(h_rows[r0:r0 + hi - lo], non_blocking=True)
+        in_ready[j].record(cs)
+
     es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e_steps)]
     torch.cuda.synchronize()
-    e2e_ms = 0.0
+    es.record(comp)
+    issue_inputs(0)
     for k in range(e_steps):
+        j = k % 2
+        if k + 1 < e_steps:
+            issue_inputs(k + 1)
+        fl[k][0].record(comp)
         flush.zero_()
-        idx = idx_t[k % 8]
-        es.record()
-        h2d = d2h = 0
-        for n in host:
-            getattr(params, n).copy_(host[n], non_blocking=True)
-            h2d += host[n].numel() * host[n].element_size()
-        for lo, hi in row_runs(idx_h[k % 8]):  # the measured patterns this batch reads
-            r0 = row_of[lo]
-            I_meas[lo:hi].copy_(h_rows[r0:r0 + hi - lo], non_blocking=True)
-            h2d += (hi - lo) * w.N * w.N * 4
-        loss, _ = pt.loss_grad(params, idx, I_meas, grads=grads)
-        for n in h_grads:
-            h_grads[n].copy_(getattr(grads, n), non_blocking=True)
-            d2h += h_grads[n].numel() * h_grads[n].element_size()
-        h_loss.copy_(loss, non_blocking=True)
-        d2h += 8
-        ee.record()
-        ee.synchronize()
-        e2e_ms += es.elapsed_time(ee)
+        fl[k][1].record(comp)
+        comp.wait_event(in_ready[j])
+        if k >= 2:
+            comp.wait_event(out_done[j])  # step k - 2's gradients have left buffer j
+        loss, _ = pt.loss_grad(d_params[j], idx_t[k % 8], d_meas[j], grads=d_grads[j])
+        d_loss[j].copy_(loss)
+        comp_done[j].record(comp)
+        cs.wait_event(comp_done[j])
+        with torch.cuda.stream(cs):
+            for n in names:
+                h_grads[j][n].copy_(getattr(d_grads[j], n), non_blocking=True)
+            h_loss[j].copy_(d_loss[j], non_blocking=True)
+        out_done[j].record(cs)
+    for j in range(2):
+        comp.wait_event(out_done[j])
+    ee.record(comp)
+    ee.synchronize()
+    e2e_ms = es.elapsed_time(ee) - sum(a.elapsed_time(b) for a, b in fl)
+    assert pt.status() == 0
+    for n in names:  # the last step's gradients reached the host
+        assert torch.equal(h_grads[(e_steps - 1) % 2][n], getattr(d_grads[(e_steps - 1) % 2], n).cpu())
     e2e_value = world * upd_step * e_steps / (e2e_ms / 1e3)
 
     cpu = None
@@ -719,7 +753,8 @@ def main():
                            "parallelism": "dp%d" % world},
                 "roofline": roofline, "stage_ms_per_call": stages,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "steps": e_steps},
+                        "steps": e_steps, "copies": "pinned host buffers, second stream, double-buffered "
+                        "(inputs of step k+1 and outputs of step k overlap the next step's compute)"},
                 "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if world > 1:
