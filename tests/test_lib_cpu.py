@@ -123,3 +123,75 @@ def test_recompute_plan_shrinks_the_workspace(lib):
     g = _geom(Nz=12, ckpt_stride=3, grad_mask=_lib.PTY_GRAD_PROBE | _lib.PTY_GRAD_POS)
     g1 = _geom(Nz=12, ckpt_stride=1, grad_mask=_lib.PTY_GRAD_PROBE | _lib.PTY_GRAD_POS)
     assert lib.pty_workspace_size(ctypes.byref(g), 16) == lib.pty_workspace_size(ctypes.byref(g1), 16)
+
+
+def test_object_modes_scale_the_workspace(lib):
+    """Per-wave arrays and the object-sized transmission / gradient grow with the object modes."""
+    n1 = lib.pty_workspace_size(ctypes.byref(_geom()), 8)
+    n3 = lib.pty_workspace_size(ctypes.byref(_geom(obj_modes=3)), 8)
+    assert n3 > 2.5 * n1
+    assert lib.pty_workspace_size(ctypes.byref(_geom(obj_modes=0)), 8) == n1  # 0 means one mode
+    for bad in (-1, 65):
+        assert lib.pty_workspace_size(ctypes.byref(_geom(obj_modes=bad)), 8) == 0
+        assert b"obj_modes" in lib.pty_last_error()
+
+
+def _constraints(**kw):
+    c = _lib.pty_constraints()
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def test_constrain_workspace_size(lib):
+    g = _geom(Nz=3, H=100, W=70, M=5)
+    assert lib.pty_constrain_workspace_size(ctypes.byref(g), ctypes.byref(_constraints(rz_sigma=1.0, rz_relax=1.0))) == 0
+    kz = lib.pty_constrain_workspace_size(ctypes.byref(g), ctypes.byref(_constraints(kz_beta=1.0, kz_relax=1.0)))
+    assert kz == (8 * 3 * 100 * 70 + 255) // 256 * 256  # one complex volume
+    # beta = alpha = 0 or relaxation 0: the filter is the identity and is skipped
+    assert lib.pty_constrain_workspace_size(ctypes.byref(g), ctypes.byref(_constraints(kz_relax=1.0))) == 0
+    assert lib.pty_constrain_workspace_size(ctypes.byref(g), ctypes.byref(_constraints(kz_beta=1.0))) == 0
+    ortho = lib.pty_constrain_workspace_size(ctypes.byref(g), ctypes.byref(_constraints(probe_orthogonalize=1)))
+    assert 0 < ortho < 64 * 1024
+    assert lib.pty_constrain_workspace_size(ctypes.byref(_geom(M=1)), ctypes.byref(_constraints(probe_orthogonalize=1))) == 0
+
+
+def test_constrain_rejects_bad_arguments_before_launch(lib):
+    buf = (ctypes.c_float * 16)()
+    p = ctypes.cast(buf, ctypes.c_void_p)
+    cases = [
+        (_geom(), _constraints(phase_positivity=1.5)),
+        (_geom(), _constraints(rz_sigma=1.0, rz_relax=-0.1)),
+        (_geom(), _constraints(rz_sigma=float("nan"), rz_relax=1.0)),
+        (_geom(), _constraints(kz_beta=-1.0, kz_relax=1.0)),
+        (_geom(), _constraints(kz_beta=1.0, kz_relax=2.0)),
+        (_geom(Nz=129), _constraints(rz_sigma=1.0, rz_relax=1.0)),
+        (_geom(W=8200), _constraints(kz_beta=1.0, kz_relax=1.0)),
+        (_geom(M=33), _constraints(probe_orthogonalize=1)),
+    ]
+    for g, c in cases:
+        assert lib.pty_constrain(ctypes.byref(g), p, p, p, p, ctypes.byref(c), None, 0, None) == _lib.PTY_EINVAL
+        assert lib.pty_last_error()
+    # the k_z filter needs dz and a workspace; orthogonalisation needs the probe
+    g = _geom()
+    c = _constraints(kz_beta=1.0, kz_relax=1.0)
+    assert lib.pty_constrain(ctypes.byref(g), p, p, p, None, ctypes.byref(c), None, 0, None) == _lib.PTY_EINVAL
+    assert lib.pty_constrain(ctypes.byref(g), p, p, p, p, ctypes.byref(c), None, 0, None) == _lib.PTY_EINVAL
+    c = _constraints(probe_orthogonalize=1)
+    assert lib.pty_constrain(ctypes.byref(g), p, p, None, p, ctypes.byref(c), None, 0, None) == _lib.PTY_EINVAL
+
+
+def test_reference_arm_prints_the_contract_line():
+    """bench.py --impl reference: the oracle timed on the host, one JSON line with the contract keys."""
+    import json
+    import subprocess
+    import sys
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--workload", "c1"], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
