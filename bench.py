@@ -519,6 +519,9 @@ def main():
     ap.add_argument("--fft", default="fp32", choices=["fp32", "bf16", "fp16", "bf16x3"],
                     help="per-slice DFTs: FP32 shared-memory FFT or split-precision tensor-core GEMMs")
     ap.add_argument("--sweep-ckpt", default="", help="comma-separated strides: print one timing line per stride")
+    ap.add_argument("--eager", dest="graph", action="store_false",
+                    help="launch every step's kernels from the host instead of replaying a CUDA graph captured "
+                         "once per batch (the default)")
     ap.add_argument("--sweep-shape", action="store_true",
                     help="step time against batch size, probe modes and slices (one line per point)")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -606,6 +609,26 @@ def main():
     torch.cuda.synchronize()
     assert pt.status() == 0
 
+    def run_step(k):
+        pt.loss_grad(params, idx_t[k % 8], I_meas, grads=grads)
+
+    per_step_launches = None
+    # (the split-precision forms keep the eager path: their first call on a device builds DFT tables)
+    args.graph = args.graph and args.fft == "fp32"
+    if args.graph:  # one graph per batch of positions, captured after the warm-up
+        graphs = []
+        for k in range(min(8, args.steps)):
+            g_ = torch.cuda.CUDAGraph()
+            c0 = _lib.pty_launch_count()
+            with torch.cuda.graph(g_):
+                run_step(k)
+            per_step_launches = _lib.pty_launch_count() - c0  # the library's kernels in one step
+            graphs.append(g_)
+        torch.cuda.synchronize()
+
+        def run_step(k):  # noqa: F811
+            graphs[k % len(graphs)].replay()
+
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     _lib.pty_profile_enable(True)
@@ -617,7 +640,7 @@ def main():
         for k in range(args.steps):
             flush.zero_()
             starts[k].record()
-            pt.loss_grad(params, idx_t[k % 8], I_meas, grads=grads)
+            run_step(k)
             ends[k].record()
         torch.cuda.synchronize()
     if world > 1:
@@ -625,6 +648,17 @@ def main():
     launches = _lib.pty_launch_count() - n0
     ncalls, stage_ms = _lib.pty_profile_read()
     _lib.pty_profile_enable(False)
+    if args.graph:
+        # replays do not pass through the host launch counter or the stage events: count the
+        # captured kernels, and take the stage times from a few eager steps after the timed region
+        launches = per_step_launches * args.steps
+        _lib.pty_profile_enable(True)
+        for k in range(args.warmup):
+            flush.zero_()
+            pt.loss_grad(params, idx_t[k % 8], I_meas, grads=grads)
+        torch.cuda.synchronize()
+        ncalls, stage_ms = _lib.pty_profile_read()
+        _lib.pty_profile_enable(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     total_ms = sum(step_ms)
     if world > 1:
@@ -750,7 +784,7 @@ def main():
                            "object": [w.Nz, w.H, w.W], "loss": "poisson", "grads": "amp,phase,probe,pos,tilt,dz",
                            "batches": "contiguous raster blocks", "start": "flat object (amp 1, phase U[0,1e-8])",
                            "l2": "flushed before every step (256 MiB write outside the step events)",
-                           "parallelism": "dp%d" % world},
+                           "parallelism": "dp%d" % world, "cuda_graph": bool(args.graph)},
                 "roofline": roofline, "stage_ms_per_call": stages,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": e_steps, "copies": "pinned host buffers, second stream, double-buffered "
