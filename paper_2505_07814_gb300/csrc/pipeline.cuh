@@ -239,6 +239,13 @@ __device__ __forceinline__ float2 ld_ro(const float2* p) {
   asm("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
   return v;
 }
+__device__ __forceinline__ float4 ld_ro(const float4* p) {
+  float4 v;
+  asm("ld.global.nc.L1::no_allocate.v4.f32 {%0, %1, %2, %3}, [%4];"
+      : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+      : "l"(p));
+  return v;
+}
 __device__ __forceinline__ float ld_ro(const float* p) {
   float v;
   asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
@@ -666,11 +673,22 @@ __global__ void __launch_bounds__(T) k_loss(LossArgs a) {
   float* L = lsm;
   double* red = reinterpret_cast<double*>(lsm + N * RS + ((N * RS) & 1));
   const int b = blockIdx.x, tid = threadIdx.x;
-  const float* Im = a.Imode + (size_t)b * a.M * NN;
-  for (int e = tid; e < NN; e += T) {
-    float acc = 0.f;
-    for (int m = 0; m < a.M; ++m) acc += Im[(size_t)m * NN + e];
-    L[(e / N) * RS + e % N] = acc;
+  // mode sum, four pixels of one k-space row per thread and load (N is a multiple of 4)
+  const float4* Im4 = reinterpret_cast<const float4*>(a.Imode + (size_t)b * a.M * NN);
+  for (int e4 = tid; e4 < NN / 4; e4 += T) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int m = 0; m < a.M; ++m) {
+      const float4 v = ld_ro(Im4 + (size_t)m * (NN / 4) + e4);
+      acc.x += v.x;
+      acc.y += v.y;
+      acc.z += v.z;
+      acc.w += v.w;
+    }
+    float* row = L + (4 * e4 / N) * RS + (4 * e4) % N;
+    row[0] = acc.x;
+    row[1] = acc.y;
+    row[2] = acc.z;
+    row[3] = acc.w;
   }
   __syncthreads();
   const float* Id = a.I_meas ? a.I_meas + (size_t)checked_index(a.idx, b, a.Ntot, a.status) * NN : nullptr;
