@@ -620,7 +620,8 @@ def main():
         for k in range(min(8, args.steps)):
             g_ = torch.cuda.CUDAGraph()
             c0 = _lib.pty_launch_count()
-            with torch.cuda.graph(g_):
+            # thread-local capture: other threads (NCCL's, under torchrun) may use CUDA meanwhile
+            with torch.cuda.graph(g_, capture_error_mode="thread_local"):
                 run_step(k)
             per_step_launches = _lib.pty_launch_count() - c0  # the library's kernels in one step
             graphs.append(g_)
