@@ -201,6 +201,41 @@ def cpu_oracle_sample(w, amp0, phase0, I_meas, idx_all, seconds):
     return P, dt
 
 
+_ORACLE_WORKER = None
+
+
+def _oracle_worker_init(workload, positions):
+    """Pool initialiser: one single-threaded oracle per process, on the same inputs as the parent."""
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[v] = "1"
+    global _ORACLE_WORKER
+    from oracle import ptycho as O
+    w, amp0, phase0, I_rows, row_of = make_inputs(workload, positions)
+    geom = O.Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, dx=w.dx, lam=w.lam)
+    _ORACLE_WORKER = (O, geom, w, amp0, phase0, _Rows(I_rows, row_of))
+
+
+def _oracle_worker(j):
+    O, geom, w, amp0, phase0, rows = _ORACLE_WORKER
+    O.loss_and_grad(geom, amp0, phase0, w.probe, w.pos, w.tilt, w.dz, rows, [j])
+    return j
+
+
+def cpu_oracle_all_cores(workload, idx, seconds_per_position, seconds):
+    """The same oracle on every host core: a spawn-started pool (no fork of a CUDA process), one
+    position per task, over a bounded sample of the batch.  Returns (positions, wall seconds, cores)."""
+    import multiprocessing as mp
+    procs = os.cpu_count() or 1
+    P = max(procs, min(len(idx), int(procs * seconds / max(seconds_per_position, 1e-3))))
+    sample = list(idx[:P])
+    with mp.get_context("spawn").Pool(procs, initializer=_oracle_worker_init, initargs=(workload, sample)) as pool:
+        pool.map(_oracle_worker, sample[:procs], chunksize=1)  # every worker initialised and warm
+        t0 = time.perf_counter()
+        pool.map(_oracle_worker, sample, chunksize=1)
+        dt = time.perf_counter() - t0
+    return len(sample), dt, procs
+
+
 def _ntot(workload):
     return {"c1": 256, "c2": 4096, "c3": 16384, "paper": 16384}[workload]
 
@@ -771,6 +806,13 @@ def main():
         cpu = {"value": P * w.M * w.Nz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "FP64 numpy oracle, loss + all gradients for the first %d positions of one %d-position "
                          "batch (%d updates, %.1f s, single-threaded pocketfft)" % (P, B, P * w.M * w.Nz, dt)}
+        try:  # the same oracle on every host core (context; the single-core figure above is the baseline)
+            Pa, dta, procs = cpu_oracle_all_cores(args.workload, idx_h[0], dt / P, args.cpu_seconds / 3)
+            cpu["all_cores"] = {"value": Pa * w.M * w.Nz / dta, "cores": procs,
+                                "sample": "%d positions of the same batch, one per task, %d spawn-started processes, "
+                                          "%.1f s" % (Pa, procs, dta)}
+        except Exception as e:  # a host without process pools still gets its single-core line
+            cpu["all_cores"] = {"unavailable": str(e)[:200]}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
