@@ -1,7 +1,7 @@
 """Build the in-tree CUDA library libpty.so for sm_103a with nvcc (no CMake, no torch extension).
 
 Each translation unit is compiled in parallel, then linked into one shared object next to this
-file.  `python -m paper_2505_07814_gb300.build` or `__graft_entry__.build()` runs it.
+file.  `python -m paper_2505_07814_gb300.build` runs it, as does the repository's build entry point.
 """
 from __future__ import annotations
 
