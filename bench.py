@@ -403,8 +403,7 @@ def run_nmse(args):
     train_s = ev0.elapsed_time(ev1) / 1e3
     del I, Y
     # inference in batches of 1024 patterns (the kernels' largest batch; 14% more patterns/s than 256)
-    net_inf = Cnn(S=128, max_batch=1024)
-    net_inf.params.copy_(net.params)
+    net_inf = Cnn(S=128, max_batch=1024, params=net.params)
     L.initial_object(net_inf, prob, batch=1024)  # warm-up
     ev0.record()
     amp_c, ph_c = L.initial_object(net_inf, prob, batch=1024)
