@@ -157,3 +157,14 @@ def test_orthogonalize_fixed_points():
     np.testing.assert_allclose(lam, [4.0, 2.0, 0.25])
     one = _modes(1, 5, 8)
     np.testing.assert_allclose(K.orthogonalize_probe(one)[0], one, rtol=1e-15)
+
+
+def test_orthogonalize_phase_convention():
+    """Each new mode is sum_m c_km P_m with the largest |c_km| real and positive (reading C5)."""
+    P = _modes(4, 6, 9)
+    Q, _ = K.orthogonalize_probe(P)
+    A, B = P.reshape(4, -1), Q.reshape(4, -1)
+    C = B @ np.linalg.pinv(A)  # B = C A, C = U^H
+    for k in range(4):
+        m = int(np.argmax(np.abs(C[k])))
+        assert abs(C[k, m].imag) <= 1e-12 * abs(C[k, m]) and C[k, m].real > 0
