@@ -68,6 +68,54 @@ __device__ __forceinline__ float2 twmul(int k, float2 z) {
   return make_float2(fmaf(z.x, c, z.y * s), fmaf(z.y, c, -z.x * s));
 }
 
+// tan(2 pi e / 32) for e = 0..4.
+__device__ __forceinline__ constexpr float tan32(int e) {
+  return e == 0 ? 0.0f
+       : e == 1 ? 0.19891236737965800607f
+       : e == 2 ? 0.41421356237309503445f
+       : e == 3 ? 0.66817863791929887896f
+                : 1.0f;
+}
+
+// Radix-2 butterfly a <- a + z, b <- a - z with z = W_R^k b, in six fused multiply-adds for any
+// rotation but 0 and -i (which cost four adds).  W = c - i s (c + i s for INV) is written as
+// f (1 - i r) with |r| <= 1: f = c, r = s / c where |s| <= |c|, else f = s, r = c / s applied to
+// the swapped components (the tangent-factored butterfly of Linzer and Feig, "Implementation of
+// efficient FFT algorithms on fused multiply-add architectures", IEEE Trans. Signal Processing
+// 41(1), 1993).  z / f then takes two FMAs, and a +- f (z / f) four; the plain product z = W b
+// followed by the sum and difference takes eight instructions.
+template <int R, bool INV>
+__device__ __forceinline__ void bfly(int k, float2& a, float2& b) {
+  const int e = k * (32 / R);  // angle in units of 2 pi / 32, 0 <= e < 16
+  const float2 x = a;
+  if (e == 0 || e == 8) {
+    const float2 z = e == 0 ? b : (INV ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x));
+    a = cadd(x, z);
+    b = csub(x, z);
+    return;
+  }
+  const int ea = e < 8 ? e : 16 - e;  // |c| = cos(2 pi ea / 32), |s| = sin(2 pi ea / 32)
+  const float sc = e < 8 ? 1.0f : -1.0f, ss = INV ? -1.0f : 1.0f;  // signs of c and s
+  float f;
+  float2 u;  // z / f
+  if (ea <= 4) {  // z = c (b.x + r b.y, b.y - r b.x), r = s / c
+    const float r = sc * ss * tan32(ea);
+    f = sc * cos32(ea);
+    u = make_float2(fmaf(r, b.y, b.x), fmaf(-r, b.x, b.y));
+  } else {  // z = s (q b.x + b.y, q b.y - b.x), q = c / s
+    const float q = sc * ss * tan32(8 - ea);
+    f = ss * cos32(8 - ea);
+    u = make_float2(fmaf(q, b.x, b.y), fmaf(q, b.y, -b.x));
+  }
+  a = make_float2(fmaf(f, u.x, x.x), fmaf(f, u.y, x.y));
+  b = make_float2(fmaf(-f, u.x, x.x), fmaf(-f, u.y, x.y));
+}
+
+// 1: the DFTs combine with bfly (six FMAs per rotated butterfly); 0: product then sum (eight)
+#ifndef PTY_DFT_FMA
+#define PTY_DFT_FMA 1
+#endif
+
 // In-register R-point DFT (R = 2 ... 32), natural order in and out, radix-2 decimation in time.
 template <int R, bool INV>
 __device__ __forceinline__ void dft(float2* x) {
@@ -88,9 +136,15 @@ __device__ __forceinline__ void dft(float2* x) {
     dft<R / 2, INV>(o);
 #pragma unroll
     for (int k = 0; k < R / 2; ++k) {
+#if PTY_DFT_FMA
+      bfly<R, INV>(k, e[k], o[k]);
+      x[k] = e[k];
+      x[k + R / 2] = o[k];
+#else
       const float2 t = twmul<R, INV>(k, o[k]);
       x[k] = cadd(e[k], t);
       x[k + R / 2] = csub(e[k], t);
+#endif
     }
   }
 }
