@@ -232,6 +232,38 @@ __host__ __device__ constexpr size_t fwd_smem_bytes() {
   return sizeof(float2) * ((size_t)wave_rows<N>() * (N + 1) + 5 * N);
 }
 
+// Bulk-copy staging of the forward's transmission patch (N = 128, fused column step, even object
+// width): rows 0..N/2-1 of the next slice's patch are copied into shared memory after the wave and
+// its tables while the current slice's last three transform steps run, one copy per row by the
+// lanes of warp 0.  A row copy starts at the 16-byte boundary at or left of the patch corner: N
+// elements, or N + 2 from the column before an odd corner (with W and N even, an odd corner lies
+// at most at W - N - 1, so the copy stays inside the row).  Stage rows have a pitch of N + 2.
+#ifndef PTY_FWD_STAGE
+#define PTY_FWD_STAGE 0
+#endif
+template <int N>
+__host__ __device__ constexpr bool fwd_staged() {
+  return PTY_FWD_STAGE && N == 128 && !PTY_FWD_SPLIT_COL;
+}
+template <int N>
+__host__ __device__ constexpr size_t fwd_stage_offset() {
+  return (fwd_smem_bytes<N>() + 127) / 128 * 128;
+}
+template <int N>
+__host__ __device__ constexpr size_t fwd_stage_bytes() {
+  return (size_t)(N / 2) * (N + 2) * sizeof(float2);
+}
+// Dynamic shared memory of k_forward (k_recompute takes fwd_smem_bytes).
+template <int N>
+__host__ __device__ constexpr size_t fwd_kernel_smem_bytes() {
+  return fwd_staged<N>() ? fwd_stage_offset<N>() + fwd_stage_bytes<N>() + 16 : fwd_smem_bytes<N>();
+}
+template <int N>
+__device__ __forceinline__ float2* fwd_stage() {
+  extern __shared__ __align__(16) float2 sm[];
+  return reinterpret_cast<float2*>(reinterpret_cast<char*>(sm) + fwd_stage_offset<N>());
+}
+
 // Loads of data written by earlier kernels and read-only here (checkpoints, spectra, transmission):
 // non-coherent and not volatile, so the compiler may batch them ahead of this thread's atomics.
 __device__ __forceinline__ float2 ld_ro(const float2* p) {
@@ -277,6 +309,49 @@ template <int N>
 __device__ __forceinline__ void prefetch_block(const float2* base) {
   constexpr size_t chunk = sizeof(float2) * N * N / 8;
   if (threadIdx.x < 8) prefetch_l2(reinterpret_cast<const char*>(base) + threadIdx.x * chunk, chunk);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+// L2 policy for data read once: evict first.
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+// Arrive on the mbarrier `bar` and add `bytes` to the transaction count its phase waits for.
+__device__ __forceinline__ void stage_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+// Copy `bytes` (a multiple of 16, both addresses 16-byte aligned) from global to shared memory,
+// completing on `bar`.  Earlier generic-proxy accesses of dst by this thread (and, through a
+// barrier, by the CTA) are ordered before the copy by the proxy fence.
+__device__ __forceinline__ void stage_copy(uint32_t bar, void* dst, const void* src, uint32_t bytes, uint64_t pol) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(bar), "l"(pol)
+      : "memory");
+}
+// One thread: one copy of `bytes` that alone completes the barrier's current phase.
+__device__ __forceinline__ void stage_issue(uint32_t bar, void* dst, const void* src, uint32_t bytes) {
+  const uint64_t pol = evict_first_policy();
+  stage_expect(bar, bytes);
+  stage_copy(bar, dst, src, bytes, pol);
+}
+constexpr long kStageSpin = 1L << 24;  // non-blocking polls before a stage wait gives up (well under a second)
+// Bounded wait for phase `parity` of `bar`; false on timeout.
+__device__ __forceinline__ bool stage_wait(uint32_t bar, uint32_t parity) {
+  for (long i = 0; i < kStageSpin; ++i) {
+    uint32_t ok;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.b32 %0, 1, 0, p;\n}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
 }
 
 // Per-wave tables, written by the first N threads (axis-0 tables indexed by k-space row p0, axis-1
@@ -352,12 +427,17 @@ struct TransLoad {
   static constexpr int kChunk = PTY_KT;
   const float2* Ts;  // patch corner in T
   int W;
-  float2* ck;  // checkpoint block or nullptr
+  float2* ck;    // checkpoint block or nullptr
+  int odd = -1;  // >= 0: rows 0..N/2-1 of the patch are staged (fwd_stage), column c at c + odd
   template <int K>
   __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     float2 t[K];
+    const bool staged = odd >= 0 && r0 + (K - 1) * rs < N / 2;
+    const float2* st = fwd_stage<N>();
 #pragma unroll
-    for (int k = 0; k < K; ++k) t[k] = ld_ro(Ts + (size_t)(r0 + k * rs) * W + c0 + k * cs);
+    for (int k = 0; k < K; ++k)
+      t[k] = staged ? st[(r0 + k * rs) * (N + 2) + c0 + k * cs + odd]
+                    : ld_ro(Ts + (size_t)(r0 + k * rs) * W + c0 + k * cs);
     if (ck) {
 #pragma unroll
       for (int k = 0; k < K; ++k) __stcs(ck + (r0 + k * rs) * N + c0 + k * cs, v[k]);
@@ -433,6 +513,37 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   prefetch_patch<N>(Tpatch, a.W);
 #endif
 
+  // Staging (fwd_staged): copy k holds slice k's rows, so the k-th wait is on phase parity k & 1;
+  // copy k + 1 is issued after the column step that read copy k.  A wait that gives up flags
+  // PTY_ETIMEOUT; that thread then reads global memory and tests the barrier no more, and warp 0
+  // stops issuing once its lane 0 gave up.
+  constexpr bool kStage = fwd_staged<N>() && F::C == 1;
+  const bool staged = kStage && (a.W % 2) == 0;
+  const int odd = i1 & 1;
+  float2* stg = fwd_stage<N>();
+  const uint32_t sbar = smem_u32(stg + (N / 2) * (N + 2));
+  uint32_t sst = 0;  // bit 0: parity of the next wait; bit 31: a wait of this thread gave up
+  auto stage_rows = [&](int sl) {  // warp 0: rows 0..N/2-1 of slice sl's patch
+    if (tid < 32 && !(__shfl_sync(0xffffffffu, sst, 0) >> 31)) {
+      const uint32_t row_bytes = (uint32_t)((N + 2 * odd) * sizeof(float2));
+      const uint64_t pol = evict_first_policy();
+      if (tid == 0) stage_expect(sbar, (N / 2) * row_bytes);
+      __syncwarp();
+      for (int r = tid; r < N / 2; r += 32)
+        stage_copy(sbar, stg + r * (N + 2), Tpatch + sl * plane + (size_t)r * a.W - odd, row_bytes, pol);
+    }
+  };
+  if constexpr (kStage) {
+    if (staged) {
+      if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      }
+      if (tid < 32) __syncwarp();
+      stage_rows(0);
+    }
+  }
+
   build_twiddles<N>(tw);
   fwd_tables<N>(ra0, ra1, pm0, pm1, d0, d1, th0, th1, dz, a.dx, a.lam);
   __syncthreads();
@@ -455,7 +566,21 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
     F::template pointwise<PTY_ADJ_BATCH>(s, trans);
     F::col_fwd(s, tw, none);
 #else
+    if constexpr (kStage) {
+      if (staged && !(sst >> 31)) {
+        if (stage_wait(sbar, sst & 1)) {
+          sst ^= 1;
+          trans.odd = odd;
+        } else {
+          sst |= 0x80000000u;
+          atomicOr(a.status, PTY_ETIMEOUT);
+        }
+      }
+    }
     F::template col_inv_fwd<true>(s, tw, trans);
+    if constexpr (kStage) {  // every thread is past the stage: fetch the next slice's rows
+      if (staged && sl + 1 < a.Nz) stage_rows(sl + 1);
+    }
 #endif
     F::block_fwd(s, tw);
     if (sl + 1 < a.Nz) {
@@ -473,6 +598,9 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
       FarStore<N> far{a.Psi ? a.Psi + (size_t)bm * NN : nullptr, a.Imode + (size_t)bm * NN};
       F::template row_fwd<false>(s, far);
     }
+  }
+  if constexpr (kStage) {  // a copy whose wait gave up may still be in flight: give it time to land
+    if (staged && tid == 0 && (sst >> 31)) stage_wait(sbar, sst & 1);
   }
 }
 
@@ -892,11 +1020,41 @@ struct AdjArgs {
   float2* gstate;
 };
 
+// Bulk-copy staging of the adjoint's once-read blocks (N = 128, split transmission and propagation
+// passes).  The checkpoint a slice's transmission pass reads and the spectrum its propagation pass
+// reads are contiguous 128 KB blocks; the first half of each (natural rows 0..63, k-space columns
+// 0..63: the first two load batches of those passes) is copied by one thread with cp.async.bulk into
+// the 64 KB of shared memory the wave leaves free, three transform steps before it is read.  The
+// other half is read from global memory as before.
+#ifndef PTY_ADJ_STAGE
+#define PTY_ADJ_STAGE 0
+#endif
+template <int N, int T>
+__host__ __device__ constexpr bool adj_staged() {
+  return PTY_ADJ_STAGE && N == 128 && PTY_ADJ_SPLIT_COL && PTY_ADJ_SPLIT_ROW;
+}
+constexpr int kStageBytes = 64 * 1024;
+// Byte offset of the stage in the adjoint's shared memory: after the wave, the tables and the
+// reduction slots of up to 1024 threads, so that it does not depend on the CTA size.
+template <int N>
+__host__ __device__ constexpr size_t adj_stage_offset() {
+  return (sizeof(float2) * ((size_t)wave_rows<N>() * (N + 1) + 5 * N) + sizeof(float) * 6 * N +
+          sizeof(double) * 5 * 32 + 127) / 128 * 128;
+}
 template <int N, int T>
 __host__ __device__ constexpr size_t adj_smem_bytes() {
-  return sizeof(float2) * ((size_t)wave_rows<N>() * (N + 1) + 5 * N) + sizeof(float) * 6 * N +
-         sizeof(double) * 5 * (T / 32);
+  static_assert(T <= 1024, "reduction slots");
+  return adj_staged<N, T>() ? adj_stage_offset<N>() + kStageBytes + 16
+                            : sizeof(float2) * ((size_t)wave_rows<N>() * (N + 1) + 5 * N) + sizeof(float) * 6 * N +
+                                  sizeof(double) * 5 * (T / 32);
 }
+// The stage in the calling kernel's dynamic shared memory.
+template <int N>
+__device__ __forceinline__ float2* adj_stage() {
+  extern __shared__ __align__(16) float2 sm[];
+  return reinterpret_cast<float2*>(reinterpret_cast<char*>(sm) + adj_stage_offset<N>());
+}
+
 
 // ---- adjoint hooks ----
 // g_psi at the far field = F_ortho^-1[2 dL/dI Psi]: forms 2 dL/dI Psi / N (k-space), replaces
@@ -930,14 +1088,17 @@ struct AdjTransLoad {
   float2* gTs;       // patch corner in the dL/dT accumulator
   const float2* ck;  // checkpoint of the wave entering slice s, or nullptr (no object gradient)
   int W;
+  bool stg = false;  // rows 0..N/2-1 of ck are in the stage (adj_stage)
   template <int K>
   __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     float2 t[K], ps[K];
+    const bool staged = stg && r0 + (K - 1) * rs < N / 2;
+    const float2* st = adj_stage<N>();
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int r = r0 + k * rs, c = c0 + k * cs;
       t[k] = ld_ro(Ts + (size_t)r * W + c);
-      if (ck) ps[k] = ld_once(ck + r * N + c);
+      if (ck) ps[k] = staged ? st[r * N + c] : ld_once(ck + r * N + c);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -956,12 +1117,18 @@ struct AdjPropStore {
   const float2* vh;  // stored v^/N^2 of this propagation, or nullptr
   const float *e0, *e1, *c0t, *c1t;
   float &dz, &t0, &t1;
+  bool stg = false;  // k-space columns 0..N/2-1 of vh (its first half) are in the stage (adj_stage)
   template <int K>
   __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     if (vh) {
       float2 x[K];
+      const bool staged = stg && c0 + (K - 1) * cs < N / 2;
+      const float2* st = adj_stage<N>();
 #pragma unroll
-      for (int k = 0; k < K; ++k) x[k] = ld_once(vh + kidx<N>(r0 + k * rs, c0 + k * cs));
+      for (int k = 0; k < K; ++k) {
+        const int e = kidx<N>(r0 + k * rs, c0 + k * cs);
+        x[k] = staged ? st[e] : ld_once(vh + e);
+      }
 #pragma unroll
       for (int k = 0; k < K; ++k) {
         const int r = r0 + k * rs, c = c0 + k * cs;
@@ -1053,6 +1220,36 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   if (want_prop && a.s1 - 1 > a.s0 - 1 && a.s1 >= 2) prefetch_block<N>(vh_base + (size_t)(a.s1 - 2) * NN);
 #endif
 
+  // Staging (adj_staged): copies alternate checkpoint (slice sl, issued after the previous slice's
+  // propagation pass) and spectrum (issued after the transmission pass); every thread waits on each
+  // copy once, in issue order, so the k-th wait is on phase parity k & 1, and copy k + 1 is issued
+  // only after every thread has passed wait k.  A wait that gives up flags PTY_ETIMEOUT; from then
+  // on that thread reads global memory and never tests the barrier again (a later parity test
+  // could match an earlier phase), and thread 0 stops issuing.
+  constexpr bool kStage = adj_staged<N, T>();
+  float2* stg = adj_stage<N>();
+  const uint32_t sbar = smem_u32(stg + kStageBytes / sizeof(float2));
+  // bit 0: parity of the next wait; bit 31: one of this thread's waits gave up (bit 0 then holds
+  // the parity of that wait)
+  uint32_t sst = 0;
+  auto stage_get = [&]() -> bool {  // wait for the next copy; false if it is not there
+    if (sst >> 31) return false;
+    if (stage_wait(sbar, sst & 1)) {
+      sst ^= 1;
+      return true;
+    }
+    sst |= 0x80000000u;
+    atomicOr(a.status, PTY_ETIMEOUT);
+    return false;
+  };
+  if constexpr (kStage) {
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbar) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      if (want_obj) stage_issue(sbar, stg, ck_base + (size_t)(a.s1 - 1) * NN, kStageBytes);
+    }
+  }
+
   build_twiddles<N>(tw);
   adj_tables<N>(cm0, cm1, cr0, cr1, e0, e1, c0, c1, f0, f1, d0, d1, th0, th1, dz, a.dx, a.lam);
   __syncthreads();
@@ -1087,7 +1284,14 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
       // the column forward: one more shared-memory round trip, but no DFT registers are live
       // while the checkpoint and transmission loads are in flight
       F::col_inv(s, tw);
+      if constexpr (kStage) {
+        if (want_obj) trans.stg = stage_get();
+      }
       F::template pointwise<PTY_ADJ_BATCH>(s, trans);
+      if constexpr (kStage) {  // the stage is free again: fetch this slice's spectrum
+        if (tid == 0 && !(sst >> 31) && want_prop && sl > 0)
+          stage_issue(sbar, stg, vh_base + (size_t)(sl - 1) * NN, kStageBytes);
+      }
       F::col_fwd(s, tw, none);
 #else
       F::template col_inv_fwd<true>(s, tw, trans);
@@ -1101,7 +1305,14 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
                              gdz, gt0, gt1};
 #if PTY_ADJ_SPLIT_ROW
         F::template row_fwd<true>(s, none);
+        if constexpr (kStage) {
+          if (want_prop) prop.stg = stage_get();
+        }
         F::template pointwise_k<PTY_ADJ_BATCH>(s, prop);
+        if constexpr (kStage) {  // the stage is free again: fetch the next slice's checkpoint
+          if (tid == 0 && !(sst >> 31) && want_obj && sl - 1 >= a.s0)
+            stage_issue(sbar, stg, ck_base + (size_t)(sl - 1) * NN, kStageBytes);
+        }
         F::row_inv(s, tw, none);
 #else
         F::row_fwd_inv(s, tw, prop);
@@ -1113,8 +1324,12 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
         F::template row_fwd<false>(s, probe);
       }
     } else if (want_obj) {
+      if constexpr (kStage) trans.stg = stage_get();
       F::template col_inv_fwd<false>(s, tw, trans);
     }
+  }
+  if constexpr (kStage) {  // a copy whose wait gave up may still be in flight: give it time to land
+    if (tid == 0 && (sst >> 31)) stage_wait(sbar, sst & 1);
   }
 
   // FP64 reduction of the five scalar partials over the CTA
@@ -1406,7 +1621,7 @@ struct Pass {
 
   int set_attributes() {
     bool ok = cudaFuncSetAttribute(fwd_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)fwd_smem_bytes<N>()) == cudaSuccess &&
+                                   (int)fwd_kernel_smem_bytes<N>()) == cudaSuccess &&
               cudaFuncSetAttribute(recompute_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)fwd_smem_bytes<N>()) == cudaSuccess &&
               cudaFuncSetAttribute(adj_kernel(), cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1534,7 +1749,7 @@ struct Pass {
   int forward(const float* I_meas) {
     int rc = forward_begin();
     if (rc || pb.B == 0) return rc;
-    PTY_LAUNCH_RC(launch_waves<C>(fwd_kernel(), pb.B * pb.M * pb.Ko, TF, fwd_smem_bytes<N>(), st, fwd_args_saved()),
+    PTY_LAUNCH_RC(launch_waves<C>(fwd_kernel(), pb.B * pb.M * pb.Ko, TF, fwd_kernel_smem_bytes<N>(), st, fwd_args_saved()),
                   "k_forward", 2);
     return loss_phase(I_meas);
   }
