@@ -173,6 +173,9 @@ def test_large_window_subset_matches_oracle_and_differences():
             for part in parts:
                 entries.append((name, np.unravel_index(int(e), gv.shape), part, h))
     assert len(entries) == 32
+    # The round-off floor of a central difference is set by the loss and h, so it is the same for
+    # the real and imaginary part of a probe entry: the tolerance scales with the entry's modulus
+    # (entries are drawn by modulus; one part alone can be far smaller than the floor allows).
     bad = []
     for name, e, part, h in entries:
         dlt = torch.zeros_like(getattr(params, name))
@@ -181,6 +184,6 @@ def test_large_window_subset_matches_oracle_and_differences():
               _loss_at(pt, _shifted(params, name, -dlt), idx, Im, g)) / (2 * h)
         gv = _np(getattr(grads, name))[e]
         an = float(np.real(gv)) if part == 1.0 else float(np.imag(gv))
-        if abs(fd - an) > 2e-2 * abs(an) + 1e-9:
-            bad.append((name, e, part, fd, an))
+        if abs(fd - an) > 2e-2 * abs(gv) + 1e-9:
+            bad.append((name, e, part, fd, an, float(abs(gv))))
     assert not bad, bad

@@ -151,9 +151,12 @@ def test_patch_outside_object_sets_status_and_stays_in_bounds():
     assert pt.status() == 0
 
 
-def test_gradient_mask_subsets():
-    """Only the requested gradients are computed; the others are untouched (may be absent)."""
-    case = make_case(N=64, M=2, Nz=3, scan=(2, 2), seed=8)
+@pytest.mark.parametrize("N", [64, 128])
+def test_gradient_mask_subsets(N):
+    """Only the requested gradients are computed; the others are untouched (may be absent).  At
+    N = 128 the mask also decides which once-read blocks the adjoint bulk-copies into shared memory
+    (checkpoints for the object gradient, spectra for dz / tilt, none for probe and positions)."""
+    case = make_case(N=N, M=2, Nz=3, scan=(2, 2), seed=8)
     idx = [0, 1, 2, 3]
     ref = oracle_grads(case, idx)
     for names in (("phase",), ("probe", "pos"), ("tilt", "dz"), ("amp", "dz")):
@@ -163,6 +166,8 @@ def test_gradient_mask_subsets():
             t.fill_(3.0)
         grads.probe.fill_(3.0)
         loss, grads = pt.loss_grad(params, idx, I_meas, grads=grads)
+        torch.cuda.synchronize()
+        assert pt.status() == 0, names
         for name in ("amp", "phase", "probe", "pos", "tilt", "dz"):
             got = _np(getattr(grads, name))
             if name in names:
