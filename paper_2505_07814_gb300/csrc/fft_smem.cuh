@@ -192,6 +192,12 @@ struct NoHook {
   __device__ __forceinline__ void operator()(int, int, int, int, float2*) {}
 };
 
+// 1: steps whose inter-step twiddles are all W^0 (digit n2 = 0 in the column steps, k1 = 0 in the
+// row steps, warp-uniform for N >= 64) skip the multiplication (exact: it multiplies by 1)
+#ifndef PTY_TW_SKIP
+#define PTY_TW_SKIP 1
+#endif
+
 template <int N, int T>
 struct Fft2 {
   static constexpr int A = N / 4, RS = N + 1;
@@ -228,8 +234,10 @@ struct Fft2 {
       }
       hook(lh, n2, 4, c, 0, v);
       dft<A, false>(v);
+      if (!PTY_TW_SKIP || n2 != 0) {
 #pragma unroll
-      for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
+        for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
+      }
 #pragma unroll
       for (int k1 = 0; k1 < A; ++k1) s[(4 * k1 + n2) * RS + c] = v[k1];
     }
@@ -300,8 +308,10 @@ struct Fft2 {
       }
       hook(lh, r, 0, A * k1, 1, v);
       dft<A, true>(v);
+      if (!PTY_TW_SKIP || k1 != 0) {
 #pragma unroll
-      for (int n2 = 1; n2 < A; ++n2) v[n2] = cmulc(tw[n2 * k1], v[n2]);
+        for (int n2 = 1; n2 < A; ++n2) v[n2] = cmulc(tw[n2 * k1], v[n2]);
+      }
 #pragma unroll
       for (int n2 = 0; n2 < A; ++n2) s[r * RS + A * k1 + n2] = v[n2];
     }
@@ -341,8 +351,10 @@ struct Fft2 {
       float2 v[A];
 #pragma unroll
       for (int k1 = 0; k1 < A; ++k1) v[k1] = s[(4 * k1 + n2) * RS + c];
+      if (!PTY_TW_SKIP || n2 != 0) {
 #pragma unroll
-      for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(tw[n2 * k1], v[k1]);
+        for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(tw[n2 * k1], v[k1]);
+      }
       dft<A, true>(v);
 #pragma unroll
       for (int n1 = 0; n1 < A; ++n1) s[(4 * n1 + n2) * RS + c] = v[n1];
@@ -362,14 +374,18 @@ struct Fft2 {
       float2 v[A];
 #pragma unroll
       for (int k1 = 0; k1 < A; ++k1) v[k1] = s[(4 * k1 + n2) * RS + c];
+      if (!PTY_TW_SKIP || n2 != 0) {
 #pragma unroll
-      for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(tw[n2 * k1], v[k1]);
+        for (int k1 = 1; k1 < A; ++k1) v[k1] = cmulc(tw[n2 * k1], v[k1]);
+      }
       dft<A, true>(v);
       hook(h, n2, 4, c, 0, v);
       if (FWD) {
         dft<A, false>(v);
+        if (!PTY_TW_SKIP || n2 != 0) {
 #pragma unroll
-        for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
+          for (int k1 = 1; k1 < A; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
+        }
 #pragma unroll
         for (int k1 = 0; k1 < A; ++k1) s[(4 * k1 + n2) * RS + c] = v[k1];
       }
@@ -389,8 +405,10 @@ struct Fft2 {
       dft<A, false>(v);
       hook(h, r, 0, A * k1, 1, v);
       dft<A, true>(v);
+      if (!PTY_TW_SKIP || k1 != 0) {
 #pragma unroll
-      for (int n2 = 1; n2 < A; ++n2) v[n2] = cmulc(tw[n2 * k1], v[n2]);
+        for (int n2 = 1; n2 < A; ++n2) v[n2] = cmulc(tw[n2 * k1], v[n2]);
+      }
 #pragma unroll
       for (int n2 = 0; n2 < A; ++n2) s[r * RS + A * k1 + n2] = v[n2];
     }

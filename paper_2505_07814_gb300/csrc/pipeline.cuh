@@ -39,6 +39,11 @@
 #ifndef PTY_FWD_SPLIT_COL
 #define PTY_FWD_SPLIT_COL 0
 #endif
+// 1: the N = 128 forward and adjoint ask for the smallest shared-memory carve-out that holds their
+// CTA (cudaFuncAttributePreferredSharedMemoryCarveout), leaving the rest of the SM's memory as L1
+#ifndef PTY_CARVEOUT
+#define PTY_CARVEOUT 1
+#endif
 // Adjoint L2 prefetch plan (cp.async.bulk.prefetch.L2 of whole 128 KB blocks).  0: at the start of
 // slice s, the checkpoint of slice s - 1 and the spectrum of the next slice's propagation.  1: at
 // the start of slice s the spectrum its own propagation reads, after its transmission step the
@@ -1636,6 +1641,22 @@ struct Pass {
       ok = ok && cudaFuncSetAttribute(k_loss<N, T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)loss_smem_bytes<N>()) == cudaSuccess;
     }
+#if PTY_CARVEOUT
+    // One N = 128 wave kernel CTA per SM: ask for the smallest shared-memory carve-out that holds it,
+    // so the rest of the SM's on-chip memory serves as L1 for the loads in flight.
+    if constexpr (N == 128) {
+      int dev = 0, smem_sm = 0;
+      ok = ok && cudaGetDevice(&dev) == cudaSuccess &&
+           cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+           smem_sm > 0;
+      auto pct = [&](size_t bytes) { return (int)((100 * (bytes + 1024) + smem_sm - 1) / (size_t)smem_sm); };
+      ok = ok &&
+           cudaFuncSetAttribute(fwd_kernel(), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                pct(fwd_kernel_smem_bytes<N>())) == cudaSuccess &&
+           cudaFuncSetAttribute(adj_kernel(), cudaFuncAttributePreferredSharedMemoryCarveout,
+                                pct(adj_smem_bytes<N, TA>())) == cudaSuccess;
+    }
+#endif
     if (!ok) {
       set_error("cudaFuncSetAttribute failed: %s", cudaGetErrorString(cudaGetLastError()));
       return PTY_ECUDA;
