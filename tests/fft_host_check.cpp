@@ -1,0 +1,119 @@
+// The shared-memory 2D FFT steps of fft_smem.cuh, compiled for the host and run one emulated
+// thread at a time (every thread finishes a step before any starts the next, as the barriers
+// after each step guarantee on the GPU), against a direct double-precision DFT.
+//
+// Prints one line per case: N, threads, and the relative L2 errors of
+//   fwd   the forward transform, read through the k-space digit layout (kbin0 / kbin1);
+//   inv   the inverse of that spectrum back to N^2 times the input;
+//   fused the fused steps (inverse end + forward start, forward end + inverse start) in a
+//         forward-then-inverse and an inverse-then-forward chain.
+#include <complex>
+#include <cstdio>
+#include <random>
+#include <vector>
+
+#include "fft_smem.cuh"
+
+using cd = std::complex<double>;
+
+template <class F>
+static void each_thread(int T, F&& f) {
+  for (int t = 0; t < T; ++t) {
+    threadIdx.x = t;
+    f();
+  }
+}
+
+static double rel(const std::vector<cd>& a, const std::vector<cd>& b) {
+  double n = 0, d = 0;
+  for (size_t i = 0; i < a.size(); ++i) {
+    n += std::norm(a[i] - b[i]);
+    d += std::norm(b[i]);
+  }
+  return std::sqrt(n / d);
+}
+
+template <int N, int T>
+static void run(unsigned seed) {
+  using F = pty::Fft2<N, T>;
+  constexpr int RS = F::RS;
+  std::vector<float2> s(N * RS), tw(N);
+  each_thread(T, [&] { pty::build_twiddles<N>(tw.data()); });
+  std::mt19937 g(seed);
+  std::normal_distribution<float> nd;
+  std::vector<cd> x(N * N);
+  for (int r = 0; r < N; ++r)
+    for (int c = 0; c < N; ++c) {
+      const float2 v = make_float2(nd(g), nd(g));
+      s[r * RS + c] = v;
+      x[r * N + c] = cd(v.x, v.y);
+    }
+  // direct DFT (separable, sign -1, unnormalised)
+  std::vector<cd> tmp(N * N), X(N * N);
+  for (int r = 0; r < N; ++r)
+    for (int k = 0; k < N; ++k) {
+      cd a = 0;
+      for (int c = 0; c < N; ++c) a += x[r * N + c] * std::polar(1.0, -2.0 * M_PI * (double)(k * c % N) / N);
+      tmp[r * N + k] = a;
+    }
+  for (int k1 = 0; k1 < N; ++k1)
+    for (int k0 = 0; k0 < N; ++k0) {
+      cd a = 0;
+      for (int r = 0; r < N; ++r) a += tmp[r * N + k1] * std::polar(1.0, -2.0 * M_PI * (double)(k0 * r % N) / N);
+      X[k0 * N + k1] = a;
+    }
+  pty::NoHook none;
+  auto read = [&](bool kspace) {
+    std::vector<cd> out(N * N);
+    for (int p0 = 0; p0 < N; ++p0)
+      for (int p1 = 0; p1 < N; ++p1) {
+        const float2 v = s[p0 * RS + p1];
+        const int i = kspace ? pty::kbin0<N>(p0) * N + pty::kbin1<N>(p1) : p0 * N + p1;
+        out[i] = cd(v.x, v.y);
+      }
+    return out;
+  };
+  auto scaled = [&](const std::vector<cd>& v, double f) {
+    std::vector<cd> o(v);
+    for (auto& z : o) z *= f;
+    return o;
+  };
+  // forward: col, block, row
+  each_thread(T, [&] { F::col_fwd(s.data(), tw.data(), none); });
+  each_thread(T, [&] { F::block_fwd(s.data(), tw.data()); });
+  each_thread(T, [&] { F::template row_fwd<true>(s.data(), none); });
+  const double e_fwd = rel(read(true), X);
+  // inverse: row, block, col
+  each_thread(T, [&] { F::row_inv(s.data(), tw.data(), none); });
+  each_thread(T, [&] { F::block_inv(s.data(), tw.data()); });
+  each_thread(T, [&] { F::col_inv(s.data(), tw.data()); });
+  const double e_inv = rel(read(false), scaled(x, (double)N * N));
+  // fused chains on the natural-layout array now holding N^2 x:
+  // forward with its last step fused into the next inverse's first (row_fwd_inv), then the inverse
+  each_thread(T, [&] { F::col_fwd(s.data(), tw.data(), none); });
+  each_thread(T, [&] { F::block_fwd(s.data(), tw.data()); });
+  each_thread(T, [&] { F::row_fwd_inv(s.data(), tw.data(), none); });
+  each_thread(T, [&] { F::block_inv(s.data(), tw.data()); });
+  each_thread(T, [&] { F::col_inv(s.data(), tw.data()); });
+  const double e_f1 = rel(read(false), scaled(x, std::pow((double)N, 4)));
+  // back to x: scale, then an inverse whose last step is fused into the next forward's first
+  // (col_inv_fwd), then the forward's remaining steps: the spectrum of x again
+  for (auto& v : s) v = make_float2(v.x / (float)std::pow((double)N, 4), v.y / (float)std::pow((double)N, 4));
+  each_thread(T, [&] { F::col_fwd(s.data(), tw.data(), none); });
+  each_thread(T, [&] { F::block_fwd(s.data(), tw.data()); });
+  each_thread(T, [&] { F::template row_fwd<true>(s.data(), none); });
+  each_thread(T, [&] { F::row_inv(s.data(), tw.data(), none); });
+  each_thread(T, [&] { F::block_inv(s.data(), tw.data()); });
+  each_thread(T, [&] { F::template col_inv_fwd<true>(s.data(), tw.data(), none); });
+  each_thread(T, [&] { F::block_fwd(s.data(), tw.data()); });
+  each_thread(T, [&] { F::template row_fwd<true>(s.data(), none); });
+  const double e_f2 = rel(read(true), scaled(X, (double)N * N));
+  std::printf("N %d T %d fwd %.3e inv %.3e fused %.3e\n", N, T, e_fwd, e_inv, std::max(e_f1, e_f2));
+}
+
+int main() {
+  run<64, 128>(1);
+  run<128, 256>(2);
+  run<128, 512>(3);
+  return 0;
+}
