@@ -50,7 +50,7 @@ enum {
                           a batch index was outside [0, Ntot) (then scan position 0 was used) */
   PTY_EWORKSPACE = 4,  /* workspace smaller than pty_workspace_size() */
   PTY_ECUDA = 8,       /* a CUDA launch failed; see pty_last_error() */
-  PTY_ETIMEOUT = 16,   /* a bounded device wait gave up (tensor-core GEMM pipeline, adjoint bulk copies) */
+  PTY_ETIMEOUT = 16,   /* a bounded device wait gave up (tensor-core GEMM pipeline; the optional bulk-copy stages) */
   PTY_ENONFINITE = 32  /* device bit: the loss or its normaliser was not finite */
 };
 
