@@ -1,15 +1,19 @@
-"""The shared-memory FFT header (paper_2505_07814_gb300/csrc/fft_smem.cuh) compiled for the host.
+"""The shared-memory FFT headers (paper_2505_07814_gb300/csrc/fft_smem.cuh and fft_cluster.cuh)
+compiled for the host.
 
-tests/fft_host_check.cpp runs the header's transform steps one emulated thread at a time, with a
+tests/fft_host_check.cpp runs the headers' transform steps one emulated thread at a time, with a
 step finished by every thread before the next starts, as the barrier after each step guarantees
-on the GPU.  It compares them with a direct double-precision 2D DFT, read through the k-space
-digit layout (kbin0 / kbin1).  Cases: N = 64 (128 threads) and N = 128 (256 and 512 threads).  Each
-is checked with the default butterflies and twiddle skip, and with each switched off.
+on the GPU.  The N = 256 transform runs on four emulated CTAs of a cluster
+(tests/host_shim/cooperative_groups.h maps a CTA's shared-memory pointer to another CTA's buffer).
+It compares them with a direct double-precision 2D DFT, read through the k-space digit layout
+(kbin0 / kbin1).  Cases: N = 64 (128 threads), N = 128 (256 and 512 threads) and N = 256 (four CTAs
+of 512 threads).  Each is checked with the default butterflies and twiddle skip, and with each
+switched off.
 
 Bounds: an FP32 FFT of N^2 = 2^14 points has a relative L2 error of a few 1e-7 (1.3e-7 measured
 for one transform, 5e-7 for the two-transform fused chains); the bounds leave 5-8x headroom and are
 far below the error of any wrong twiddle, sign or index (a 0.1% error in one butterfly constant
-gives 3e-4).
+gives 3e-4, a cross-CTA write to the wrong rank 1.4).
 """
 import os
 import re
@@ -32,7 +36,7 @@ def test_fft_steps_match_direct_dft(tmp_path, defines):
                     os.path.join(ROOT, "tests", "fft_host_check.cpp"), "-o", exe], check=True)
     out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
     rows = re.findall(r"N (\d+) T (\d+) fwd (\S+) inv (\S+) fused (\S+)", out)
-    assert [(int(n), int(t)) for n, t, *_ in rows] == [(64, 128), (128, 256), (128, 512)], out
+    assert [(int(n), int(t)) for n, t, *_ in rows] == [(64, 128), (128, 256), (128, 512), (256, 512)], out
     for n, t, fwd, inv, fused in rows:
         assert float(fwd) <= 1e-6 and float(inv) <= 1e-6, (n, t, fwd, inv)
         assert float(fused) <= 2e-6, (n, t, fused)
