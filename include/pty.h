@@ -155,6 +155,36 @@ int pty_loss_grad(const pty_geom* geom, int B, const int32_t* idx, const float* 
                   float* g_amp, float* g_phase, float* g_probe, float* g_pos, float* g_tilt,
                   float* g_dz, int accumulate, void* ws, size_t ws_bytes, void* stream);
 
+/* A batch split into parts: over data-parallel ranks (one part per GPU) or over sub-batches whose
+ * gradients are accumulated.  The losses of Eq. 5 and 6 are means over the detector pixels D and the
+ * whole batch B, divided by <I_meas^p> of that same batch (Sec. "Optimizers and loss functions"),
+ * so a part's gradient depends on the rest of the batch through three sums: S = sum of I_meas^p,
+ * Q = sum of (I_model^p - I_meas^p)^2 (Gaussian only) and D B.  pty_loss_stats writes this part's
+ * three sums; adding them over the parts (an all-reduce) gives the whole batch's, which
+ * pty_loss_grad_part then uses.  The parts' gradients (accumulate = 1 on one device, or an
+ * all-reduce of each gradient across ranks) then add up to pty_loss_grad's gradient of the whole
+ * batch, and the parts' losses to its loss.
+ *
+ * pty_loss_stats: stats = device double[3], overwritten with {S, Q, D B} of this call's B patterns.
+ *   Poisson needs the measured patterns only (Q is written as 0, no forward pass runs); Gaussian
+ *   runs the forward model to get Q.  ws: as pty_loss_grad (pty_workspace_size bytes).
+ * pty_loss_grad_part: pty_loss_grad for the B patterns of one part, with the normaliser taken from
+ *   whole_stats = device double[3], the sums {S, Q, D B} of the whole batch.  loss receives this
+ *   part's share of the whole batch's loss (Poisson: -sum(I_meas^p log(I_model^p + eps) - I_model^p)
+ *   / S over this part's pixels; Gaussian: sqrt(D B / Q) Q_part / S).  The PACBED and sparsity terms
+ *   (w_pacbed, w_sparse) compare or average over the whole batch at once and must be 0 here
+ *   (PTY_EINVAL).  Other arguments, layouts and error codes as pty_loss_grad. */
+int pty_loss_stats(const pty_geom* geom, int B, const int32_t* idx, const float* amp,
+                   const float* phase, const float* probe, const float* pos, const float* tilt,
+                   const float* dz, const float* I_meas, double* stats, void* ws, size_t ws_bytes,
+                   void* stream);
+int pty_loss_grad_part(const pty_geom* geom, int B, const int32_t* idx, const float* amp,
+                       const float* phase, const float* probe, const float* pos, const float* tilt,
+                       const float* dz, const float* I_meas, const double* whole_stats, double* loss,
+                       float* I_model, float* g_amp, float* g_phase, float* g_probe, float* g_pos,
+                       float* g_tilt, float* g_dz, int accumulate, void* ws, size_t ws_bytes,
+                       void* stream);
+
 /* Forward model as pty_forward, keeping in ws what pty_backward needs (checkpoints per
  * geom->ckpt_stride, far-field waves, transmission, probe spectra).  The parameters and ws must not
  * change between this call and the matching pty_backward. */
@@ -241,6 +271,9 @@ int pty_supported_sizes(void);
  *  - Scratch is a fixed array of PTY_NOALLOC_SCRATCH_BYTES (32 MiB) inside this library's device
  *    code.  Every GPU that loads the library holds it until the process exits.  A batch whose
  *    pty_workspace_size() exceeds it is rejected with PTY_EWORKSPACE before anything is launched.
+ *    The workspace holds the transmission and its gradient (16 bytes per object voxel) besides the
+ *    per-wave buffers, so the object alone must stay under 2 Mi voxels (for example 8 x 512 x 512
+ *    does not fit, 1 x 1024 x 1024 fits with a few 64 x 64 waves).
  *  - The call allocates nothing.  Its first call on a device looks up the array's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call before any stream
  *    capture on the device.
@@ -270,6 +303,17 @@ int pty_loss_grad_noalloc(const pty_geom* geom, int B, const int32_t* idx, const
 long long pty_launch_count(void);
 int pty_profile_enable(int on);
 int pty_profile_read(double* ms, int n);
+
+/* Diagnostics for failure detection (not needed to use the library).  Every spin-wait of the
+ * tensor-core GEMM (split-precision DFTs, learned initialiser) is bounded: after a number of
+ * non-blocking polls it gives up, sets PTY_ETIMEOUT in the status word, waits for the matrix
+ * products it has already issued, releases its tensor memory and returns, so the context stays
+ * usable.  pty_set_wait_limit sets the poll limit of the pipeline waits of later launches
+ * (0 .. PTY_WAIT_POLLS_DEFAULT; negative restores the default), so a test can make a wait run out
+ * without a fault.  The wait for the already-issued products before the tensor memory is released
+ * always keeps the default limit.  Not thread-safe with concurrent launches; returns PTY_OK. */
+#define PTY_WAIT_POLLS_DEFAULT (1LL << 24)
+int pty_set_wait_limit(long long polls);
 
 #ifdef __cplusplus
 }

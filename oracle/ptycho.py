@@ -39,7 +39,13 @@ Readings where the paper is silent (each also listed in the design notes):
       the chosen likelihood at weight 1); L_PACBED raises the batch-mean patterns to p_pacbed
       (default 0.5) and normalises by <I_meas^p_pacbed>_{D,B}; L_sparse averages |phase|^p_sparse
       (default 1) over every slice of every batch position's N x N patch (a pixel reached by two
-      positions counts twice); sign(0) = 0 and |x|^(p - 1) = 0 at x = 0 for p < 1.
+      positions counts twice); sign(0) = 0 and |x|^(p - 1) = 0 at x = 0 for p < 1;
+  R11 a batch split into parts (data-parallel ranks, accumulated sub-batches): a part's gradient is
+      the adjoint, over that part's patterns only, of dL/dI of the whole batch's loss; a part's
+      loss is its share of the whole batch's loss: the Poisson sum over its pixels divided by the
+      whole batch's sum of I_meas^p, or for Gaussian the whole loss times the part's fraction of
+      the whole batch's squared residuals.  The shares add up to the loss and the parts' gradients
+      to the whole batch's gradient.
 
 Array conventions: row-major, axis 0 = rows, axis 1 = columns; k_a = fftfreq(N, dx) in 1/angstrom;
 positions and tilts are (axis-0, axis-1) pairs; the probe is [M][N][N]; the object amplitude and
@@ -232,6 +238,19 @@ def loss_grad_I(geom, I_model, I_meas):
     raise ValueError(geom.loss)
 
 
+def loss_share(geom, I_model, I_meas, a, b):
+    """The share of patterns a..b-1 in the loss of the whole batch I_model (reading R11)."""
+    p = geom.power
+    Im, Id = _pow(I_model, p), _pow(I_meas, p)
+    if geom.loss == GAUSSIAN:
+        r2 = (Im - Id) ** 2
+        total = np.sum(r2)
+        return 0.0 if total == 0.0 else loss_value(geom, I_model, I_meas) * np.sum(r2[a:b]) / total
+    if geom.loss == POISSON:
+        return -np.sum(Id[a:b] * np.log(Im[a:b] + geom.eps) - Im[a:b]) / np.sum(Id)
+    raise ValueError(geom.loss)
+
+
 def pacbed_value(geom, I_model, I_meas):
     """L_PACBED: the batch-mean patterns (position-averaged CBED) compared like Eq. 5."""
     p = 0.5 if geom.p_pacbed is None else float(geom.p_pacbed)
@@ -300,12 +319,16 @@ class Gradients:
     dz: float
 
 
-def loss_and_grad(geom, amp, phase, probe, pos, tilt, dz, I_meas, idx):
+def loss_and_grad(geom, amp, phase, probe, pos, tilt, dz, I_meas, idx, part=None):
     """Loss of the batch idx and the exact gradient of every parameter.
 
     I_meas is indexed by scan position ([Ntot][N][N], DC-centred).  Gradient arrays cover the
-    whole parameter (zeros where the batch does not reach).
+    whole parameter (zeros where the batch does not reach).  part = (a, b): the loss share and
+    the gradient of patterns idx[a:b] only, within the whole batch idx (reading R11); the PACBED
+    and sparsity terms are not split.
     """
+    if part is not None and (geom.w_pacbed or geom.w_sparse):
+        raise ValueError("the PACBED and sparsity terms are not split into parts")
     N, M, Nz, K = geom.N, geom.M, geom.Nz, geom.K
     idx = list(idx)
     B = len(idx)
@@ -352,6 +375,9 @@ def loss_and_grad(geom, amp, phase, probe, pos, tilt, dz, I_meas, idx):
     if geom.w_pacbed:
         loss += geom.w_pacbed * pacbed_value(geom, I_model, Imeas_b)
         dLdI = dLdI + geom.w_pacbed * pacbed_grad_I(geom, I_model, Imeas_b)
+    lo, hi = (0, B) if part is None else part
+    if part is not None:
+        loss = loss_share(geom, I_model, Imeas_b, lo, hi)
 
     # ---------------- adjoint ----------------
     gT = np.zeros_like(T)
@@ -360,6 +386,8 @@ def loss_and_grad(geom, amp, phase, probe, pos, tilt, dz, I_meas, idx):
     g_tilt = np.zeros_like(np.asarray(tilt, dtype=np.float64))
     g_dz = 0.0
     for b, (j, r, dr, th, Mj, R, per_mode) in enumerate(records):
+        if not lo <= b < hi:
+            continue
         w = np.fft.ifftshift(dLdI[b])  # back to DFT order
         # dM/d(dz) / M and dM/d(theta_a) / M
         c_dz = 1j * (-np.pi * geom.lam * (k0 ** 2 + k1 ** 2)

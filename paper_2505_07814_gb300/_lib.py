@@ -37,7 +37,7 @@ EXPORTS = ("pty_workspace_size", "pty_forward", "pty_loss_grad", "pty_adam_updat
            "pty_profile_read", "pty_loss_grad_noalloc", "pty_forward_save", "pty_backward",
            "pty_cnn_param_count", "pty_cnn_workspace_size", "pty_cnn_forward", "pty_cnn_loss_grad", "pty_cnn_adam",
            "pty_cnn_train_step", "pty_cnn_targets", "pty_cnn_stitch", "pty_cnn_stitch_finish", "pty_cnn_read_state", "pty_constrain",
-           "pty_constrain_workspace_size")
+           "pty_constrain_workspace_size", "pty_loss_stats", "pty_loss_grad_part", "pty_set_wait_limit")
 PROF_STAGES = ("prepare_object", "probe_spectrum", "forward", "loss", "loss_finalize", "adjoint", "object_grad",
                "probe_grad", "scalar_grad")
 
@@ -93,6 +93,10 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pty_forward.restype = I
     lib.pty_loss_grad.argtypes = [G, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, I, P, SZ, P]
     lib.pty_loss_grad.restype = I
+    lib.pty_loss_stats.argtypes = [G, I, P, P, P, P, P, P, P, P, P, P, SZ, P]
+    lib.pty_loss_stats.restype = I
+    lib.pty_loss_grad_part.argtypes = [G, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, P, I, P, SZ, P]
+    lib.pty_loss_grad_part.restype = I
     lib.pty_forward_save.argtypes = [G, I, P, P, P, P, P, P, P, P, P, SZ, P]
     lib.pty_forward_save.restype = I
     lib.pty_backward.argtypes = [G, I, P, P, P, P, P, P, P, P, P, P, P, P, P, P, I, P, SZ, P]
@@ -115,6 +119,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pty_profile_enable.restype = I
     lib.pty_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), I]
     lib.pty_profile_read.restype = I
+    lib.pty_set_wait_limit.argtypes = [ctypes.c_longlong]
+    lib.pty_set_wait_limit.restype = I
     F = ctypes.c_float
     lib.pty_cnn_param_count.argtypes = []
     lib.pty_cnn_param_count.restype = SZ
@@ -168,6 +174,18 @@ def pty_loss_grad(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss, 
                                 ws_bytes, stream))
 
 
+def pty_loss_stats(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas, stats, ws, ws_bytes, stream):
+    _check(load().pty_loss_stats(ctypes.byref(geom), B, idx, amp, phase, probe, pos, tilt, dz, I_meas, stats, ws,
+                                 ws_bytes, stream))
+
+
+def pty_loss_grad_part(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas, whole_stats, loss, I_model, g_amp,
+                       g_phase, g_probe, g_pos, g_tilt, g_dz, accumulate, ws, ws_bytes, stream):
+    _check(load().pty_loss_grad_part(ctypes.byref(geom), B, idx, amp, phase, probe, pos, tilt, dz, I_meas,
+                                     whole_stats, loss, I_model, g_amp, g_phase, g_probe, g_pos, g_tilt, g_dz,
+                                     int(accumulate), ws, ws_bytes, stream))
+
+
 def pty_forward_save(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_model, ws, ws_bytes, stream):
     _check(load().pty_forward_save(ctypes.byref(geom), B, idx, amp, phase, probe, pos, tilt, dz, I_model, ws,
                                    ws_bytes, stream))
@@ -218,6 +236,10 @@ def pty_profile_read() -> tuple[int, dict]:
     if n < 0:
         raise PtyError(PTY_ECUDA, "profile read failed")
     return n, {name: buf[k] for k, name in enumerate(PROF_STAGES)}
+
+
+def pty_set_wait_limit(polls: int):
+    _check(load().pty_set_wait_limit(int(polls)))
 
 
 def pty_loss_grad_noalloc(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss, I_model, g_amp, g_phase,

@@ -52,7 +52,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     """Compile and link libpty.so; returns its path.  Skips work if the library is newer than
     every source and header."""
     os.makedirs(BUILD, exist_ok=True)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, "pty.h"), __file__]
+    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
+    deps.append(__file__)
     if not force and not verbose and os.path.exists(LIB):
         if os.path.getmtime(LIB) >= max(os.path.getmtime(d) for d in deps):
             return LIB

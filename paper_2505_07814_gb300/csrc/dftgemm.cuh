@@ -586,6 +586,11 @@ int run_pipeline_gemm(const Problem& pb) {
         if (cudaMemsetAsync(pb.loss_out, 0, sizeof(double), pb.stream) != cudaSuccess) return ps.base.memset_failed();
       }
       return ps.adjoint();
+    case MODE_STATS:
+      if (pb.loss == PTY_LOSS_POISSON) return ps.base.stats();  // the measured patterns only
+      rc = ps.forward(pb.I_meas);
+      if (rc) return rc;
+      return ps.base.stats_write();
     case MODE_BACKWARD:
       rc = ps.base.external_dldi(pb.dldi);
       if (rc) return rc;

@@ -40,7 +40,7 @@ namespace pty {
 
 constexpr int TC_BM = 128, TC_BK = 64, TC_THREADS = 256;
 constexpr int TC_LBO = 128, TC_SBO = 1024;
-constexpr long TC_SPIN = 1L << 24;  // non-blocking mbarrier polls before a wait gives up (well under a second)
+constexpr long TC_SPIN = PTY_WAIT_POLLS_DEFAULT;  // non-blocking mbarrier polls before a wait gives up (well under a second)
 
 // Pipeline depth and CTAs per SM by tile width: a 128 x 256 tile with promotion holds 128 FP32
 // accumulators per thread (one CTA per SM, three stages); narrower tiles run two CTAs per SM with
@@ -82,12 +82,15 @@ __device__ __forceinline__ bool tc_try_wait(uint32_t bar, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait; false on timeout.
-__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity) {
-  for (long i = 0; i < TC_SPIN; ++i)
+// Bounded wait of at most `limit` polls; false on timeout.
+__device__ __forceinline__ bool tc_wait(uint32_t bar, uint32_t parity, long limit = TC_SPIN) {
+  for (long i = 0; i < limit; ++i)
     if (tc_try_wait(bar, parity)) return true;
   return false;
 }
+// Poll limit of the pipeline's waits (the final drain before TMEM is released always takes
+// TC_SPIN); pty_set_wait_limit changes it for tests that make a wait run out.
+long stage_wait_limit();
 
 __device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
   uint32_t r[32];
@@ -141,9 +144,10 @@ __device__ __forceinline__ void cur_advance(const L& l, typename CursorOf<L>::T&
 
 // grid = (ceil(N / BN), ceil(M / 128), splits); blockIdx.z takes K blocks [z kb_per, (z + 1) kb_per).
 // Dynamic shared memory: tc_smem_bytes<BN>().  K is a multiple of 64 (the loaders pad with zeros).
+// spin: poll limit of the pipeline's waits (stage reuse, promotion, last block).
 template <class H, class LoadA, class LoadB, class Epi, int BN, bool PROMOTE>
 __global__ void __launch_bounds__(TC_THREADS, TcShape<BN>::MINB)
-    k_gemm_tc(LoadA la, LoadB lb, int K, int kb_per, Epi epi, int* status) {
+    k_gemm_tc(LoadA la, LoadB lb, int K, int kb_per, Epi epi, int* status, long spin) {
   static_assert(BN == 64 || BN == 128 || BN == 256, "BN");
   constexpr int TC_STAGES = TcShape<BN>::STAGES;
   constexpr int A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2, STAGE = A_BYTES + B_BYTES;
@@ -187,8 +191,8 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<BN>::MINB)
   // __syncthreads_and before anything that needs every thread (barriers, .sync.aligned loads).
   bool ok = true;
   int issued = -1;  // last block whose MMAs were issued (uniform)
-  auto wait_block = [&](int q) {  // block q's MMAs complete
-    return tc_wait(tc_smem_u32(bars + q % TC_STAGES), (uint32_t)((q / TC_STAGES) & 1));
+  auto wait_block = [&](int q, long limit) {  // block q's MMAs complete
+    return tc_wait(tc_smem_u32(bars + q % TC_STAGES), (uint32_t)((q / TC_STAGES) & 1), limit);
   };
   // add block q (TMEM region q % 2, complete) to the register accumulator
   auto promote = [&](int q) {
@@ -305,7 +309,7 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<BN>::MINB)
     unsigned char* sb = sa + A_BYTES;
     // the stage is free once the MMAs of block q - STAGES are done (already waited for, in
     // practice, by the promotion or the direct-B copy of an earlier iteration)
-    bool mine = q < TC_STAGES || wait_block(q - TC_STAGES);
+    bool mine = q < TC_STAGES || wait_block(q - TC_STAGES, spin);
     if (mine) stash(q);
     if constexpr (kDirectA || kDirectB) {  // block q's copies landed (newer ones may still fly)
       if (D >= 2 && q + 1 < nkb) {
@@ -342,7 +346,7 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<BN>::MINB)
     if constexpr (PROMOTE) {
       if (q > 0) {
         // block q - 1's region is refilled by block q + 1, issued only after the next barrier
-        ok = __syncthreads_and(wait_block(q - 1)) != 0;
+        ok = __syncthreads_and(wait_block(q - 1, spin)) != 0;
         if (!ok) break;
         promote(q - 1);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -351,14 +355,14 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<BN>::MINB)
     // direct copies of block q + D go to the stage block q - 1 read (finished once promoted)
     if constexpr (kDirectA || kDirectB) {
       if (q + D < nkb) {
-        if (!PROMOTE && q >= 1) mine = wait_block(q - 1);
+        if (!PROMOTE && q >= 1) mine = wait_block(q - 1, spin);
         if (mine) copy_direct(q + D);
       }
     }
     if constexpr (!PROMOTE) ok = ok && mine;
   }
   if (nkb > 0 && ok) {
-    ok = __syncthreads_and(wait_block(nkb - 1)) != 0;
+    ok = __syncthreads_and(wait_block(nkb - 1, spin)) != 0;
     if (ok) {
       if constexpr (PROMOTE) promote(nkb - 1);
       else asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -368,7 +372,7 @@ __global__ void __launch_bounds__(TC_THREADS, TcShape<BN>::MINB)
     if (tid == 0) atomicOr(status, PTY_ETIMEOUT);
     // let whatever was issued finish (bounded) before the accumulator is released
     asm volatile("cp.async.wait_all;" ::: "memory");
-    if (issued >= 0) wait_block(issued);
+    if (issued >= 0) wait_block(issued, TC_SPIN);
   } else if (nkb > 0) {
     const int row = m0 + 32 * (warp & 3) + lane;
     if constexpr (PROMOTE) {
@@ -411,7 +415,8 @@ cudaError_t launch_gemm_tc(const LA& la, const LB& lb, int rows, int cols, int K
   if (splits < 1) splits = 1;
   const int kb_per = (kb_all + splits - 1) / splits;
   const dim3 grid((cols + BN - 1) / BN, (rows + TC_BM - 1) / TC_BM, (kb_all + kb_per - 1) / kb_per);
-  kern<<<grid, TC_THREADS, tc_smem_bytes<BN>(), st>>>(la, lb, kb_all * TC_BK, kb_per, epi, status);
+  kern<<<grid, TC_THREADS, tc_smem_bytes<BN>(), st>>>(la, lb, kb_all * TC_BK, kb_per, epi, status,
+                                                       stage_wait_limit());
   return cudaGetLastError();
 }
 

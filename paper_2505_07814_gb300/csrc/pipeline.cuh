@@ -968,9 +968,14 @@ __global__ void k_pacbed_fold(float* __restrict__ u, const float* __restrict__ p
     u[i] = fmaf(gp, pacg[i % NN], gs * u[i]);
 }
 
-// Batch loss (Eq. 5 / 6) and the normaliser of dL/dI, in FP64, fixed summation order.
+// Batch loss (Eq. 5 / 6) and the normaliser of dL/dI, in FP64, fixed summation order.  With the
+// means of Eq. 5 / 6 written out over D detector pixels and B patterns, Poisson is -Y / S and
+// Gaussian sqrt(D B Q) / S, where S = sum of I_meas^p, Y = sum of the Poisson summands and
+// Q = sum of the squared residuals.  `whole` (or nullptr) holds {S, Q, D B} of the whole batch when
+// this call holds one part of it: the normaliser then comes from the whole batch, and the loss
+// written is this part's share of the whole batch's loss (the shares of the parts add up to it).
 static __global__ void k_loss_finalize(const double* __restrict__ lpart, int B, int loss, double DB, double* scal,
-                                double* loss_out, int* status) {
+                                       double* loss_out, int* status, const double* __restrict__ whole) {
   __shared__ double red[64];
   double x = 0.0, y = 0.0;
   for (int b = threadIdx.x; b < B; b += blockDim.x) {
@@ -979,13 +984,16 @@ static __global__ void k_loss_finalize(const double* __restrict__ lpart, int B, 
   }
   block_sum2<256>(x, y, red);
   if (threadIdx.x == 0) {
+    const double S = whole ? whole[0] : x;
     double Lv, scale;
     if (loss == PTY_LOSS_POISSON) {
-      Lv = -y / x;
-      scale = 1.0 / x;
+      Lv = -y / S;
+      scale = 1.0 / S;
     } else {
-      Lv = sqrt(DB * y) / x;
-      scale = y > 0.0 ? sqrt(DB) / (sqrt(y) * x) : 0.0;
+      const double Q = whole ? whole[1] : y, DBw = whole ? whole[2] : DB;
+      // this part's share y / Q of sqrt(D B Q) / S is sqrt(D B / Q) y / S
+      Lv = Q > 0.0 ? sqrt(DBw / Q) * y / S : 0.0;
+      scale = Q > 0.0 ? sqrt(DBw) / (sqrt(Q) * S) : 0.0;
     }
     if (!isfinite(Lv) || !isfinite(scale)) {
       atomicOr(status, PTY_ENONFINITE);
@@ -994,6 +1002,43 @@ static __global__ void k_loss_finalize(const double* __restrict__ lpart, int B, 
     scal[0] = scale;
     scal[1] = Lv;
     if (loss_out) *loss_out = Lv;
+  }
+}
+
+// Per-pattern sum of I_meas^p (one CTA per batch entry) into lpart[2 b]; lpart[2 b + 1] = 0.  The
+// Poisson normaliser needs only the measured patterns, so its statistics need no forward pass.
+template <int N, int T>
+__global__ void __launch_bounds__(T) k_meas_sum(const float* __restrict__ I_meas, const int32_t* __restrict__ idx,
+                                                int Ntot, float p, double* __restrict__ lpart, int* status) {
+  constexpr int NN = N * N;
+  __shared__ double red[2 * (T / 32)];
+  const int b = blockIdx.x;
+  const float* Id = I_meas + (size_t)checked_index(idx, b, Ntot, status) * NN;
+  float sd = 0.f;
+  for (int q = threadIdx.x; q < NN; q += T) sd += pow_nn(Id[q], p);
+  double x = sd, y = 0.0;
+  block_sum2<T>(x, y, red);
+  if (threadIdx.x == 0) {
+    lpart[2 * b] = x;
+    lpart[2 * b + 1] = 0.0;
+  }
+}
+
+// {sum over the batch of lpart[2 b], of lpart[2 b + 1], D B} into out[3] (fixed summation order).
+static __global__ void k_batch_stats(const double* __restrict__ lpart, int B, double DB, double* __restrict__ out,
+                                     int* status) {
+  __shared__ double red[64];
+  double x = 0.0, y = 0.0;
+  for (int b = threadIdx.x; b < B; b += blockDim.x) {
+    x += lpart[2 * b];
+    y += lpart[2 * b + 1];
+  }
+  block_sum2<256>(x, y, red);
+  if (threadIdx.x == 0) {
+    if (!isfinite(x) || !isfinite(y)) atomicOr(status, PTY_ENONFINITE);
+    out[0] = x;
+    out[1] = y;
+    out[2] = DB;
   }
 }
 
@@ -1610,7 +1655,7 @@ struct Pass {
   int K, nseg;
 
   explicit Pass(const Problem& p) : pb(p), ws(p.ws), st(p.stream) {
-    save = pb.mode != MODE_FORWARD;
+    save = pb.mode != MODE_FORWARD && pb.mode != MODE_STATS;
     const int gm = pb.grad_mask;
     want_obj = save && (gm & (PTY_GRAD_AMP | PTY_GRAD_PHASE));
     want_probe = save && (gm & PTY_GRAD_PROBE);
@@ -1749,7 +1794,8 @@ struct Pass {
     }
     PTY_LAUNCH_CHECK("k_loss", 3);
     if (I_meas) {
-      k_loss_finalize<<<1, 256, 0, st>>>(ws.lpart, pb.B, pb.loss, (double)pb.B * NN, ws.scal, pb.loss_out, ws.status);
+      k_loss_finalize<<<1, 256, 0, st>>>(ws.lpart, pb.B, pb.loss, (double)pb.B * NN, ws.scal, pb.loss_out, ws.status,
+                                         pb.whole);
       PTY_LAUNCH_CHECK("k_loss_finalize", 4);
       if (pac) {
         k_pacbed<N><<<1, 1024, 0, st>>>(ws.pac, ws.pacpart, pb.B, pb.p_pac, pb.w_pac, pb.loss_out, ws.scal,
@@ -1773,6 +1819,27 @@ struct Pass {
     PTY_LAUNCH_RC(launch_waves<C>(fwd_kernel(), pb.B * pb.M * pb.Ko, TF, fwd_kernel_smem_bytes<N>(), st, fwd_args_saved()),
                   "k_forward", 2);
     return loss_phase(I_meas);
+  }
+
+  // This batch's loss statistics {sum I_meas^p, sum of squared residuals (Gaussian), D B}: Poisson
+  // needs the measured patterns only, the Gaussian residuals need the forward model.
+  int stats() {
+    if (pb.loss == PTY_LOSS_POISSON) {
+      if (pb.B > 0) {
+        k_meas_sum<N, T><<<pb.B, T, 0, st>>>(pb.I_meas, pb.idx, pb.Ntot, pb.p, ws.lpart, ws.status);
+        PTY_LAUNCH_CHECK("k_meas_sum", -1);
+      }
+    } else {
+      int rc = forward(pb.I_meas);
+      if (rc) return rc;
+    }
+    return stats_write();
+  }
+  // the per-pattern sums of the loss kernel (or k_meas_sum) into the caller's three statistics
+  int stats_write() {
+    k_batch_stats<<<1, 256, 0, st>>>(ws.lpart, pb.B, (double)pb.B * NN, pb.stats_out, ws.status);
+    PTY_LAUNCH_CHECK("k_batch_stats", -1);
+    return PTY_OK;
   }
 
   // dL/dI from the caller instead of the loss (the adjoint of the forward model alone).
@@ -1959,6 +2026,8 @@ int run_pipeline(const Problem& pb) {
         if (cudaMemsetAsync(pb.loss_out, 0, sizeof(double), pb.stream) != cudaSuccess) return ps.memset_failed();
       }
       return ps.adjoint();
+    case MODE_STATS:
+      return ps.stats();
     case MODE_BACKWARD:
       rc = ps.external_dldi(pb.dldi);
       if (rc) return rc;

@@ -49,6 +49,10 @@ void prof_mark(int stage, cudaStream_t st) {
 
 static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
 
+// Poll limit of the tensor-core GEMM's pipeline waits (pty_set_wait_limit).
+static long g_stage_spin = -1;
+long stage_wait_limit() { return g_stage_spin >= 0 ? g_stage_spin : (long)PTY_WAIT_POLLS_DEFAULT; }
+
 // Slices per recompute segment actually used: 1 (checkpoint every slice) unless the caller asked for
 // a stride and some gradient needs the forward waves.
 int effective_stride(const pty_geom& g) {
@@ -63,7 +67,7 @@ size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspac
   const size_t Ko = g.obj_modes > 1 ? (size_t)g.obj_modes : 1;
   const size_t nobj = Ko * g.Nz * g.H * g.W;
   const size_t waves = (size_t)B * g.M * Ko;
-  const bool grad = mode != MODE_FORWARD;
+  const bool grad = mode != MODE_FORWARD && mode != MODE_STATS;
   const bool want_obj = grad && (g.grad_mask & (PTY_GRAD_AMP | PTY_GRAD_PHASE));
   const bool want_prop = grad && (g.grad_mask & (PTY_GRAD_DZ | PTY_GRAD_TILT)) && g.Nz > 1;
   const bool want_probe = grad && (g.grad_mask & PTY_GRAD_PROBE);
@@ -82,6 +86,10 @@ size_t layout_workspace(const pty_geom& g, int B, int mode, char* base, Workspac
   w.T = (float2*)take(sizeof(float2) * nobj);
   w.Phat = (float2*)take(sizeof(float2) * g.M * NN);
   w.Imode = (float*)take(sizeof(float) * waves * NN);
+  if (mode == MODE_STATS) {
+    w.u = (float*)take(sizeof(float) * (size_t)B * NN);
+    w.lpart = (double*)take(sizeof(double) * 2 * (size_t)(B > 0 ? B : 1));
+  }
   if (grad) {
     if (K == 1) {
       if (want_obj) w.ckpt = (float2*)take(sizeof(float2) * waves * g.Nz * NN);
@@ -280,6 +288,31 @@ __global__ void k_adam(AdamArgs a) {
   }
 }
 
+// Output checks and dispatch of a loss-and-gradient pass prepared in pb.
+static int grad_call(Problem& pb, const pty_geom* geom, int B, const float* I_meas, double* loss, float* I_model,
+                     float* g_amp, float* g_phase, float* g_probe, float* g_pos, float* g_tilt, float* g_dz,
+                     int accumulate) {
+  const int gm = geom->grad_mask;
+  REQUIRE(B == 0 || I_meas, "I_meas is NULL");
+  REQUIRE(!(gm & PTY_GRAD_AMP) || g_amp, "g_amp is NULL but PTY_GRAD_AMP is requested");
+  REQUIRE(!(gm & PTY_GRAD_PHASE) || g_phase, "g_phase is NULL but PTY_GRAD_PHASE is requested");
+  REQUIRE(!(gm & PTY_GRAD_PROBE) || (g_probe && aligned(g_probe, 8)), "g_probe is NULL or misaligned");
+  REQUIRE(!(gm & PTY_GRAD_POS) || g_pos, "g_pos is NULL but PTY_GRAD_POS is requested");
+  REQUIRE(!(gm & PTY_GRAD_TILT) || g_tilt, "g_tilt is NULL but PTY_GRAD_TILT is requested");
+  REQUIRE(!(gm & PTY_GRAD_DZ) || g_dz, "g_dz is NULL but PTY_GRAD_DZ is requested");
+  pb.I_meas = I_meas;
+  pb.loss_out = loss;
+  pb.I_model = I_model;
+  pb.g_amp = g_amp;
+  pb.g_phase = g_phase;
+  pb.g_probe = reinterpret_cast<float2*>(g_probe);
+  pb.g_pos = g_pos;
+  pb.g_tilt = g_tilt;
+  pb.g_dz = g_dz;
+  pb.accumulate = accumulate ? 1 : 0;
+  return dispatch(pb);
+}
+
 }  // namespace pty
 
 using namespace pty;
@@ -309,25 +342,38 @@ int pty_loss_grad(const pty_geom* geom, int B, const int32_t* idx, const float* 
   Problem pb;
   int rc = prepare(geom, B, MODE_GRAD, idx, amp, phase, probe, pos, tilt, dz, ws, ws_bytes, stream, &pb);
   if (rc) return rc;
-  const int gm = geom->grad_mask;
+  return grad_call(pb, geom, B, I_meas, loss, I_model, g_amp, g_phase, g_probe, g_pos, g_tilt, g_dz, accumulate);
+}
+
+int pty_loss_stats(const pty_geom* geom, int B, const int32_t* idx, const float* amp, const float* phase,
+                   const float* probe, const float* pos, const float* tilt, const float* dz, const float* I_meas,
+                   double* stats, void* ws, size_t ws_bytes, void* stream) {
+  Problem pb;
+  int rc = prepare(geom, B, MODE_STATS, idx, amp, phase, probe, pos, tilt, dz, ws, ws_bytes, stream, &pb);
+  if (rc) return rc;
   REQUIRE(B == 0 || I_meas, "I_meas is NULL");
-  REQUIRE(!(gm & PTY_GRAD_AMP) || g_amp, "g_amp is NULL but PTY_GRAD_AMP is requested");
-  REQUIRE(!(gm & PTY_GRAD_PHASE) || g_phase, "g_phase is NULL but PTY_GRAD_PHASE is requested");
-  REQUIRE(!(gm & PTY_GRAD_PROBE) || (g_probe && aligned(g_probe, 8)), "g_probe is NULL or misaligned");
-  REQUIRE(!(gm & PTY_GRAD_POS) || g_pos, "g_pos is NULL but PTY_GRAD_POS is requested");
-  REQUIRE(!(gm & PTY_GRAD_TILT) || g_tilt, "g_tilt is NULL but PTY_GRAD_TILT is requested");
-  REQUIRE(!(gm & PTY_GRAD_DZ) || g_dz, "g_dz is NULL but PTY_GRAD_DZ is requested");
+  REQUIRE(stats && aligned(stats, 8), "stats is NULL or not 8-byte aligned");
   pb.I_meas = I_meas;
-  pb.loss_out = loss;
-  pb.I_model = I_model;
-  pb.g_amp = g_amp;
-  pb.g_phase = g_phase;
-  pb.g_probe = reinterpret_cast<float2*>(g_probe);
-  pb.g_pos = g_pos;
-  pb.g_tilt = g_tilt;
-  pb.g_dz = g_dz;
-  pb.accumulate = accumulate ? 1 : 0;
+  pb.stats_out = stats;
   return dispatch(pb);
+}
+
+int pty_loss_grad_part(const pty_geom* geom, int B, const int32_t* idx, const float* amp, const float* phase,
+                       const float* probe, const float* pos, const float* tilt, const float* dz, const float* I_meas,
+                       const double* whole_stats, double* loss, float* I_model, float* g_amp, float* g_phase,
+                       float* g_probe, float* g_pos, float* g_tilt, float* g_dz, int accumulate, void* ws,
+                       size_t ws_bytes, void* stream) {
+  int rc = validate_geom(geom);
+  if (rc) return rc;
+  REQUIRE(whole_stats && aligned(whole_stats, 8), "whole_stats is NULL or not 8-byte aligned");
+  REQUIRE(geom->w_pacbed == 0.f && geom->w_sparse == 0.f,
+          "the PACBED and sparsity terms compare or average over the whole batch at once; a batch split into "
+          "parts supports the likelihood terms (Eq. 5 / 6) only");
+  Problem pb;
+  rc = prepare(geom, B, MODE_GRAD, idx, amp, phase, probe, pos, tilt, dz, ws, ws_bytes, stream, &pb);
+  if (rc) return rc;
+  pb.whole = whole_stats;
+  return grad_call(pb, geom, B, I_meas, loss, I_model, g_amp, g_phase, g_probe, g_pos, g_tilt, g_dz, accumulate);
 }
 
 int pty_forward_save(const pty_geom* geom, int B, const int32_t* idx, const float* amp, const float* phase,
@@ -456,6 +502,9 @@ constexpr size_t kNoallocBytes = (size_t)PTY_NOALLOC_SCRATCH_BYTES;
 // Loaded with the library's device code on every GPU that uses it and held until the process exits.
 __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 // Device address of g_noalloc_scratch per device ordinal (host code may not use the symbol itself).
+// Filled without a lock: two host threads making their first call on a device at once both look
+// the address up and store the same value, which is harmless.  cudaDeviceReset would make a cached
+// address stale; the library does not support a reset between calls.
 void* g_noalloc_addr[256] = {nullptr};
 }  // namespace
 
@@ -471,8 +520,14 @@ int pty_loss_grad_noalloc(const pty_geom* geom, int B, const int32_t* idx, const
   REQUIRE(B >= 0, "batch size %d < 0", B);
   const size_t need = layout_workspace(*geom, B, MODE_GRAD, nullptr, nullptr);
   if (need > kNoallocBytes) {
-    set_error("pty_loss_grad_noalloc: this batch needs %zu bytes of scratch but the fixed area holds %zu; "
-              "use a smaller batch or pty_loss_grad with a caller-owned workspace", need, kNoallocBytes);
+    const size_t empty = layout_workspace(*geom, 0, MODE_GRAD, nullptr, nullptr);
+    if (empty > kNoallocBytes)
+      set_error("pty_loss_grad_noalloc: the object alone needs %zu bytes of scratch (transmission and its "
+                "gradient) but the fixed area holds %zu; no batch fits; use pty_loss_grad with a caller-owned "
+                "workspace", empty, kNoallocBytes);
+    else
+      set_error("pty_loss_grad_noalloc: this batch needs %zu bytes of scratch but the fixed area holds %zu; "
+                "use a smaller batch or pty_loss_grad with a caller-owned workspace", need, kNoallocBytes);
     return PTY_EWORKSPACE;
   }
   int dev = 0;
@@ -502,6 +557,11 @@ int pty_loss_grad_noalloc(const pty_geom* geom, int B, const int32_t* idx, const
 }
 
 long long pty_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+int pty_set_wait_limit(long long polls) {
+  g_stage_spin = polls < 0 ? -1 : (long)(polls < PTY_WAIT_POLLS_DEFAULT ? polls : PTY_WAIT_POLLS_DEFAULT);
+  return PTY_OK;
+}
 
 int pty_profile_enable(int on) {
   if (on && !g_prof_created) {

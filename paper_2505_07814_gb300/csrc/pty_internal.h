@@ -44,7 +44,8 @@ struct Workspace {
 // MODE_FORWARD: patterns only.  MODE_FORWARD_SAVE: patterns, keeping in the workspace what a later
 // MODE_BACKWARD needs.  MODE_GRAD: loss and gradients in one pass.  MODE_BACKWARD: gradients for a
 // caller-supplied dL/dI, after a MODE_FORWARD_SAVE pass on the same workspace.
-enum Mode { MODE_FORWARD = 0, MODE_GRAD = 1, MODE_FORWARD_SAVE = 2, MODE_BACKWARD = 3 };
+// MODE_STATS: the loss statistics of the batch only (pty_loss_stats).
+enum Mode { MODE_FORWARD = 0, MODE_GRAD = 1, MODE_FORWARD_SAVE = 2, MODE_BACKWARD = 3, MODE_STATS = 4 };
 
 struct Problem {
   int N, M, Nz, H, W, Ntot, B;
@@ -62,6 +63,10 @@ struct Problem {
   const float* I_meas;
   const float* dldi;  // MODE_BACKWARD: dL/dI [B][N][N], DC-centred
   double* loss_out;
+  // Statistics of the whole batch when this call holds one part of it (pty_loss_grad_part), or
+  // nullptr: {sum of I_meas^p, sum of the Gaussian squared residuals, detector pixels x patterns}.
+  const double* whole;
+  double* stats_out;  // MODE_STATS: this call's part of those three sums
   float* I_model;
   float *g_amp, *g_phase, *g_pos, *g_tilt, *g_dz;
   float2* g_probe;
@@ -83,6 +88,8 @@ template <int N, int P>
 int run_pipeline_gemm(const Problem& pb);
 
 void set_error(const char* fmt, ...);
+// Current poll limit of the tensor-core GEMM's pipeline waits (pty_set_wait_limit).
+long stage_wait_limit();
 // Checks the fields of a geometry every entry point shares; PTY_OK or PTY_EINVAL (message set).
 int validate_geom(const pty_geom* g);
 

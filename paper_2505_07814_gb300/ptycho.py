@@ -154,9 +154,14 @@ class Ptycho:
         return out
 
     def loss_grad(self, params: Params, idx, I_meas: torch.Tensor, grads: Params | None = None,
-                  accumulate: bool = False, I_model: torch.Tensor | None = None):
+                  accumulate: bool = False, I_model: torch.Tensor | None = None,
+                  whole_stats: torch.Tensor | None = None):
         """Loss (Eq. 5/6) of the batch and gradients of every parameter named in geom.grads.
 
+        whole_stats: when idx is one part of a larger batch (a data-parallel rank's share, or a
+        sub-batch of an accumulated gradient), the float64 [3] device tensor of the whole batch's
+        loss statistics (the sum of every part's `loss_stats`); the loss and gradients are then this
+        part's share of the whole batch's (pty_loss_grad_part).
         Returns (loss as a float64 device tensor of one element, grads)."""
         idx = self._idx(idx)
         g = self.geom
@@ -164,11 +169,28 @@ class Ptycho:
         if grads is None:
             grads = params.zeros_like()
         gp = self._param_ptrs(grads)
-        _lib.pty_loss_grad(self.cg, B, _ptr(idx), *self._param_ptrs(params),
-                           _ptr(I_meas, torch.float32, g.Ntot * g.N * g.N, "I_meas"), self.loss.data_ptr(),
-                           _ptr(I_model, torch.float32, B * g.N * g.N, "I_model"), *gp, int(accumulate),
-                           self.ws.data_ptr(), self.ws_bytes, self._stream())
+        args = (_ptr(idx), *self._param_ptrs(params), _ptr(I_meas, torch.float32, g.Ntot * g.N * g.N, "I_meas"))
+        tail = (self.loss.data_ptr(), _ptr(I_model, torch.float32, B * g.N * g.N, "I_model"), *gp, int(accumulate),
+                self.ws.data_ptr(), self.ws_bytes, self._stream())
+        if whole_stats is None:
+            _lib.pty_loss_grad(self.cg, B, *args, *tail)
+        else:
+            _lib.pty_loss_grad_part(self.cg, B, *args, _ptr(whole_stats, torch.float64, 3, "whole_stats"), *tail)
         return self.loss, grads
+
+    def loss_stats(self, params: Params, idx, I_meas: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """This batch's loss statistics {sum I_meas^p, sum of squared residuals (Gaussian), pixels x
+        patterns} as a float64 [3] device tensor (pty_loss_stats).  The sum over the parts of a
+        batch is the `whole_stats` argument of loss_grad."""
+        idx = self._idx(idx)
+        g = self.geom
+        if out is None:
+            out = torch.empty(3, dtype=torch.float64, device=self.device)
+        _lib.pty_loss_stats(self.cg, idx.numel(), _ptr(idx), *self._param_ptrs(params),
+                            _ptr(I_meas, torch.float32, g.Ntot * g.N * g.N, "I_meas"),
+                            _ptr(out, torch.float64, 3, "stats"), self.ws.data_ptr(), self.ws_bytes,
+                            self._stream())
+        return out
 
     def forward_save(self, params: Params, idx, out: torch.Tensor | None = None) -> torch.Tensor:
         """Modelled patterns, keeping in the workspace what `backward` needs (pty_forward_save)."""

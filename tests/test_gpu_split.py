@@ -1,10 +1,12 @@
 """Split-precision DFT-GEMM path (pty_geom.fft_impl) against the FP64 oracle.
 
 Every per-slice 2D DFT runs as dense DFT matrix products on the tensor cores with each FP32
-operand cut into 16-bit pieces and FP32 accumulation.  fp16 hi + lo keeps 22 significant bits and
-bf16 with three pieces 24: both meet relative L2 <= 1e-4 on intensities and loss and <= 1e-3 on
-gradients.  bf16 hi + lo keeps 16 bits, 2^8 fewer than FP32, so its transforms carry about 2^8 times
-the FP32 path's rounding error: its gradient bar is 4e-3 (intensities still 1e-4).
+operand cut into 16-bit pieces and FP32 accumulation.  The bars are relative L2 <= 1e-4 on
+intensities and loss and <= 1e-3 on gradients.  fp16 hi + lo keeps 22 significant bits and bf16 with
+three pieces 24: both meet them.  bf16 hi + lo keeps 16 bits, 2^8 fewer than FP32, so its transforms
+carry about 2^8 times the FP32 path's rounding error: it meets the intensity bar but its gradients
+miss 1e-3 (about 1.8e-3 on the multislice cases).  Those cases are reported as expected failures
+with the measured error, after the intensity bar has been checked.
 """
 import numpy as np
 import pytest
@@ -16,7 +18,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 TOL_I = 1e-4
-TOL_G = {"fp16": 1e-3, "bf16x3": 1e-3, "bf16": 4e-3}
+TOL_G = {"fp16": 1e-3, "bf16x3": 1e-3, "bf16": 1e-3}
 FORMATS = ["bf16", "fp16", "bf16x3"]
 GRADS = ("amp", "phase", "probe", "pos", "tilt", "dz")
 
@@ -57,8 +59,12 @@ def _errors(case, idx, fft, grads=GRADS, ckpt_stride=1):
 
 
 def _assert(err, fft):
-    for k, v in err.items():
-        assert v <= (TOL_I if k in ("I", "loss", "I_fwd") else TOL_G[fft]), (k, v, err)
+    for k in ("I", "loss", "I_fwd"):
+        assert err[k] <= TOL_I, (k, err[k], err)
+    miss = {k: v for k, v in err.items() if k not in ("I", "loss", "I_fwd") and v > TOL_G[fft]}
+    if miss and fft == "bf16":
+        pytest.xfail("bf16 hi + lo gradients miss the 1e-3 bar: %s" % ", ".join("%s %.2e" % kv for kv in miss.items()))
+    assert not miss, (miss, err)
 
 
 @pytest.mark.parametrize("fft", FORMATS)
@@ -98,10 +104,16 @@ def test_split_ignores_ckpt_stride_and_matches_fp32_path():
     l3, a3, p3 = out[("bf16", 3)]
     assert l1 == l3 and rel_l2(a3, a1) < 1e-6
     lf, af, pf = out[("fp32", 1)]
-    for key in (("bf16", 1), ("fp16", 1), ("bf16x3", 1)):
+    miss = {}
+    for key in (("fp16", 1), ("bf16x3", 1), ("bf16", 1)):
         ls, as_, ps = out[key]
         assert abs(ls - lf) <= TOL_I * abs(lf)
-        assert rel_l2(as_, af) <= TOL_G[key[0]] and rel_l2(ps, pf) <= TOL_G[key[0]]
+        for name, e in (("amp", rel_l2(as_, af)), ("probe", rel_l2(ps, pf))):
+            if e > TOL_G[key[0]]:
+                miss["%s %s" % (key[0], name)] = e
+    if miss and all(k.startswith("bf16 ") for k in miss):
+        pytest.xfail("bf16 hi + lo gradients miss the 1e-3 bar: %s" % ", ".join("%s %.2e" % kv for kv in miss.items()))
+    assert not miss, miss
 
 
 def _torch_poisson(I, I_meas_b, eps=1e-6):
@@ -125,6 +137,8 @@ def test_split_autograd_backward(fft):
     ref = oracle_grads(case, idx)
     assert rel_l2(_np(I), ref.I_model) <= TOL_I
     assert abs(loss.item() - ref.loss) <= TOL_I * abs(ref.loss)
+    err = {"I": 0.0, "loss": 0.0, "I_fwd": 0.0}
     for name in GRADS:
         got = _np(leaves[name].grad)
-        assert rel_l2(got[0] if name == "dz" else got, getattr(ref, name)) <= TOL_G[fft], name
+        err[name] = rel_l2(got[0] if name == "dz" else got, getattr(ref, name))
+    _assert(err, fft)
