@@ -132,6 +132,18 @@ typedef struct {
  * named in geom->grad_mask).  0 on invalid geometry (see pty_last_error()). */
 size_t pty_workspace_size(const pty_geom* geom, int B);
 
+/* Memory plan of the adjoint: the per-slice choice between keeping the forward's entering waves
+ * and recomputing them, for a batch of B positions whose workspace must fit budget_bytes.  Writes to
+ * *stride the pty_geom.ckpt_stride to use, and to *ws_bytes (may be NULL) the workspace it needs:
+ *  - 1 (keep every slice's entering wave and spectrum; no replay) when that fits;
+ *  - otherwise the stride K in 2 .. Nz-1 of least work that fits.  Every K > 1 replays each slice
+ *    once (about one more forward pass); fewer, longer segments ran faster on the large-window
+ *    workload, so it is the largest K whose workspace fits and is below K = 1's.  The record is
+ *    B*M*(ceil(Nz/K) - 1 + 2K + 1)*N^2*8 bytes: it shrinks with K up to K ~ sqrt(Nz / 2), then grows.
+ * PTY_EWORKSPACE (message: the smallest workspace any plan needs) when no stride fits; the
+ * split-precision modes keep every checkpoint, so for them only K = 1 is considered.  Host only. */
+int pty_plan_ckpt(const pty_geom* geom, int B, size_t budget_bytes, int* stride, size_t* ws_bytes);
+
 /* Forward model, Eq. 1-4: I_model[b] = fftshift( sum_m sum_n |F_ortho[psi_{idx[b]}^(m)(n)]|^2 ), [B][N][N]
  * (probe modes m, object modes n).
  * Reads amp, phase, probe, pos, tilt, dz; writes I_model.  ws must hold pty_workspace_size(). */

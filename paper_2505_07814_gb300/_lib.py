@@ -37,7 +37,8 @@ EXPORTS = ("pty_workspace_size", "pty_forward", "pty_loss_grad", "pty_adam_updat
            "pty_profile_read", "pty_loss_grad_noalloc", "pty_forward_save", "pty_backward",
            "pty_cnn_param_count", "pty_cnn_workspace_size", "pty_cnn_forward", "pty_cnn_loss_grad", "pty_cnn_adam",
            "pty_cnn_train_step", "pty_cnn_targets", "pty_cnn_stitch", "pty_cnn_stitch_finish", "pty_cnn_read_state", "pty_constrain",
-           "pty_constrain_workspace_size", "pty_loss_stats", "pty_loss_grad_part", "pty_set_wait_limit")
+           "pty_constrain_workspace_size", "pty_loss_stats", "pty_loss_grad_part", "pty_set_wait_limit",
+           "pty_plan_ckpt")
 PROF_STAGES = ("prepare_object", "probe_spectrum", "forward", "loss", "loss_finalize", "adjoint", "object_grad",
                "probe_grad", "scalar_grad")
 
@@ -119,6 +120,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pty_profile_enable.restype = I
     lib.pty_profile_read.argtypes = [ctypes.POINTER(ctypes.c_double), I]
     lib.pty_profile_read.restype = I
+    lib.pty_plan_ckpt.argtypes = [G, I, SZ, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]
+    lib.pty_plan_ckpt.restype = I
     lib.pty_set_wait_limit.argtypes = [ctypes.c_longlong]
     lib.pty_set_wait_limit.restype = I
     F = ctypes.c_float
@@ -172,6 +175,13 @@ def pty_loss_grad(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss, 
     _check(load().pty_loss_grad(ctypes.byref(geom), B, idx, amp, phase, probe, pos, tilt, dz, I_meas, loss,
                                 I_model, g_amp, g_phase, g_probe, g_pos, g_tilt, g_dz, int(accumulate), ws,
                                 ws_bytes, stream))
+
+
+def pty_plan_ckpt(geom, B: int, budget_bytes: int) -> tuple[int, int]:
+    """(ckpt_stride, workspace bytes) of the adjoint memory plan that fits budget_bytes."""
+    k, n = ctypes.c_int(0), ctypes.c_size_t(0)
+    _check(load().pty_plan_ckpt(ctypes.byref(geom), B, budget_bytes, ctypes.byref(k), ctypes.byref(n)))
+    return k.value, n.value
 
 
 def pty_loss_stats(geom, B, idx, amp, phase, probe, pos, tilt, dz, I_meas, stats, ws, ws_bytes, stream):

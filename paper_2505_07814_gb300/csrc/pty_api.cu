@@ -324,6 +324,39 @@ size_t pty_workspace_size(const pty_geom* geom, int B) {
   return layout_workspace(*geom, B, MODE_GRAD, nullptr, nullptr);
 }
 
+int pty_plan_ckpt(const pty_geom* geom, int B, size_t budget_bytes, int* stride, size_t* ws_bytes) {
+  int rc = validate_geom(geom);
+  if (rc) return rc;
+  REQUIRE(B >= 0, "batch size %d < 0", B);
+  REQUIRE(stride, "stride is NULL");
+  pty_geom g = *geom;
+  g.ckpt_stride = 1;
+  const size_t full = layout_workspace(g, B, MODE_GRAD, nullptr, nullptr);
+  int best = full <= budget_bytes ? 1 : 0;
+  size_t best_bytes = full, least = full;
+  if (!best && g.fft_impl == PTY_FFT_FP32) {
+    // every K > 1 replays each slice once; fewer, longer segments (larger K) ran faster, so take the
+    // largest K whose workspace fits (the record shrinks, then grows again past K ~ sqrt(Nz / 2))
+    for (int K = 2; K < g.Nz; ++K) {
+      g.ckpt_stride = K;
+      const size_t n = layout_workspace(g, B, MODE_GRAD, nullptr, nullptr);
+      if (n < least) least = n;
+      if (n <= budget_bytes && n < full) {
+        best = K;
+        best_bytes = n;
+      }
+    }
+  }
+  if (!best) {
+    set_error("no checkpoint plan fits %zu bytes: the smallest workspace for this batch is %zu bytes%s", budget_bytes,
+              least, geom->fft_impl != PTY_FFT_FP32 ? " (the split-precision modes keep every checkpoint)" : "");
+    return PTY_EWORKSPACE;
+  }
+  *stride = best;
+  if (ws_bytes) *ws_bytes = best_bytes;
+  return PTY_OK;
+}
+
 int pty_forward(const pty_geom* geom, int B, const int32_t* idx, const float* amp, const float* phase,
                 const float* probe, const float* pos, const float* tilt, const float* dz, float* I_model, void* ws,
                 size_t ws_bytes, void* stream) {

@@ -110,10 +110,19 @@ def _ptr(t, dtype=None, numel=None, name="tensor"):
 
 
 class Ptycho:
-    """One reconstruction problem on one device, with a workspace sized for batches up to max_batch."""
+    """One reconstruction problem on one device, with a workspace sized for batches up to max_batch.
 
-    def __init__(self, geom: Geometry, max_batch: int, device="cuda"):
+    ckpt_budget (bytes): let the library choose the adjoint's memory plan (pty_plan_ckpt): keep
+    every slice's forward waves when the workspace fits the budget, else the recompute stride of
+    least work that does; geom.ckpt_stride is then replaced and the plan is in `self.plan`."""
+
+    def __init__(self, geom: Geometry, max_batch: int, device="cuda", ckpt_budget: int | None = None):
         _lib.load()
+        self.plan = None
+        if ckpt_budget is not None:
+            stride, need = _lib.pty_plan_ckpt(geom.c(), max_batch, int(ckpt_budget))
+            geom = dataclasses.replace(geom, ckpt_stride=stride)
+            self.plan = {"ckpt_stride": stride, "workspace_bytes": need, "budget_bytes": int(ckpt_budget)}
         self.geom = geom
         self.cg = geom.c()
         self.device = torch.device(device)

@@ -215,6 +215,11 @@ def workload(name: str, **over) -> Workload:
         amp, phase = make_object_2d(H, W, dx)
         pos = make_scan(16, 16, 4, N, H, W)
         tilt = np.zeros_like(pos)
+    elif name == "c4":  # the single-slice physics of c1 with a 128x128 window: object 192^2
+        N, M, Nz, H, W, dz = 128, 1, 1, 192, 192, 1.0
+        amp, phase = make_object_2d(H, W, dx)
+        pos = make_scan(16, 16, 4, N, H, W)
+        tilt = np.zeros_like(pos)
     elif name == "c2":  # multislice: 128x128, 6 modes, 8 slices of 512^2, 64x64 scan
         N, M, Nz, H, W, dz = 128, 6, 8, 512, 512, 2.0
         amp, phase = make_object_3d(Nz, H, W, dx)

@@ -3,20 +3,17 @@
 Multislice workload (N = 128, M = 6, Nz = 8, object 8 x 512 x 512, 4096 positions) with one
 512-position batch, exactly the benchmark's first batch and kernel configuration.  The point of
 evaluation is the workload's own object (not the flat start, where the position, tilt and dz
-gradients vanish), against synthetic measured patterns.
-  * every modelled pattern of the batch and the loss against the oracle (rel. L2 <= 1e-5);
-  * sampled per-position outputs the oracle computes one position at a time: position and tilt
-    gradients of sampled positions, and the object gradient at pixels that only one position of
-    the batch reaches.  With the Poisson loss L = -sum(d log I - I) / sum(d) over the batch, a
-    single-position oracle call differs only in the normaliser, so it is rescaled by
-    sum_j(d) / sum_batch(d) (rel. L2 <= 1e-4);
-  * the gradients that sum over all positions (probe, dz) by central differences of the GPU
-    forward (FP64 loss on the host), h = 1e-3 along a random direction.
+gradients vanish), against synthetic measured patterns.  The oracle runs over the whole batch on
+every host core (tests/oracle_pool.py), and every output is compared element by element: every
+modelled pattern and the loss (rel. L2 <= 1e-5), the whole object amplitude and phase gradients,
+the probe, position and tilt gradients and dz (rel. L2 <= 1e-4).  The probe and dz gradients are
+also checked by central differences of the GPU forward (FP64 loss on the host).
 
 Large-window workload (N = 256 on four-CTA clusters, M = 12, Nz = 20, object 20 x 1024 x 1024):
 the oracle on a 16-position subset for every output, and central differences of 32 entries drawn at
 random from the largest-magnitude gradient entries of each kind (single entries with tiny
-gradients change an FP32 loss by less than its rounding).
+gradients change an FP32 loss by less than its rounding).  The same subset also runs under a
+memory budget below the every-slice record, where the library's plan recomputes segments.
 """
 import numpy as np
 import pytest
@@ -24,17 +21,35 @@ import pytest
 from oracle import ptycho as O
 from paper_2505_07814_gb300 import synth
 from tests.cases import c64, f32, rel_l2
+from tests.oracle_pool import poisson_loss_and_grad
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 NAMES = ("amp", "phase", "probe", "pos", "tilt", "dz")
-# Large-window subset: the object gradients sum conj(psi) g over 16 positions x 12 modes, with g
-# driven by the Poisson weight d / I; on dark-field pixels (I orders of magnitude below the
-# bright field) the FP32 forward's absolute error becomes a large relative error of I that this
-# weight passes on.  Measured: 2.2e-4 on both object gradients here (1.0e-4 with 4 slices, 7.4e-4
-# with 2 modes, where the patterns are darker); every other output stays below 1e-4.
-TOL_C3 = {"amp": 3e-4, "phase": 3e-4}
+# Large-window subset: the object gradients are held to the 1e-4 bar.  They miss it (measured
+# 2.2e-4) and so does any single-precision evaluation of the same formulas: numpy's complex64
+# FFTs give 1.7e-4 on this subset, 1.7e-4 even with the FP64 dL/dI and with the object gradient
+# summed in FP64.  The error is that of the far-field wave on dark-field pixels (intensity 1e-4 of
+# the peak after 20 slices), which the Poisson weight d / I turns into a large part of the adjoint
+# wave.  When the bar is missed the test measures that FP32 floor on the same inputs and reports an
+# expected failure only if the GPU stays within 1.5 x of it.
+FLOOR_FACTOR = 1.5
+
+
+def _object_bar(errs, w, idx, I_meas):
+    """Object gradients against 1e-4; on a miss, the FP32 floor of these inputs decides."""
+    miss = {n: errs[n] for n in ("amp", "phase") if errs[n] > 1e-4}
+    if not miss:
+        return
+    from tests.fp32_floor import object_gradients_fp32
+    ref = errs["_ref"]
+    ga, gp = object_gradients_fp32(_oracle_geom(w), w.amp, w.phase, w.probe, w.pos, w.tilt, w.dz, I_meas, idx)
+    floor = {"amp": rel_l2(ga, ref.amp), "phase": rel_l2(gp, ref.phase)}
+    for n, e in miss.items():
+        assert floor[n] > 1e-4 and e <= FLOOR_FACTOR * floor[n], (n, e, floor)
+    pytest.xfail("object gradients miss 1e-4 (%s); single-precision floor of the same inputs: %s" % (
+        ", ".join("%s %.2e" % kv for kv in miss.items()), ", ".join("%s %.2e" % kv for kv in floor.items())))
 
 
 def _setup(w, idx, B, I_meas):
@@ -90,34 +105,13 @@ def test_multislice_batch_512_matches_oracle():
     torch.cuda.synchronize()
     assert pt.status() == 0
     g = _oracle_geom(w)
-    ref_I = O.model_patterns(g, w.amp, w.phase, w.probe, w.pos, w.tilt, w.dz, idx)
-    assert rel_l2(_np(I_model), ref_I) <= 1e-5
-    ref_loss = O.loss_value(g, ref_I, I_meas[idx])
-    assert abs(loss.item() - ref_loss) <= 1e-5 * abs(ref_loss)
-
-    d_batch = float(I_meas[idx].sum())
-    corners = np.array([O.crop_index(w.pos[j])[0] for j in idx])
-    sampled = [0, 257, 511]
-    got_pt, ref_pt = [], []
-    for j in sampled:
-        r = O.loss_and_grad(g, w.amp, w.phase, w.probe, w.pos, w.tilt, w.dz, I_meas, [j])
-        s = float(I_meas[j].sum()) / d_batch
-        got_pt += [_np(grads.pos)[j], _np(grads.tilt)[j]]
-        ref_pt += [s * r.pos[j], s * r.tilt[j]]
-        if j == 0:
-            # pixels of position 0's window that no other position of the batch reaches
-            cover = np.zeros((w.H, w.W), dtype=np.int32)
-            for c0, c1 in corners:
-                cover[c0:c0 + w.N, c1:c1 + w.N] += 1
-            c0, c1 = corners[0]
-            mask = np.zeros((w.H, w.W), dtype=bool)
-            mask[c0:c0 + w.N, c1:c1 + w.N] = cover[c0:c0 + w.N, c1:c1 + w.N] == 1
-            assert mask.sum() >= 16  # the 4 x 4 corner the raster step leaves to position 0, in every slice
-            for name in ("amp", "phase"):
-                got = _np(getattr(grads, name))[:, mask]
-                exp = s * getattr(r, name)[:, mask]
-                assert rel_l2(got, exp) <= 1e-4, (name, rel_l2(got, exp))
-    assert rel_l2(np.array(got_pt), np.array(ref_pt)) <= 1e-4
+    ref = poisson_loss_and_grad(g, w.amp, w.phase, w.probe, w.pos, w.tilt, w.dz, I_meas, idx)
+    assert rel_l2(_np(I_model), ref.I_model) <= 1e-5
+    assert abs(loss.item() - ref.loss) <= 1e-5 * abs(ref.loss)
+    for name in NAMES:
+        got = _np(getattr(grads, name))
+        err = rel_l2(got[0] if name == "dz" else got, getattr(ref, name))
+        assert err <= 1e-4, (name, err)
 
     # probe and dz: central differences of the GPU forward along random directions
     Im = I_meas[idx].astype(np.float64)
@@ -154,10 +148,29 @@ def test_large_window_subset_matches_oracle_and_differences():
     assert pt.status() == 0
     ref = O.loss_and_grad(g, w.amp, w.phase, w.probe, w.pos, w.tilt, w.dz, I_meas, idx)
     assert abs(loss.item() - ref.loss) <= 1e-5 * abs(ref.loss)
+    errs = {"_ref": ref}
     for n in NAMES:
         got = _np(getattr(grads, n))
+        errs[n] = rel_l2(got[0] if n == "dz" else got, getattr(ref, n))
+        if n not in ("amp", "phase"):
+            assert errs[n] <= 1e-4, (n, errs[n])
+
+    # a memory budget below the every-slice record: the library's plan recomputes segments, with
+    # the same results
+    from paper_2505_07814_gb300.ptycho import Ptycho
+    budget = int(0.6 * pt.ws_bytes)
+    pt2 = Ptycho(pt.geom, B, device="cuda", ckpt_budget=budget)
+    assert pt2.plan["ckpt_stride"] > 1 and pt2.ws_bytes <= budget, pt2.plan
+    loss2, grads2 = pt2.loss_grad(params, idx, I_t)
+    torch.cuda.synchronize()
+    assert pt2.status() == 0
+    assert abs(loss2.item() - ref.loss) <= 1e-5 * abs(ref.loss)
+    for n in NAMES:
+        got = _np(getattr(grads2, n))
         err = rel_l2(got[0] if n == "dz" else got, getattr(ref, n))
-        assert err <= TOL_C3.get(n, 1e-4), (n, err)
+        assert err <= max(1e-4, errs[n] + 2e-5), ("recompute plan", pt2.plan, n, err)
+        assert rel_l2(got, _np(getattr(grads, n))) <= 1e-5, ("plans disagree", n)
+    del pt2
 
     # 32 central differences of the GPU forward (FP64 loss on the host), entries drawn from the
     # largest gradients of each kind.  h = 1e-3 for the object, probe and dz; a single position or
@@ -187,3 +200,4 @@ def test_large_window_subset_matches_oracle_and_differences():
         if abs(fd - an) > 2e-2 * abs(gv) + 1e-9:
             bad.append((name, e, part, fd, an, float(abs(gv))))
     assert not bad, bad
+    _object_bar(errs, w, idx, I_meas)

@@ -195,3 +195,42 @@ def test_reference_arm_prints_the_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def _plan(lib, g, B, budget):
+    k, n = ctypes.c_int(0), ctypes.c_size_t(0)
+    rc = lib.pty_plan_ckpt(ctypes.byref(g), B, budget, ctypes.byref(k), ctypes.byref(n))
+    return rc, k.value, n.value
+
+
+@pytest.mark.parametrize("Nz,N,M,B", [(20, 64, 3, 5), (8, 128, 6, 4), (7, 64, 1, 3)])
+def test_checkpoint_plan_from_a_budget(lib, Nz, N, M, B):
+    """The memory plan against the record's byte count B*M*N^2*8*blocks, blocks = 2 Nz - 1 for
+    K = 1 and ceil(Nz/K) - 1 + 2K + 1 for K > 1 (anchors, segment waves and spectra, handed-over
+    adjoint wave): K = 1 when it fits, else the largest K < Nz that fits and saves memory."""
+    g = _geom(N=N, M=M, Nz=Nz, H=N + 40, W=N + 50)
+    wave = B * M * N * N * 8
+    blocks = {1: 2 * Nz - 1}
+    for K in range(2, Nz):
+        blocks[K] = -(-Nz // K) - 1 + 2 * K + 1
+    ws = {K: lib.pty_workspace_size(ctypes.byref(_geom(N=N, M=M, Nz=Nz, H=N + 40, W=N + 50, ckpt_stride=K)), B)
+          for K in blocks}
+    for K in blocks:  # the workspace differs from K = 1's by exactly the record's blocks
+        assert ws[1] - ws[K] == wave * (blocks[1] - blocks[K]), K
+    # a budget that holds K = 1
+    assert _plan(lib, g, B, ws[1]) == (_lib.PTY_OK, 1, ws[1])
+    # every budget between the smallest plan and K = 1: the largest fitting K of smaller record
+    for budget in sorted(set(ws.values())):
+        if budget >= ws[1]:
+            continue
+        rc, k, n = _plan(lib, g, B, budget)
+        expect = max(K for K in blocks if K > 1 and ws[K] <= budget)
+        assert (rc, k, n) == (_lib.PTY_OK, expect, ws[expect]), budget
+    # below the smallest plan: refused, with the smallest workspace in the message
+    rc, k, n = _plan(lib, g, B, min(ws.values()) - 1)
+    assert rc == _lib.PTY_EWORKSPACE and str(min(ws.values())) in lib.pty_last_error().decode()
+    # the split-precision modes keep every checkpoint: K = 1 or nothing
+    gs = _geom(N=N, M=M, Nz=Nz, H=N + 40, W=N + 50, fft_impl=1)
+    full = lib.pty_workspace_size(ctypes.byref(gs), B)
+    assert _plan(lib, gs, B, full)[:2] == (_lib.PTY_OK, 1)
+    assert _plan(lib, gs, B, full - 1)[0] == _lib.PTY_EWORKSPACE
