@@ -1,11 +1,15 @@
 #!/usr/bin/env python
 """Throughput of one pass of the ptychography hot path: forward model, loss and adjoint.
 
-A step is one pty_loss_grad call over one batch of scan positions of the multislice workload
-(128 x 128 window, 6 probe modes, 8 slices of 512 x 512, 4096 positions, batch 512 positions
-taken as contiguous raster blocks): shifted probes, all transmissions and propagations, the far
-field, the Poisson loss and every gradient (object amplitude and phase, probe, positions, tilts,
-dz).  The metric counts position x mode x slice wavefield updates per second.
+A step is one pty_loss_grad call over one batch of scan positions: shifted probes, all
+transmissions and propagations, the far field, the Poisson loss and every gradient (object
+amplitude and phase, probe, positions, tilts, dz).  The metric counts position x mode x slice
+wavefield updates per second.  The default workload is the largest: 256 x 256 windows (four-CTA
+clusters), 12 probe modes, 20 slices of 1024 x 1024, 16384 positions, batches of 256 positions
+taken as contiguous raster blocks; the 128 x 128 multislice workload (6 modes, 8 slices of
+512 x 512, batches of 512) is timed in the same run and reported under "also".  With several ranks
+each step is the data-parallel step: every rank its own block of positions, an all-reduce of the
+loss statistics and of every gradient.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the host cores on a
@@ -14,6 +18,7 @@ bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -28,17 +33,13 @@ sys.path.insert(0, ROOT)
 
 METRIC = "wavefield updates/s (fwd+adjoint, 1 GB300)"
 UNIT = "position*mode*slice updates/s"
-# name -> (description, default batch).  c2 is the configuration the headline metric is quoted on.
+# name -> (description, default batch).  c3, the largest configuration, is the default.
 WORKLOADS = {
     "c2": ("multislice N=128 M=6 Nz=8, object 8x512x512, 4096 positions", 512),
     "c1": ("single-slice N=64 M=1 Nz=1, object 128x128, 256 positions", 256),
     "c3": ("multislice N=256 M=12 Nz=20, object 20x1024x1024, 16384 positions", 256),
     "paper": ("paper-shaped N=128 M=12 Nz=6, object 6x614x614, 16384 positions", 16),
 }
-
-# FP32 CUDA-core peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz max clock.
-ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2070e6 / 1e12
-
 
 def fft2_flops(N):
     """Nominal 5 n log2 n flops of a complex FFT of n = N^2 points."""
@@ -60,23 +61,23 @@ def flops_per_wave(N, Nz, stage):
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("fft_smem.cuh", "pipeline.cuh"):
+    for f in ("fft_smem.cuh", "fft_cluster.cuh", "pipeline.cuh"):
         with open(os.path.join(ROOT, "paper_2505_07814_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was taken on the
-    current kernel source; None otherwise."""
+def ncu_traffic(kernel, workload, B):
+    """DRAM bytes per launch of `kernel` on `workload` at batch B from the committed ncu summary
+    (profiles/traffic.json), if it was taken on the current kernel source; None otherwise."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    e = d.get(kernel)
-    if not e or e.get("source_hash") != kernel_source_hash():
+    e = d.get(workload, {}).get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash() or e.get("full_batch") != B:
         return None
     return e.get("dram_bytes_per_launch_full_size")
 
@@ -255,7 +256,7 @@ def run_reference(args, rank):
         return
     import numpy as np
 
-    P = 2  # positions per step: a bounded sample of one batch
+    P = 1 if args.workload == "c3" else 2  # positions per step: a bounded sample of one batch
     batches = [batch_indices(k, args.batch, _ntot(args.workload))[:P] for k in range(args.warmup + args.steps)]
     w, amp0, phase0, I_rows, row_of = make_inputs(args.workload, [p for b in batches for p in b])
     from oracle import ptycho as O
@@ -544,13 +545,305 @@ def run_cnn(args):
                       "gpu_launches": launches}), flush=True)
 
 
+def fma_peak_tflops(torch, dev):
+    """Measured FP32 fused-multiply-add throughput of this GPU (pty_fma_probe), TFLOP/s, best of 5."""
+    from paper_2505_07814_gb300 import _lib
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    sink = torch.zeros(1, dtype=torch.float32, device=dev)
+    blocks, iters = 4 * sms, 2048
+    flops = blocks * 512 * iters * 256
+    st = torch.cuda.current_stream(dev).cuda_stream
+    _lib.pty_fma_probe(sink.data_ptr(), blocks, 64, st)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = 0.0
+    for _ in range(5):
+        e0.record()
+        _lib.pty_fma_probe(sink.data_ptr(), blocks, iters, st)
+        e1.record()
+        e1.synchronize()
+        best = max(best, flops / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
+
+
+def alu_peak_tflops(sms, mhz):
+    """FP32 CUDA-core peak from unit counts: SMs x 128 FP32 lanes x 2 flop (FMA) x clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+class Workload:
+    """One workload on this rank's GPU: inputs resident in HBM, the Ptycho problem, the batches this
+    rank takes, and (one GPU) a CUDA graph of each batch's step."""
+
+    def __init__(self, args, name, B, dev, rank, world):
+        import torch
+
+        from paper_2505_07814_gb300.ptycho import Geometry, Params, Ptycho
+        self.name, self.B, self.dev, self.world = name, B, dev, world
+        Ntot = _ntot(name)
+        # weak scaling: every rank its own blocks of B positions (a global batch of world x B); with
+        # more than one rank each step is the data-parallel step (statistics and gradient all-reduce)
+        self.idx_h = rank_batches(rank, world, B, Ntot)
+        w, amp0, phase0, I_rows, row_of = make_inputs(name, [p for b in self.idx_h for p in b])
+        self.w, self.amp0, self.phase0, self.I_rows, self.row_of = w, amp0, phase0, I_rows, row_of
+        f32 = dict(dtype=torch.float32, device=dev)
+        self.params = Params(amp=torch.tensor(amp0, **f32), phase=torch.tensor(phase0, **f32),
+                             probe=torch.tensor(w.probe, dtype=torch.complex64, device=dev),
+                             pos=torch.tensor(w.pos, **f32), tilt=torch.tensor(w.tilt, **f32),
+                             dz=torch.tensor([w.dz], **f32))
+        # measured patterns [Ntot][N][N] on the device; only the rows the timed batches read are filled
+        self.I_meas = torch.zeros((w.Ntot, w.N, w.N), **f32)
+        rows_t = torch.tensor(I_rows, **f32)
+        for p_, r_ in row_of.items():
+            self.I_meas[p_] = rows_t[r_]
+        del rows_t
+        self.idx_t = [torch.tensor(i, dtype=torch.int32, device=dev) for i in self.idx_h]
+        self.geom = Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, Ntot=w.Ntot, dx=w.dx, lam=w.lam, loss="poisson",
+                             ckpt_stride=args.ckpt_stride, fft=args.fft, w_pacbed=args.w_pacbed,
+                             w_sparse=args.w_sparse)
+        self.pt = Ptycho(self.geom, B, device=dev)
+        self.grads = self.params.zeros_like()
+        self.graphs = None
+        self.per_step_launches = None
+
+    def step(self, k, params=None, I_meas=None, grads=None):
+        """One pass over batch k: loss and every gradient (the data-parallel step on several ranks)."""
+        params = params or self.params
+        I_meas = self.I_meas if I_meas is None else I_meas
+        grads = grads or self.grads
+        if self.world == 1:
+            return self.pt.loss_grad(params, self.idx_t[k % 8], I_meas, grads=grads)[0]
+        import torch.distributed as dist
+
+        from paper_2505_07814_gb300 import data_parallel as DP
+        return DP.loss_grad(self.pt, params, self.idx_t[k % 8], I_meas, grads, dist.all_reduce)[0]
+
+    def capture(self, steps):
+        """One CUDA graph per batch (one GPU, FP32 FFTs): replays remove the host launch gaps."""
+        import torch
+
+        from paper_2505_07814_gb300 import _lib
+        self.graphs = []
+        for k in range(min(8, steps)):
+            g_ = torch.cuda.CUDAGraph()
+            c0 = _lib.pty_launch_count()
+            # thread-local capture: other threads may use CUDA meanwhile
+            with torch.cuda.graph(g_, capture_error_mode="thread_local"):
+                self.step(k)
+            self.per_step_launches = _lib.pty_launch_count() - c0  # the library's kernels in one step
+            self.graphs.append(g_)
+        torch.cuda.synchronize()
+
+    def run(self, k):
+        if self.graphs:
+            self.graphs[k % len(self.graphs)].replay()
+        else:
+            self.step(k)
+
+    @property
+    def updates_per_step(self):
+        return self.B * self.w.M * self.w.Nz
+
+
+def time_steps(wl, steps, warmup, graph, flush, clock_id):
+    """Warm-up, then exactly `steps` timed steps (CUDA events on the launching stream, L2 flushed
+    before each outside the events), clocks sampled meanwhile.  Returns (total ms, launches, stage
+    times per call, calls, clock summary)."""
+    import torch
+
+    from paper_2505_07814_gb300 import _lib
+    for k in range(warmup):
+        wl.step(k)
+    torch.cuda.synchronize()
+    assert wl.pt.status() == 0
+    if graph:
+        wl.capture(steps)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    _lib.pty_profile_enable(True)
+    n0 = _lib.pty_launch_count()
+    if wl.world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(clock_id) as clk:
+        for k in range(steps):
+            flush.zero_()
+            starts[k].record()
+            wl.run(k)
+            ends[k].record()
+        torch.cuda.synchronize()
+    if wl.world > 1:
+        dist.barrier()
+    launches = _lib.pty_launch_count() - n0
+    ncalls, stage_ms = _lib.pty_profile_read()
+    _lib.pty_profile_enable(False)
+    if graph:
+        # replays pass neither the host launch counter nor the stage events: count the captured
+        # kernels, and take the stage times from a few eager steps after the timed region
+        launches = wl.per_step_launches * steps
+        _lib.pty_profile_enable(True)
+        for k in range(warmup):
+            flush.zero_()
+            wl.step(k)
+        torch.cuda.synchronize()
+        ncalls, stage_ms = _lib.pty_profile_read()
+        _lib.pty_profile_enable(False)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    return total_ms, launches, stage_ms, ncalls, clk.summary()
+
+
+def roofline_of(wl, args, stage_ms, ncalls, sms, clocks, fma_tflops):
+    """The dominant kernel against the FP32 ALU roofline (the wave never leaves shared memory), or
+    the split-precision GEMMs against the measured bf16 tensor peak."""
+    w, B = wl.w, wl.B
+    if args.fft == "fp32":
+        dom = max(("forward", "adjoint"), key=lambda s: stage_ms[s])
+        avg_ms = stage_ms[dom] / max(ncalls, 1)
+        flops = B * w.M * flops_per_wave(w.N, w.Nz, dom)
+        achieved = flops / (avg_ms / 1e3) / 1e12
+        max_mhz = clocks.get("sm_max_mhz") or 2070.0
+        peak = alu_peak_tflops(sms, max_mhz)
+        traffic = ncu_traffic("k_" + dom, wl.name, B)
+        r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+             "traffic": traffic, "kernel": "k_" + dom, "avg_launch_ms": avg_ms, "flops_per_launch": flops,
+             "peak_source": "%d SMs (device) x 128 FP32 lanes x 2 flop x %.0f MHz max SM clock (derived)" % (
+                 sms, max_mhz)}
+        if clocks.get("sm_mhz"):
+            p2 = alu_peak_tflops(sms, clocks["sm_mhz"])
+            r["peak_at_sampled_clock"] = p2
+            r["frac_at_sampled_clock"] = achieved / p2
+        if fma_tflops:
+            r["measured_fma_peak"] = fma_tflops
+            r["frac_of_measured_fma_peak"] = achieved / fma_tflops
+        return r
+    # split-precision DFTs: 8 Nz GEMMs of [B M N rows x terms 2N] x [terms 2N x 2N] per pass; the
+    # time is the whole forward + adjoint (pointwise stages and operand splits included), so this is
+    # a lower bound on the GEMMs' own rate
+    terms = {"bf16": 3, "fp16": 3, "bf16x3": 6}[args.fft]
+    gemm_flops = 8 * w.Nz * 2.0 * (B * w.M * w.N) * (2 * w.N) * (terms * 2 * w.N)
+    avg_ms = (stage_ms["forward"] + stage_ms["adjoint"]) / max(ncalls, 1)
+    achieved = gemm_flops / (avg_ms / 1e3) / 1e12
+    peak = 1900.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peak = json.load(fh).get("bf16_tflops") or peak
+    except (OSError, ValueError):
+        pass
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "k_gemm_tc (every DFT GEMM of the pass)", "avg_pass_ms": avg_ms,
+            "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; fp16 taken equal)"}
+
+
+def end_to_end(wl, e_steps, flush):
+    """The metric end to end through the public API from pinned host buffers: every step copies its
+    inputs in (every parameter and the batch's measured patterns) and every gradient and the loss
+    out.  The copies run on a second stream into double buffers, so that step k + 1's inputs and
+    step k's outputs move while the next step computes; the timed region spans all e_steps steps,
+    with the L2 flush before each step timed separately and taken out."""
+    import torch
+    params, grads, I_meas, w = wl.params, wl.grads, wl.I_meas, wl.w
+    names = ("amp", "phase", "probe", "pos", "tilt", "dz")
+    host = {n: getattr(params, n).cpu().pin_memory() for n in names}
+    h_rows = torch.tensor(wl.I_rows).pin_memory()
+    h_grads = [{n: torch.empty_like(getattr(grads, n), device="cpu").pin_memory() for n in names} for _ in range(2)]
+    h_loss = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
+    d_params = [params, params.zeros_like()]
+    d_grads = [grads, params.zeros_like()]
+    d_meas = [I_meas, torch.zeros_like(I_meas)]
+    d_loss = [torch.zeros(1, dtype=torch.float64, device=wl.dev) for _ in range(2)]
+    comp = torch.cuda.current_stream(wl.dev)
+    cs = torch.cuda.Stream(device=wl.dev)
+    in_ready, comp_done, out_done = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
+    h2d = sum(host[n].numel() * host[n].element_size() for n in names)
+    h2d += sum((hi - lo) * w.N * w.N * 4 for lo, hi in row_runs(wl.idx_h[0]))
+    d2h = sum(h_grads[0][n].numel() * h_grads[0][n].element_size() for n in names) + 8
+
+    def issue_inputs(k):
+        j = k % 2
+        if k >= 2:
+            cs.wait_event(comp_done[j])  # step k - 2 is done with buffer j
+        with torch.cuda.stream(cs):
+            for n in names:
+                getattr(d_params[j], n).copy_(host[n], non_blocking=True)
+            for lo, hi in row_runs(wl.idx_h[k % 8]):  # the measured patterns this batch reads
+                r0 = wl.row_of[lo]
+                d_meas[j][lo:hi].copy_(h_rows[r0:r0 + hi - lo], non_blocking=True)
+        in_ready[j].record(cs)
+
+    es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e_steps)]
+    torch.cuda.synchronize()
+    es.record(comp)
+    issue_inputs(0)
+    for k in range(e_steps):
+        j = k % 2
+        if k + 1 < e_steps:
+            issue_inputs(k + 1)
+        fl[k][0].record(comp)
+        flush.zero_()
+        fl[k][1].record(comp)
+        comp.wait_event(in_ready[j])
+        if k >= 2:
+            comp.wait_event(out_done[j])  # step k - 2's gradients have left buffer j
+        loss = wl.step(k, d_params[j], d_meas[j], d_grads[j])
+        d_loss[j].copy_(loss)
+        comp_done[j].record(comp)
+        cs.wait_event(comp_done[j])
+        with torch.cuda.stream(cs):
+            for n in names:
+                h_grads[j][n].copy_(getattr(d_grads[j], n), non_blocking=True)
+            h_loss[j].copy_(d_loss[j], non_blocking=True)
+        out_done[j].record(cs)
+    for j in range(2):
+        comp.wait_event(out_done[j])
+    ee.record(comp)
+    ee.synchronize()
+    e2e_ms = es.elapsed_time(ee) - sum(a.elapsed_time(b) for a, b in fl)
+    assert wl.pt.status() == 0
+    for n in names:  # the last step's gradients reached the host
+        assert torch.equal(h_grads[(e_steps - 1) % 2][n], getattr(d_grads[(e_steps - 1) % 2], n).cpu())
+    return e2e_ms, h2d, d2h
+
+
+def cpu_baseline(args, wl):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload (one host core; the
+    same on every core as context)."""
+    w = wl.w
+    P, dt = cpu_oracle_sample(w, wl.amp0, wl.phase0, _Rows(wl.I_rows, wl.row_of), wl.idx_h[0], args.cpu_seconds)
+    cpu = {"value": P * w.M * w.Nz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": "FP64 numpy oracle, loss + all gradients for the first %d positions of one %d-position "
+                     "batch (%d updates, %.1f s, single-threaded pocketfft)" % (P, wl.B, P * w.M * w.Nz, dt)}
+    try:  # the same oracle on every host core (context; the single-core figure above is the baseline)
+        Pa, dta, procs = cpu_oracle_all_cores(wl.name, wl.idx_h[0], dt / P, args.cpu_seconds / 3)
+        cpu["all_cores"] = {"value": Pa * w.M * w.Nz / dta, "cores": procs,
+                            "sample": "%d positions of the same batch, one per task, %d spawn-started processes, "
+                                      "%.1f s" % (Pa, procs, dta)}
+    except Exception as e:  # a host without process pools still gets its single-core line
+        cpu["all_cores"] = {"unavailable": str(e)[:200]}
+    return cpu
+
+
+def config_of(args, wl):
+    w, B = wl.w, wl.B
+    return {"workload": "%s, batch %d" % (WORKLOADS[wl.name][0], B), "N": w.N, "M": w.M, "Nz": w.Nz,
+            "positions": w.Ntot, "batch": B, "ckpt_stride": args.ckpt_stride, "fft": args.fft,
+            "w_pacbed": args.w_pacbed, "w_sparse": args.w_sparse, "checkpoint_bytes": wl.geom.checkpoint_bytes(B),
+            "object": [w.Nz, w.H, w.W], "loss": "poisson", "grads": "amp,phase,probe,pos,tilt,dz",
+            "batches": "contiguous raster blocks", "start": "flat object (amp 1, phase U[0,1e-8])",
+            "l2": "flushed before every step (256 MiB write outside the step events)",
+            "parallelism": "dp%d" % wl.world, "cuda_graph": bool(wl.graphs)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
+    ap.add_argument("--also", default="c2",
+                    help="comma-separated workloads also timed (device only) in the same run and reported under "
+                         "'also' ('' for none)")
     ap.add_argument("--batch", type=int, default=0, help="positions per step (0: the workload's default)")
     ap.add_argument("--ckpt-stride", type=int, default=1, help="adjoint memory plan (pty_geom.ckpt_stride)")
     ap.add_argument("--fft", default="fp32", choices=["fp32", "bf16", "fp16", "bf16x3"],
@@ -558,7 +851,7 @@ def main():
     ap.add_argument("--sweep-ckpt", default="", help="comma-separated strides: print one timing line per stride")
     ap.add_argument("--eager", dest="graph", action="store_false",
                     help="launch every step's kernels from the host instead of replaying a CUDA graph captured "
-                         "once per batch (the default)")
+                         "once per batch (the default on one GPU)")
     ap.add_argument("--sweep-shape", action="store_true",
                     help="step time against batch size, probe modes and slices (one line per point)")
     ap.add_argument("--e2e-steps", type=int, default=20)
@@ -590,7 +883,6 @@ def main():
         run_reference(args, rank)
         return
 
-    import numpy as np
     import torch
 
     from paper_2505_07814_gb300 import _lib, build
@@ -605,236 +897,63 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     build.build()
     _lib.load()
-
-    B = args.batch
-    Ntot = _ntot(args.workload)
-    # each rank takes its own batches (weak scaling: independent position blocks, no collective)
-    idx_h = rank_batches(rank, world, B, Ntot)
-    w, amp0, phase0, I_rows, row_of = make_inputs(args.workload, [p for b in idx_h for p in b])
-    f32 = dict(dtype=torch.float32, device=dev)
-    params = Params(amp=torch.tensor(amp0, **f32), phase=torch.tensor(phase0, **f32),
-                    probe=torch.tensor(w.probe, dtype=torch.complex64, device=dev), pos=torch.tensor(w.pos, **f32),
-                    tilt=torch.tensor(w.tilt, **f32), dz=torch.tensor([w.dz], **f32))
-    # measured patterns [Ntot][N][N] on the device; only the rows the timed batches read are filled
-    I_meas = torch.zeros((w.Ntot, w.N, w.N), **f32)
-    rows_t = torch.tensor(I_rows, **f32)
-    for p_, r_ in row_of.items():
-        I_meas[p_] = rows_t[r_]
-    del rows_t
-    idx_t = [torch.tensor(i, dtype=torch.int32, device=dev) for i in idx_h]
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # 256 MiB > 129 MB L2
 
-    def geometry(stride):
-        return Geometry(N=w.N, M=w.M, Nz=w.Nz, H=w.H, W=w.W, Ntot=w.Ntot, dx=w.dx, lam=w.lam, loss="poisson",
-                        ckpt_stride=stride, fft=args.fft, w_pacbed=args.w_pacbed, w_sparse=args.w_sparse)
-
-    if args.sweep_ckpt:
-        sweep_ckpt(args, w, geometry, params, I_meas, idx_t, flush, dev, torch, Ptycho)
+    if args.sweep_ckpt or args.constrain or args.sweep_shape:
+        wl = Workload(args, args.workload, args.batch, dev, rank, world)
+        geometry = lambda K: dataclasses.replace(wl.geom, ckpt_stride=K)  # noqa: E731
+        if args.sweep_ckpt:
+            sweep_ckpt(args, wl.w, geometry, wl.params, wl.I_meas, wl.idx_t, flush, dev, torch, Ptycho)
+        elif args.constrain:
+            run_constrain(args, wl.w, geometry(1), wl.params, flush, torch, Ptycho)
+        else:
+            sweep_shape(args, wl.w, wl.amp0, wl.phase0, wl.I_meas, wl.idx_t, flush, dev, torch, Geometry, Params,
+                        Ptycho)
         return
-    if args.constrain:
-        run_constrain(args, w, geometry(1), params, flush, torch, Ptycho)
-        return
-    if args.sweep_shape:
-        sweep_shape(args, w, amp0, phase0, I_meas, idx_t, flush, dev, torch, Geometry, Params, Ptycho)
-        return
-    geom = geometry(args.ckpt_stride)
-    pt = Ptycho(geom, B, device=dev)
-    grads = params.zeros_like()
 
-    for k in range(args.warmup):
-        pt.loss_grad(params, idx_t[k % 8], I_meas, grads=grads)
-    torch.cuda.synchronize()
-    assert pt.status() == 0
-
-    def run_step(k):
-        pt.loss_grad(params, idx_t[k % 8], I_meas, grads=grads)
-
-    per_step_launches = None
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clock_id = gpu_smi_id(torch, dev)
+    graph = args.graph and args.fft == "fp32" and world == 1
     # (the split-precision forms keep the eager path: their first call on a device builds DFT tables)
-    args.graph = args.graph and args.fft == "fp32"
-    if args.graph:  # one graph per batch of positions, captured after the warm-up
-        graphs = []
-        for k in range(min(8, args.steps)):
-            g_ = torch.cuda.CUDAGraph()
-            c0 = _lib.pty_launch_count()
-            # thread-local capture: other threads (NCCL's, under torchrun) may use CUDA meanwhile
-            with torch.cuda.graph(g_, capture_error_mode="thread_local"):
-                run_step(k)
-            per_step_launches = _lib.pty_launch_count() - c0  # the library's kernels in one step
-            graphs.append(g_)
-        torch.cuda.synchronize()
-
-        def run_step(k):  # noqa: F811
-            graphs[k % len(graphs)].replay()
-
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    _lib.pty_profile_enable(True)
-    n0 = _lib.pty_launch_count()
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(gpu_smi_id(torch, dev)) as clk:
-        for k in range(args.steps):
-            flush.zero_()
-            starts[k].record()
-            run_step(k)
-            ends[k].record()
-        torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
-    launches = _lib.pty_launch_count() - n0
-    ncalls, stage_ms = _lib.pty_profile_read()
-    _lib.pty_profile_enable(False)
-    if args.graph:
-        # replays do not pass through the host launch counter or the stage events: count the
-        # captured kernels, and take the stage times from a few eager steps after the timed region
-        launches = per_step_launches * args.steps
-        _lib.pty_profile_enable(True)
-        for k in range(args.warmup):
-            flush.zero_()
-            pt.loss_grad(params, idx_t[k % 8], I_meas, grads=grads)
-        torch.cuda.synchronize()
-        ncalls, stage_ms = _lib.pty_profile_read()
-        _lib.pty_profile_enable(False)
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    total_ms = sum(step_ms)
+    wl = Workload(args, args.workload, args.batch, dev, rank, world)
+    total_ms, launches, stage_ms, ncalls, clocks = time_steps(wl, args.steps, args.warmup, graph, flush, clock_id)
     if world > 1:
         total_ms = max_over_ranks(total_ms, dist, dev)
-    upd_step = B * w.M * w.Nz
-    value = world * upd_step * args.steps / (total_ms / 1e3)
-
-    if args.fft == "fp32":
-        # dominant kernel and its roofline (FP32 ALU bound: the wave never leaves shared memory)
-        dom = max(("forward", "adjoint"), key=lambda s: stage_ms[s])
-        avg_ms = stage_ms[dom] / max(ncalls, 1)
-        flops = B * w.M * flops_per_wave(w.N, w.Nz, dom)
-        achieved = flops / (avg_ms / 1e3) / 1e12
-        # ncu DRAM bytes exist for the 512-position multislice launch only (profiles/traffic.json)
-        traffic = ncu_traffic("k_" + dom) if (args.workload == "c2" and B == 512) else None
-        roofline = {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": achieved / ALU_PEAK_TFLOPS, "traffic": traffic, "kernel": "k_" + dom,
-                    "avg_launch_ms": avg_ms, "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2070 MHz (derived)"}
-    else:
-        # split-precision DFTs: 8 Nz GEMMs of [B M N rows x terms 2N] x [terms 2N x 2N] per pass;
-        # the time is the whole forward + adjoint (pointwise stages and operand splits included),
-        # so this is a lower bound on the GEMMs' own rate
-        terms = {"bf16": 3, "fp16": 3, "bf16x3": 6}[args.fft]
-        gemm_flops = 8 * w.Nz * 2.0 * (B * w.M * w.N) * (2 * w.N) * (terms * 2 * w.N)
-        avg_ms = (stage_ms["forward"] + stage_ms["adjoint"]) / max(ncalls, 1)
-        achieved = gemm_flops / (avg_ms / 1e3) / 1e12
-        peak = 1900.0
-        try:
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
-                peak = json.load(fh).get("bf16_tflops") or peak
-        except (OSError, ValueError):
-            pass
-        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                    "traffic": None, "kernel": "k_gemm_tc (every DFT GEMM of the pass)", "avg_pass_ms": avg_ms,
-                    "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; fp16 taken equal)"}
+    value = world * wl.updates_per_step * args.steps / (total_ms / 1e3)
+    fma = fma_peak_tflops(torch, dev) if rank == 0 else None
+    roofline = roofline_of(wl, args, stage_ms, ncalls, sms, clocks, fma)
     stages = {k: v / max(ncalls, 1) for k, v in stage_ms.items()}
-
-    # end to end through the public API from pinned host buffers: every step copies its inputs in
-    # (every parameter and the batch's measured patterns) and every gradient and the loss out.  The
-    # copies run on a second stream into double buffers, so that step k + 1's inputs and step k's
-    # outputs move while the next step computes; the timed region spans all e_steps steps, with the
-    # L2 flush before each step timed separately and taken out.
-    names = ("amp", "phase", "probe", "pos", "tilt", "dz")
-    host = {n: getattr(params, n).cpu().pin_memory() for n in names}
-    h_rows = torch.tensor(I_rows).pin_memory()
-    h_grads = [{n: torch.empty_like(getattr(grads, n), device="cpu").pin_memory() for n in names} for _ in range(2)]
-    h_loss = [torch.empty(1, dtype=torch.float64).pin_memory() for _ in range(2)]
-    d_params = [params, params.zeros_like()]
-    d_grads = [grads, params.zeros_like()]
-    d_meas = [I_meas, torch.zeros_like(I_meas)]
-    d_loss = [torch.zeros(1, dtype=torch.float64, device=dev) for _ in range(2)]
-    comp = torch.cuda.current_stream(dev)
-    cs = torch.cuda.Stream(device=dev)
-    in_ready, comp_done, out_done = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
     e_steps = min(args.e2e_steps, args.steps)
-    h2d = sum(host[n].numel() * host[n].element_size() for n in names)
-    h2d += sum((hi - lo) * w.N * w.N * 4 for lo, hi in row_runs(idx_h[0]))
-    d2h = sum(h_grads[0][n].numel() * h_grads[0][n].element_size() for n in names) + 8
+    e2e_ms, h2d, d2h = end_to_end(wl, e_steps, flush)
+    if world > 1:
+        e2e_ms = max_over_ranks(e2e_ms, dist, dev)
+    e2e_value = world * wl.updates_per_step * e_steps / (e2e_ms / 1e3)
+    cpu = cpu_baseline(args, wl) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    config = config_of(args, wl)
 
-    def issue_inputs(k):
-        j = k % 2
-        if k >= 2:
-            cs.wait_event(comp_done[j])  # step k - 2 is done with buffer j
-        with torch.cuda.stream(cs):
-            for n in names:
-                getattr(d_params[j], n).copy_(host[n], non_blocking=True)
-            for lo, hi in row_runs(idx_h[k % 8]):  # the measured patterns this batch reads
-                r0 = row_of[lo]
-                d_meas[j][lo:hi].copy_(h_rows[r0:r0 + hi - lo], non_blocking=True)
-        in_ready[j].record(cs)
-
-    es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    fl = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(e_steps)]
-    torch.cuda.synchronize()
-    es.record(comp)
-    issue_inputs(0)
-    for k in range(e_steps):
-        j = k % 2
-        if k + 1 < e_steps:
-            issue_inputs(k + 1)
-        fl[k][0].record(comp)
-        flush.zero_()
-        fl[k][1].record(comp)
-        comp.wait_event(in_ready[j])
-        if k >= 2:
-            comp.wait_event(out_done[j])  # step k - 2's gradients have left buffer j
-        loss, _ = pt.loss_grad(d_params[j], idx_t[k % 8], d_meas[j], grads=d_grads[j])
-        d_loss[j].copy_(loss)
-        comp_done[j].record(comp)
-        cs.wait_event(comp_done[j])
-        with torch.cuda.stream(cs):
-            for n in names:
-                h_grads[j][n].copy_(getattr(d_grads[j], n), non_blocking=True)
-            h_loss[j].copy_(d_loss[j], non_blocking=True)
-        out_done[j].record(cs)
-    for j in range(2):
-        comp.wait_event(out_done[j])
-    ee.record(comp)
-    ee.synchronize()
-    e2e_ms = es.elapsed_time(ee) - sum(a.elapsed_time(b) for a, b in fl)
-    assert pt.status() == 0
-    for n in names:  # the last step's gradients reached the host
-        assert torch.equal(h_grads[(e_steps - 1) % 2][n], getattr(d_grads[(e_steps - 1) % 2], n).cpu())
-    e2e_value = world * upd_step * e_steps / (e2e_ms / 1e3)
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        P, dt = cpu_oracle_sample(w, amp0, phase0, _Rows(I_rows, row_of), idx_h[0], args.cpu_seconds)
-        cpu = {"value": P * w.M * w.Nz / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "FP64 numpy oracle, loss + all gradients for the first %d positions of one %d-position "
-                         "batch (%d updates, %.1f s, single-threaded pocketfft)" % (P, B, P * w.M * w.Nz, dt)}
-        try:  # the same oracle on every host core (context; the single-core figure above is the baseline)
-            Pa, dta, procs = cpu_oracle_all_cores(args.workload, idx_h[0], dt / P, args.cpu_seconds / 3)
-            cpu["all_cores"] = {"value": Pa * w.M * w.Nz / dta, "cores": procs,
-                                "sample": "%d positions of the same batch, one per task, %d spawn-started processes, "
-                                          "%.1f s" % (Pa, procs, dta)}
-        except Exception as e:  # a host without process pools still gets its single-core line
-            cpu["all_cores"] = {"unavailable": str(e)[:200]}
+    also = {}
+    for name in [a for a in args.also.split(",") if a and a != args.workload]:
+        del wl
+        torch.cuda.empty_cache()
+        wl = Workload(args, name, WORKLOADS[name][1], dev, rank, world)
+        t_ms, l_, st_ms, nc, clk2 = time_steps(wl, args.steps, args.warmup, graph, flush, clock_id)
+        if world > 1:
+            t_ms = max_over_ranks(t_ms, dist, dev)
+        also[name] = {"value": world * wl.updates_per_step * args.steps / (t_ms / 1e3), "unit": UNIT,
+                      "ms_per_step": t_ms / args.steps, "steps": args.steps, "gpu_launches": l_,
+                      "config": config_of(args, wl), "roofline": roofline_of(wl, args, st_ms, nc, sms, clk2, fma),
+                      "stage_ms_per_call": {k: v / max(nc, 1) for k, v in st_ms.items()}, "clocks": clk2}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None,
                 "dtype": "f32" if args.fft == "fp32" else "f32 (DFTs: %s split, f32 accumulate)" % args.fft,
-                "data": "synthetic",
-                "config": {"workload": "%s, batch %d" % (WORKLOADS[args.workload][0], B), "N": w.N, "M": w.M,
-                           "Nz": w.Nz, "positions": w.Ntot, "batch": B, "ckpt_stride": args.ckpt_stride,
-                           "fft": args.fft, "w_pacbed": args.w_pacbed, "w_sparse": args.w_sparse,
-                           "checkpoint_bytes": geom.checkpoint_bytes(B),
-                           "object": [w.Nz, w.H, w.W], "loss": "poisson", "grads": "amp,phase,probe,pos,tilt,dz",
-                           "batches": "contiguous raster blocks", "start": "flat object (amp 1, phase U[0,1e-8])",
-                           "l2": "flushed before every step (256 MiB write outside the step events)",
-                           "parallelism": "dp%d" % world, "cuda_graph": bool(args.graph)},
-                "roofline": roofline, "stage_ms_per_call": stages,
+                "data": "synthetic", "config": config, "roofline": roofline, "stage_ms_per_call": stages,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "steps": e_steps, "copies": "pinned host buffers, second stream, double-buffered "
                         "(inputs of step k+1 and outputs of step k overlap the next step's compute)"},
-                "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clk.summary()}
+                "cpu_baseline": cpu, "gpu_launches": launches, "clocks": clocks, "also": also}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

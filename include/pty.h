@@ -327,6 +327,12 @@ int pty_profile_read(double* ms, int n);
 #define PTY_WAIT_POLLS_DEFAULT (1LL << 24)
 int pty_set_wait_limit(long long polls);
 
+/* Diagnostics: FP32 fused-multiply-add throughput of this GPU, the measured denominator of the
+ * ALU roofline.  Launches `blocks` CTAs of 512 threads on `stream`; each thread runs iters x 128
+ * independent FMAs (eight chains), so a launch does blocks x 512 x iters x 256 flops.  sink: a
+ * device float that is never written in practice.  Time it with events on the stream. */
+int pty_fma_probe(float* sink, int blocks, int iters, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

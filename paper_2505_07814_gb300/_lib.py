@@ -38,7 +38,7 @@ EXPORTS = ("pty_workspace_size", "pty_forward", "pty_loss_grad", "pty_adam_updat
            "pty_cnn_param_count", "pty_cnn_workspace_size", "pty_cnn_forward", "pty_cnn_loss_grad", "pty_cnn_adam",
            "pty_cnn_train_step", "pty_cnn_targets", "pty_cnn_stitch", "pty_cnn_stitch_finish", "pty_cnn_read_state", "pty_constrain",
            "pty_constrain_workspace_size", "pty_loss_stats", "pty_loss_grad_part", "pty_set_wait_limit",
-           "pty_plan_ckpt")
+           "pty_plan_ckpt", "pty_fma_probe")
 PROF_STAGES = ("prepare_object", "probe_spectrum", "forward", "loss", "loss_finalize", "adjoint", "object_grad",
                "probe_grad", "scalar_grad")
 
@@ -122,6 +122,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.pty_profile_read.restype = I
     lib.pty_plan_ckpt.argtypes = [G, I, SZ, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_size_t)]
     lib.pty_plan_ckpt.restype = I
+    lib.pty_fma_probe.argtypes = [P, I, I, P]
+    lib.pty_fma_probe.restype = I
     lib.pty_set_wait_limit.argtypes = [ctypes.c_longlong]
     lib.pty_set_wait_limit.restype = I
     F = ctypes.c_float
@@ -246,6 +248,10 @@ def pty_profile_read() -> tuple[int, dict]:
     if n < 0:
         raise PtyError(PTY_ECUDA, "profile read failed")
     return n, {name: buf[k] for k, name in enumerate(PROF_STAGES)}
+
+
+def pty_fma_probe(sink, blocks: int, iters: int, stream):
+    _check(load().pty_fma_probe(sink, blocks, iters, stream))
 
 
 def pty_set_wait_limit(polls: int):

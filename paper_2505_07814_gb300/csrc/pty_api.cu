@@ -313,6 +313,27 @@ static int grad_call(Problem& pb, const pty_geom* geom, int B, const float* I_me
   return dispatch(pb);
 }
 
+// FP32 FMA throughput probe: eight independent chains per thread, 16 fused multiply-adds of each
+// per iteration.  The result is stored only if it equals a value it never takes, so the work is
+// not optimised away and nothing is written.
+__global__ void __launch_bounds__(512) k_fma_probe(float* sink, int iters) {
+  float a[8];
+#pragma unroll
+  for (int c = 0; c < 8; ++c) a[c] = (float)(threadIdx.x + c);
+  const float b = 0.999f, d = 0.001f;
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+#pragma unroll
+      for (int c = 0; c < 8; ++c) a[c] = fmaf(a[c], b, d);
+    }
+  }
+  float r = 0.f;
+#pragma unroll
+  for (int c = 0; c < 8; ++c) r += a[c];
+  if (r == -1.0f) sink[0] = r;
+}
+
 }  // namespace pty
 
 using namespace pty;
@@ -590,6 +611,18 @@ int pty_loss_grad_noalloc(const pty_geom* geom, int B, const int32_t* idx, const
 }
 
 long long pty_launch_count(void) { return __atomic_load_n(&g_launches, __ATOMIC_RELAXED); }
+
+int pty_fma_probe(float* sink, int blocks, int iters, void* stream) {
+  REQUIRE(sink && blocks > 0 && iters > 0, "pty_fma_probe: sink NULL or blocks / iters <= 0");
+  k_fma_probe<<<blocks, 512, 0, (cudaStream_t)stream>>>(sink, iters);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_error("k_fma_probe launch failed: %s", cudaGetErrorString(e));
+    return PTY_ECUDA;
+  }
+  note_launch();
+  return PTY_OK;
+}
 
 int pty_set_wait_limit(long long polls) {
   g_stage_spin = polls < 0 ? -1 : (long)(polls < PTY_WAIT_POLLS_DEFAULT ? polls : PTY_WAIT_POLLS_DEFAULT);
