@@ -58,6 +58,12 @@
 #ifndef PTY_FWD_PF
 #define PTY_FWD_PF 0
 #endif
+// Adjoint L1 prefetch: > 0 prefetches the first PTY_ADJ_L1PF KB of each checkpoint and spectrum
+// block into L1 (prefetch.global.L1, one 128-byte line per thread) two transform steps before the
+// pass that reads it, so that those loads hit the SM's own cache; 0: off.
+#ifndef PTY_ADJ_L1PF
+#define PTY_ADJ_L1PF 0
+#endif
 // 1: the adjoint reads checkpoints and spectra with evict-first (streaming) loads, so they do not
 // displace the transmission and its gradient accumulator from L2 (adjoint 3.685 -> 3.655 ms)
 #ifndef PTY_ADJ_LDCS
@@ -303,6 +309,11 @@ __device__ __forceinline__ void prefetch_l2(const void* p, size_t bytes) {
   const uintptr_t a = (uintptr_t)p & ~(uintptr_t)15;
   const uintptr_t e = ((uintptr_t)p + bytes + 15) & ~(uintptr_t)15;
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"((unsigned)(e - a)) : "memory");
+}
+// L1 prefetch of the first `bytes` of a block, one 128-byte line per thread and pass.
+__device__ __forceinline__ void prefetch_l1(const void* base, int bytes) {
+  for (int l = threadIdx.x * 128; l < bytes; l += blockDim.x * 128)
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(base) + l));
 }
 // Rows [0, N) of an N-wide patch with row stride W (elements), one row per thread tid < N.
 template <int N>
@@ -1302,6 +1313,9 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
 
   build_twiddles<N>(tw);
   adj_tables<N>(cm0, cm1, cr0, cr1, e0, e1, c0, c1, f0, f1, d0, d1, th0, th1, dz, a.dx, a.lam);
+#if PTY_ADJ_L1PF
+  if (want_obj) prefetch_l1(ck_base + (size_t)(a.s1 - 1) * NN, PTY_ADJ_L1PF * 1024);
+#endif
   __syncthreads();
 
   if (a.s1 == a.Nz) {
@@ -1342,6 +1356,9 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
         if (tid == 0 && !(sst >> 31) && want_prop && sl > 0)
           stage_issue(sbar, stg, vh_base + (size_t)(sl - 1) * NN, kStageBytes);
       }
+#if PTY_ADJ_L1PF
+      if (want_prop && sl > 0) prefetch_l1(vh_base + (size_t)(sl - 1) * NN, PTY_ADJ_L1PF * 1024);
+#endif
       F::col_fwd(s, tw, none);
 #else
       F::template col_inv_fwd<true>(s, tw, trans);
@@ -1363,6 +1380,9 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
           if (tid == 0 && !(sst >> 31) && want_obj && sl - 1 >= a.s0)
             stage_issue(sbar, stg, ck_base + (size_t)(sl - 1) * NN, kStageBytes);
         }
+#if PTY_ADJ_L1PF
+        if (want_obj && sl - 1 >= a.s0) prefetch_l1(ck_base + (size_t)(sl - 1) * NN, PTY_ADJ_L1PF * 1024);
+#endif
         F::row_inv(s, tw, none);
 #else
         F::row_fwd_inv(s, tw, prop);
