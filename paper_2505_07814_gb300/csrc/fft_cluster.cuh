@@ -22,7 +22,15 @@
 
 #include "fft_smem.cuh"
 
+// Tasks of the cross-CTA step unrolled together (each thread runs eight; unrolling lets the loads of
+// several tasks, remote and in a hook, be in flight at once).
+#ifndef PTY_C1_UNROLL
+#define PTY_C1_UNROLL 1
+#endif
+
 namespace pty {
+
+constexpr int kC1Unroll = PTY_C1_UNROLL;
 
 template <int T>
 struct Fft2<256, T> {
@@ -56,7 +64,7 @@ struct Fft2<256, T> {
 #pragma unroll
     for (int r = 0; r < 4; ++r) rem[r] = remote(s, r);
     cluster_sync();
-#pragma unroll 1
+#pragma unroll kC1Unroll
     for (int i = 0; i < 8; ++i) {
       const int t = threadIdx.x + i * T;
       const int c = 64 * q + t % 64, n2 = t / 64;

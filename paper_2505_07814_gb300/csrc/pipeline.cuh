@@ -36,6 +36,15 @@
 #ifndef PTY_ADJ_SPLIT_ROW
 #define PTY_ADJ_SPLIT_ROW 1
 #endif
+// The same two choices for the N = 256 cluster adjoint.  Its column step is the cross-CTA step, so
+// a separate transmission pass costs a second pass through distributed shared memory per slice;
+// its tasks are small (4 and 16 elements), so the fused hooks hold few registers.
+#ifndef PTY_ADJ256_SPLIT_COL
+#define PTY_ADJ256_SPLIT_COL 0
+#endif
+#ifndef PTY_ADJ256_SPLIT_ROW
+#define PTY_ADJ256_SPLIT_ROW 0
+#endif
 #ifndef PTY_FWD_SPLIT_COL
 #define PTY_FWD_SPLIT_COL 0
 #endif
@@ -1094,6 +1103,16 @@ template <int N, int T>
 __host__ __device__ constexpr bool adj_staged() {
   return PTY_ADJ_STAGE && N == 128 && PTY_ADJ_SPLIT_COL && PTY_ADJ_SPLIT_ROW;
 }
+// Whether the adjoint's transmission (COL) and propagation (ROW) steps run as their own pointwise
+// passes (true) or inside the neighbouring transform steps (false), per window size.
+template <int N>
+__host__ __device__ constexpr bool adj_split_col() {
+  return N == 256 ? PTY_ADJ256_SPLIT_COL != 0 : PTY_ADJ_SPLIT_COL != 0;
+}
+template <int N>
+__host__ __device__ constexpr bool adj_split_row() {
+  return N == 256 ? PTY_ADJ256_SPLIT_ROW != 0 : PTY_ADJ_SPLIT_ROW != 0;
+}
 constexpr int kStageBytes = 64 * 1024;
 // Byte offset of the stage in the adjoint's shared memory: after the wave, the tables and the
 // reduction slots of up to 1024 threads, so that it does not depend on the CTA size.
@@ -1343,7 +1362,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
     AdjTransLoad<N> trans{a.T + sl * plane + patch, a.gT + sl * plane + patch,
                           want_obj ? ck_base + (size_t)sl * NN : nullptr, a.W};
     if (sl > 0 || want_probe || want_pos) {  // (sl > 0: propagate back into slice sl - 1)
-#if PTY_ADJ_SPLIT_COL
+      if constexpr (adj_split_col<N>()) {
       // column inverse, then the transmission step as its own pass with deep load batches, then
       // the column forward: one more shared-memory round trip, but no DFT registers are live
       // while the checkpoint and transmission loads are in flight
@@ -1360,9 +1379,9 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
       if (want_prop && sl > 0) prefetch_l1(vh_base + (size_t)(sl - 1) * NN, PTY_ADJ_L1PF * 1024);
 #endif
       F::col_fwd(s, tw, none);
-#else
-      F::template col_inv_fwd<true>(s, tw, trans);
-#endif
+      } else {
+        F::template col_inv_fwd<true>(s, tw, trans);
+      }
 #if PTY_ADJ_PF == 1
       if (sl - 1 >= a.s0 && want_obj) prefetch_block<N>(ck_base + (size_t)(sl - 1) * NN);
 #endif
@@ -1370,7 +1389,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
       if (sl > 0) {
         AdjPropStore<N> prop{cm0, cm1, want_prop ? vh_base + (size_t)(sl - 1) * NN : nullptr, e0, e1, c0, c1,
                              gdz, gt0, gt1};
-#if PTY_ADJ_SPLIT_ROW
+        if constexpr (adj_split_row<N>()) {
         F::template row_fwd<true>(s, none);
         if constexpr (kStage) {
           if (want_prop) prop.stg = stage_get();
@@ -1384,9 +1403,9 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
         if (want_obj && sl - 1 >= a.s0) prefetch_l1(ck_base + (size_t)(sl - 1) * NN, PTY_ADJ_L1PF * 1024);
 #endif
         F::row_inv(s, tw, none);
-#else
-        F::row_fwd_inv(s, tw, prop);
-#endif
+        } else {
+          F::row_fwd_inv(s, tw, prop);
+        }
         F::block_inv(s, tw);
       } else {
         ProbeStore<N> probe{want_probe ? a.gPhat + (size_t)m * NN : nullptr, a.Phat + (size_t)m * NN, cr0, cr1, f0,
