@@ -2,28 +2,30 @@
 //
 // The wave (512 KB) does not fit one SM's shared memory, so CTA q of the cluster holds rows
 // [64 q, 64 q + 64) as float2 s[64][257] and the four CTAs exchange data through distributed shared
-// memory.  Along axis 0 the split is n = 64 n1 + n2 (n1 = the CTA, n2 = its local row):
-//   C1   for every (local row n2, column c): 4-point DFT over the four CTAs, times W_256^{n2 k1},
-//        result k1 written to CTA k1 (the only step touching other CTAs' shared memory);
-//   C2a  16-point DFT over the local rows n2 = 4 m1 + m2 (over m1), times W_64^{m2 j1};
-//   C2b  4-point DFT over m2: local position 4 j1 + j2 of CTA q holds bin q + 4 j1 + 64 j2.
-// Along axis 1 (local to each CTA) n = 16 a + b:
+// memory.  Axis 0 (across the CTAs) splits as n = 16 a + b (a, b = 0..15), so row n lives in CTA
+// a / 4 at local row 16 (a % 4) + b, and bin k = k1 + 16 k2:
+//   X1   for every (column c, b): 16-point DFT over a (four rows from each CTA), times
+//        W_256^{b k1}; result k1 goes back to the place of a = k1 (CTA k1 / 4, local row
+//        16 (k1 % 4) + b).  The only step touching other CTAs' shared memory;
+//   X2   for every (column c, k1): 16-point DFT over b (16 consecutive local rows); local row
+//        16 (k1 % 4) + k2 of CTA k1 / 4 then holds bin k1 + 16 k2, i.e. global position 16 k1 + k2.
+// Axis 1 (local to each CTA) splits as n = 16 a + b:
 //   RA   16-point DFT over a, times W_256^{b k1};   RB   16-point DFT over b.
-// The forward transform runs C1, C2a, C2b, RA, RB (natural -> k-space), the inverse the mirror
-// images in reverse order.  The step API is that of the single-CTA Fft2 in fft_smem.cuh, so the
-// same kernels drive both: "col" is the cross-CTA step next to the natural layout (its hook sees 4
-// elements, rows 64 n1 + n2 of one column, lanes on consecutive columns), "block" the three local
-// steps in between, "row" the step next to k-space (hook on 16 consecutive positions of one local
-// row, lanes on consecutive rows).  Every cross-CTA step starts and ends with a cluster barrier;
-// all CTAs of a cluster run the same sequence of steps.
+// The forward transform runs X1, X2, RA, RB (natural -> k-space), the inverse the mirror images in
+// reverse order.  The step API is that of the single-CTA Fft2 in fft_smem.cuh, so the same kernels
+// drive both: "col" is the cross-CTA step next to the natural layout (its hook sees 16 elements,
+// rows 16 a + b of one column, lanes on consecutive columns), "block" the two local steps in
+// between, "row" the step next to k-space (hook on 16 consecutive positions of one local row, lanes
+// on consecutive rows).  Every cross-CTA step starts and ends with a cluster barrier; all CTAs of a
+// cluster run the same sequence of steps.
 #pragma once
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "fft_smem.cuh"
 
-// Tasks of the cross-CTA step unrolled together (each thread runs eight; unrolling lets the loads of
-// several tasks, remote and in a hook, be in flight at once).
+// Tasks of the cross-CTA step unrolled together (each thread runs two); unrolling lets the remote
+// loads of both tasks be in flight at once.
 #ifndef PTY_C1_UNROLL
 #define PTY_C1_UNROLL 1
 #endif
@@ -53,91 +55,65 @@ struct Fft2<256, T> {
     }
   }
 
-  // ---- C1 and its inverse, optionally fused around a natural-layout hook ----
-  // INV_IN: the input is k-space side (after C2a^-1) and gets the inverse 4-point DFT first;
-  // FWD_OUT: the forward 4-point DFT is applied before writing back.  Natural-layout elements are
-  // rows 64 n1 + n2 (n1 = 0..3) of column c.
+  // ---- X1 and its inverse, optionally fused around a natural-layout hook ----
+  // Task (c, b): element a is row 16 a + b (CTA a / 4, local row 16 (a % 4) + b); the k-space side
+  // keeps bin k1 in the same place.  INV_IN: the input is the k-space side and gets the conjugate
+  // twiddle and the inverse 16-point DFT first; FWD_OUT: the forward DFT and the twiddle are
+  // applied before writing back.
   template <bool INV_IN, bool FWD_OUT, bool WRITE, class H>
-  __device__ static void c1_step(float2* s, const float2* tw, H& h) {
+  __device__ static void x1_step(float2* s, const float2* tw, H& h) {
     const int q = rank();
     float2* rem[4];
 #pragma unroll
     for (int r = 0; r < 4; ++r) rem[r] = remote(s, r);
     cluster_sync();
 #pragma unroll kC1Unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 2; ++i) {
       const int t = threadIdx.x + i * T;
-      const int c = 64 * q + t % 64, n2 = t / 64;
-      const int e = n2 * RS + c;
-      float2 v[4];
+      const int c = 64 * q + t % 64, b = t / 64;
+      float2 v[16];
       if (!(std::remove_reference_t<H>::kReplaces && !INV_IN)) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) v[r] = rem[r][e];
+        for (int a = 0; a < 16; ++a) v[a] = rem[a / 4][(16 * (a % 4) + b) * RS + c];
       }
       if (INV_IN) {
+        if (!PTY_TW_SKIP || b != 0) {
 #pragma unroll
-        for (int k1 = 1; k1 < 4; ++k1) v[k1] = cmulc(tw[n2 * k1], v[k1]);
-        dft<4, true>(v);
+          for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmulc(tw[b * k1], v[k1]);
+        }
+        dft<16, true>(v);
       }
-      hook<4>(h, n2, L, c, 0, v);
+      hook<16>(h, b, 16, c, 0, v);
       if (FWD_OUT) {
-        dft<4, false>(v);
+        dft<16, false>(v);
+        if (!PTY_TW_SKIP || b != 0) {
 #pragma unroll
-        for (int k1 = 1; k1 < 4; ++k1) v[k1] = cmul(v[k1], tw[n2 * k1]);
+          for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
+        }
       }
       if (WRITE) {
 #pragma unroll
-        for (int r = 0; r < 4; ++r) rem[r][e] = v[r];
+        for (int a = 0; a < 16; ++a) rem[a / 4][(16 * (a % 4) + b) * RS + c] = v[a];
       }
     }
     cluster_sync();
   }
 
   // ---- local steps ----
-  __device__ static void c2a_fwd(float2* s, const float2* tw) {
-#pragma unroll 1
-    for (int i = 0; i < 2; ++i) {
-      const int t = threadIdx.x + i * T;
-      const int c = t % N, m2 = t / N;
-      float2 v[16];
-#pragma unroll
-      for (int m1 = 0; m1 < 16; ++m1) v[m1] = s[(4 * m1 + m2) * RS + c];
-      dft<16, false>(v);
-#pragma unroll
-      for (int j1 = 1; j1 < 16; ++j1) v[j1] = cmul(v[j1], tw[4 * m2 * j1]);
-#pragma unroll
-      for (int j1 = 0; j1 < 16; ++j1) s[(4 * j1 + m2) * RS + c] = v[j1];
-    }
-    __syncthreads();
-  }
-  __device__ static void c2a_inv(float2* s, const float2* tw) {
-#pragma unroll 1
-    for (int i = 0; i < 2; ++i) {
-      const int t = threadIdx.x + i * T;
-      const int c = t % N, m2 = t / N;
-      float2 v[16];
-#pragma unroll
-      for (int j1 = 0; j1 < 16; ++j1) v[j1] = s[(4 * j1 + m2) * RS + c];
-#pragma unroll
-      for (int j1 = 1; j1 < 16; ++j1) v[j1] = cmulc(tw[4 * m2 * j1], v[j1]);
-      dft<16, true>(v);
-#pragma unroll
-      for (int m1 = 0; m1 < 16; ++m1) s[(4 * m1 + m2) * RS + c] = v[m1];
-    }
-    __syncthreads();
-  }
+  // X2: task (c, g) for column c and local row group g (k1 % 4): 16-point DFT over the rows
+  // 16 g + b (b -> k2), no twiddle after it.
   template <bool INV>
-  __device__ static void c2b(float2* s) {
-#pragma unroll 2
-    for (int i = 0; i < 8; ++i) {
+  __device__ static void x2_step(float2* s) {
+#pragma unroll 1
+    for (int i = 0; i < 2; ++i) {
       const int t = threadIdx.x + i * T;
-      const int c = t % N, j1 = t / N;
-      float2 v[4];
+      const int c = t % N, g = t / N;
+      float2 v[16];
 #pragma unroll
-      for (int m = 0; m < 4; ++m) v[m] = s[(4 * j1 + m) * RS + c];
-      dft<4, INV>(v);
+      for (int b = 0; b < 16; ++b) v[b] = s[(16 * g + b) * RS + c];
+      dft<16, INV>(v);
 #pragma unroll
-      for (int m = 0; m < 4; ++m) s[(4 * j1 + m) * RS + c] = v[m];
+      for (int b = 0; b < 16; ++b) s[(16 * g + b) * RS + c] = v[b];
     }
     __syncthreads();
   }
@@ -150,8 +126,10 @@ struct Fft2<256, T> {
 #pragma unroll
       for (int a = 0; a < 16; ++a) v[a] = s[r * RS + 16 * a + b];
       dft<16, false>(v);
+      if (!PTY_TW_SKIP || b != 0) {
 #pragma unroll
-      for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
+        for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
+      }
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) s[r * RS + 16 * k1 + b] = v[k1];
     }
@@ -165,6 +143,10 @@ struct Fft2<256, T> {
       float2 v[16];
 #pragma unroll
       for (int k1 = 0; k1 < 16; ++k1) v[k1] = s[r * RS + 16 * k1 + b];
+      if (!PTY_TW_SKIP || b != 0) {
+#pragma unroll
+        for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmulc(tw[b * k1], v[k1]);
+      }
       dft<16, true>(v);
 #pragma unroll
       for (int a = 0; a < 16; ++a) s[r * RS + 16 * a + b] = v[a];
@@ -187,11 +169,7 @@ struct Fft2<256, T> {
       }
       if (FWD_IN) dft<16, false>(v);
       hook<16>(h, 64 * q + r, 0, 16 * k1, 1, v);
-      if (INV_OUT) {
-        dft<16, true>(v);
-#pragma unroll
-        for (int b = 1; b < 16; ++b) v[b] = cmulc(tw[b * k1], v[b]);
-      }
+      if (INV_OUT) dft<16, true>(v);
       if (WRITE) {
 #pragma unroll
         for (int b = 0; b < 16; ++b) s[r * RS + 16 * k1 + b] = v[b];
@@ -203,11 +181,10 @@ struct Fft2<256, T> {
   // ---- the step API shared with the single-CTA FFT ----
   template <class LH>
   __device__ static void col_fwd(float2* s, const float2* tw, LH& lh) {
-    c1_step<false, true, true>(s, tw, lh);
+    x1_step<false, true, true>(s, tw, lh);
   }
   __device__ static void block_fwd(float2* s, const float2* tw) {
-    c2a_fwd(s, tw);
-    c2b<false>(s);
+    x2_step<false>(s);
     ra_fwd(s, tw);
   }
   template <bool WRITE, class SH>
@@ -220,16 +197,15 @@ struct Fft2<256, T> {
   }
   __device__ static void block_inv(float2* s, const float2* tw) {
     ra_inv(s, tw);
-    c2b<true>(s);
-    c2a_inv(s, tw);
+    x2_step<true>(s);
   }
   __device__ static void col_inv(float2* s, const float2* tw) {
     NoHook none;
-    c1_step<true, false, true>(s, tw, none);
+    x1_step<true, false, true>(s, tw, none);
   }
   template <bool FWD, class H>
   __device__ static void col_inv_fwd(float2* s, const float2* tw, H& h) {
-    c1_step<true, FWD, FWD>(s, tw, h);
+    x1_step<true, FWD, FWD>(s, tw, h);
   }
   template <class H>
   __device__ static void row_fwd_inv(float2* s, const float2* tw, H& h) {

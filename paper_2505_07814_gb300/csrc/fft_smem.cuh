@@ -151,16 +151,16 @@ __device__ __forceinline__ void dft(float2* x) {
 
 // Position of frequency bin k along axis 0 / axis 1 of the k-space layout, and the inverse maps.
 // N <= 128: axis 0 split k = k1 + A k2 at position 4 k1 + k2, axis 1 split k = k1 + 4 k2 at A k1 + k2.
-// N = 256 (four-CTA cluster, fft_cluster.cuh): axis 0 position 64 q + 4 j1 + j2 holds bin
-// q + 4 j1 + 64 j2; axis 1 position 16 k1 + k2 holds bin k1 + 16 k2.
+// N = 256 (four-CTA cluster, fft_cluster.cuh): both axes split k = k1 + 16 k2 at position
+// 16 k1 + k2.
 template <int N>
 __host__ __device__ constexpr int kpos0(int k) {
-  if constexpr (N == 256) return 64 * (k % 4) + 4 * ((k / 4) % 16) + k / 64;
+  if constexpr (N == 256) return 16 * (k % 16) + k / 16;
   else return 4 * (k % (N / 4)) + k / (N / 4);
 }
 template <int N>
 __host__ __device__ constexpr int kbin0(int p) {
-  if constexpr (N == 256) return p / 64 + 4 * ((p % 64) / 4) + 64 * (p % 4);
+  if constexpr (N == 256) return p / 16 + 16 * (p % 16);
   else return p / 4 + (N / 4) * (p % 4);
 }
 template <int N>

@@ -156,18 +156,16 @@ static void run256(unsigned seed) {
     }
   };
   auto fwd = [&] {
-    step([&](float2* s) { F::c1_step<false, true, true>(s, tw.data(), none); });
-    step([&](float2* s) { F::c2a_fwd(s, tw.data()); });
-    step([&](float2* s) { F::c2b<false>(s); });
+    step([&](float2* s) { F::x1_step<false, true, true>(s, tw.data(), none); });
+    step([&](float2* s) { F::x2_step<false>(s); });
     step([&](float2* s) { F::ra_fwd(s, tw.data()); });
     step([&](float2* s) { F::rb_step<true, false, true>(s, nullptr, none); });
   };
   auto inv = [&] {
     step([&](float2* s) { F::rb_step<false, true, true>(s, tw.data(), none); });
     step([&](float2* s) { F::ra_inv(s, tw.data()); });
-    step([&](float2* s) { F::c2b<true>(s); });
-    step([&](float2* s) { F::c2a_inv(s, tw.data()); });
-    step([&](float2* s) { F::c1_step<true, false, true>(s, tw.data(), none); });
+    step([&](float2* s) { F::x2_step<true>(s); });
+    step([&](float2* s) { F::x1_step<true, false, true>(s, tw.data(), none); });
   };
   auto read = [&](bool kspace) {
     std::vector<cd> out(N * N);
@@ -189,27 +187,23 @@ static void run256(unsigned seed) {
   inv();
   const double e_inv = rel(read(false), scaled(x, (double)N * N));
   // fused: forward ending in RB -> RB^-1 (row_fwd_inv), then the rest of the inverse
-  step([&](float2* s) { F::c1_step<false, true, true>(s, tw.data(), none); });
-  step([&](float2* s) { F::c2a_fwd(s, tw.data()); });
-  step([&](float2* s) { F::c2b<false>(s); });
+  step([&](float2* s) { F::x1_step<false, true, true>(s, tw.data(), none); });
+  step([&](float2* s) { F::x2_step<false>(s); });
   step([&](float2* s) { F::ra_fwd(s, tw.data()); });
   step([&](float2* s) { F::row_fwd_inv(s, tw.data(), none); });
   step([&](float2* s) { F::ra_inv(s, tw.data()); });
-  step([&](float2* s) { F::c2b<true>(s); });
-  step([&](float2* s) { F::c2a_inv(s, tw.data()); });
-  step([&](float2* s) { F::c1_step<true, false, true>(s, tw.data(), none); });
+  step([&](float2* s) { F::x2_step<true>(s); });
+  step([&](float2* s) { F::x1_step<true, false, true>(s, tw.data(), none); });
   const double e_f1 = rel(read(false), scaled(x, std::pow((double)N, 4)));
   for (auto& c : cta)
     for (auto& v : c) v = make_float2(v.x / (float)std::pow((double)N, 4), v.y / (float)std::pow((double)N, 4));
-  // fused: inverse ending in C1^-1 -> C1 (col_inv_fwd), then the rest of the forward
+  // fused: inverse ending in X1^-1 -> X1 (col_inv_fwd), then the rest of the forward
   fwd();
   step([&](float2* s) { F::rb_step<false, true, true>(s, tw.data(), none); });
   step([&](float2* s) { F::ra_inv(s, tw.data()); });
-  step([&](float2* s) { F::c2b<true>(s); });
-  step([&](float2* s) { F::c2a_inv(s, tw.data()); });
+  step([&](float2* s) { F::x2_step<true>(s); });
   step([&](float2* s) { F::col_inv_fwd<true>(s, tw.data(), none); });
-  step([&](float2* s) { F::c2a_fwd(s, tw.data()); });
-  step([&](float2* s) { F::c2b<false>(s); });
+  step([&](float2* s) { F::x2_step<false>(s); });
   step([&](float2* s) { F::ra_fwd(s, tw.data()); });
   step([&](float2* s) { F::rb_step<true, false, true>(s, nullptr, none); });
   const double e_f2 = rel(read(true), scaled(X, (double)N * N));
