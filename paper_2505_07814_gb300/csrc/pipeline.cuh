@@ -37,13 +37,14 @@
 #define PTY_ADJ_SPLIT_ROW 1
 #endif
 // The same two choices for the N = 256 cluster adjoint.  Its column step is the cross-CTA step, so
-// a separate transmission pass costs a second pass through distributed shared memory per slice;
-// its tasks are small (4 and 16 elements), so the fused hooks hold few registers.
+// a separate transmission pass costs a second pass through distributed shared memory per slice
+// (large-window workload: adjoint 63.5 ms split, 46.8 ms fused); the propagation pass measured
+// slightly faster split (45.0 against 45.9 ms).
 #ifndef PTY_ADJ256_SPLIT_COL
 #define PTY_ADJ256_SPLIT_COL 0
 #endif
 #ifndef PTY_ADJ256_SPLIT_ROW
-#define PTY_ADJ256_SPLIT_ROW 0
+#define PTY_ADJ256_SPLIT_ROW 1
 #endif
 #ifndef PTY_FWD_SPLIT_COL
 #define PTY_FWD_SPLIT_COL 0
@@ -66,6 +67,11 @@
 // 2.490 ms without on the same workload)
 #ifndef PTY_FWD_PF
 #define PTY_FWD_PF 0
+#endif
+// 1: the N = 256 adjoint prefetches to L2, at the start of each slice, its CTA's part of the next
+// slice's transmission patch, checkpoint and spectrum (the large-window object does not fit L2)
+#ifndef PTY_ADJ256_PF
+#define PTY_ADJ256_PF 0
 #endif
 // Adjoint L1 prefetch: > 0 prefetches the first PTY_ADJ_L1PF KB of each checkpoint and spectrum
 // block into L1 (prefetch.global.L1, one 128-byte line per thread) two transform steps before the
@@ -324,10 +330,13 @@ __device__ __forceinline__ void prefetch_l1(const void* base, int bytes) {
   for (int l = threadIdx.x * 128; l < bytes; l += blockDim.x * 128)
     asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(base) + l));
 }
-// Rows [0, N) of an N-wide patch with row stride W (elements), one row per thread tid < N.
-template <int N>
-__device__ __forceinline__ void prefetch_patch(const float2* base, int W) {
-  if (threadIdx.x < N) prefetch_l2(base + (size_t)threadIdx.x * W, sizeof(float2) * N);
+// Rows [0, N) of an N-wide patch with row stride W (elements), one row per thread tid < N.  With
+// C > 1 CTAs per wave, CTA `rank` takes its own N / C columns of every row (the columns its
+// cross-CTA step reads).
+template <int N, int C = 1>
+__device__ __forceinline__ void prefetch_patch(const float2* base, int W, int rank = 0) {
+  if (threadIdx.x < N)
+    prefetch_l2(base + (size_t)threadIdx.x * W + rank * (N / C), sizeof(float2) * (N / C));
 }
 // A contiguous N*N block, split over the first 8 threads.
 template <int N>
@@ -535,7 +544,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   const size_t plane = (size_t)a.H * a.W;
   const float2* Tpatch = a.T + (OM ? (size_t)(bm % Ko) * a.Nz * plane : 0) + (size_t)i0 * a.W + i1;
 #if PTY_FWD_PF
-  prefetch_patch<N>(Tpatch, a.W);
+  prefetch_patch<N, F::C>(Tpatch, a.W, F::rank());
 #endif
 
   // Staging (fwd_staged): copy k holds slice k's rows, so the k-th wait is on phase parity k & 1;
@@ -582,7 +591,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
   F::block_inv(s, tw);
   for (int sl = 0; sl < a.Nz; ++sl) {
 #if PTY_FWD_PF
-    if (sl + 1 < a.Nz) prefetch_patch<N>(Tpatch + (sl + 1) * plane, a.W);
+    if (sl + 1 < a.Nz) prefetch_patch<N, F::C>(Tpatch + (sl + 1) * plane, a.W, F::rank());
 #endif
     TransLoad<N> trans{Tpatch + sl * plane, a.W, a.ckpt ? a.ckpt + ((size_t)bm * a.Nz + sl) * NN : nullptr};
 #if PTY_FWD_SPLIT_COL
@@ -1353,6 +1362,16 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
   float gdz = 0.f, gt0 = 0.f, gt1 = 0.f, gp0 = 0.f, gp1 = 0.f;
   NoHook none;
   for (int sl = a.s1 - 1; sl >= a.s0; --sl) {
+#if PTY_ADJ256_PF
+    if constexpr (F::C > 1) {
+      if (sl - 1 >= a.s0) {
+        prefetch_patch<N, F::C>(a.T + (sl - 1) * plane + patch, a.W, F::rank());
+        if (want_obj) prefetch_patch<N, F::C>(ck_base + (size_t)(sl - 1) * NN, N, F::rank());
+      }
+      if (want_prop && sl - 2 >= a.s0 - 1 && sl >= 2)
+        prefetch_patch<N, F::C>(vh_base + (size_t)(sl - 2) * NN, N, F::rank());
+    }
+#endif
 #if PTY_ADJ_PF == 0
     if (sl - 1 >= a.s0 && want_obj) prefetch_block<N>(ck_base + (size_t)(sl - 1) * NN);
     if (sl - 2 >= a.s0 - 1 && sl >= 2 && want_prop) prefetch_block<N>(vh_base + (size_t)(sl - 2) * NN);
