@@ -151,26 +151,26 @@ __device__ __forceinline__ void dft(float2* x) {
 
 // Position of frequency bin k along axis 0 / axis 1 of the k-space layout, and the inverse maps.
 // N <= 128: axis 0 split k = k1 + A k2 at position 4 k1 + k2, axis 1 split k = k1 + 4 k2 at A k1 + k2.
-// N = 256 (four-CTA cluster, fft_cluster.cuh): axis 0 split k = k1 + 32 k2 at position 8 k1 + k2,
-// axis 1 split k = k1 + 8 k2 at 32 k1 + k2.
+// N = 256 (four-CTA cluster, fft_cluster.cuh): both axes split k = k1 + 16 k2 at position
+// 16 k1 + k2.
 template <int N>
 __host__ __device__ constexpr int kpos0(int k) {
-  if constexpr (N == 256) return 8 * (k % 32) + k / 32;
+  if constexpr (N == 256) return 16 * (k % 16) + k / 16;
   else return 4 * (k % (N / 4)) + k / (N / 4);
 }
 template <int N>
 __host__ __device__ constexpr int kbin0(int p) {
-  if constexpr (N == 256) return p / 8 + 32 * (p % 8);
+  if constexpr (N == 256) return p / 16 + 16 * (p % 16);
   else return p / 4 + (N / 4) * (p % 4);
 }
 template <int N>
 __host__ __device__ constexpr int kpos1(int k) {
-  if constexpr (N == 256) return 32 * (k % 8) + k / 8;
+  if constexpr (N == 256) return 16 * (k % 16) + k / 16;
   else return (N / 4) * (k % 4) + k / 4;
 }
 template <int N>
 __host__ __device__ constexpr int kbin1(int p) {
-  if constexpr (N == 256) return p / 32 + 8 * (p % 32);
+  if constexpr (N == 256) return p / 16 + 16 * (p % 16);
   else return p / (N / 4) + 4 * (p % (N / 4));
 }
 // Index of k-space element (p0, p1) in global k-space buffers (stored transposed).

@@ -125,10 +125,10 @@ template <>
 struct Launch<128> {
   static constexpr int T = 512, TF = PTY_TF128, TA = PTY_TA128, MINB_F = 1, MINB_A = 1;
 };
-// N = 256: every wave kernel runs as four-CTA clusters (fft_cluster.cuh), 256 threads per CTA.
+// N = 256: every wave kernel runs as four-CTA clusters (fft_cluster.cuh), 512 threads per CTA.
 template <>
 struct Launch<256> {
-  static constexpr int T = 256, TF = 256, TA = 256, MINB_F = 1, MINB_A = 1;
+  static constexpr int T = 512, TF = 512, TA = 512, MINB_F = 1, MINB_A = 1;
 };
 
 // Rows of a wave one CTA holds in shared memory (a quarter of the wave at N = 256).

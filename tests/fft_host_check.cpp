@@ -115,7 +115,7 @@ static void run(unsigned seed) {
 // N = 256 on four emulated CTAs: CTA q holds rows [64 q, 64 q + 64) as float2 [64][257]; k-space
 // row p0 = 64 q + local row.  The cluster FFT's sub-steps are each one barrier-delimited step.
 static void run256(unsigned seed) {
-  constexpr int N = 256, T = 256, L = 64;
+  constexpr int N = 256, T = 512, L = 64;
   using F = pty::Fft2<N, T>;
   constexpr int RS = F::RS;
   std::vector<float2> cta[4];
@@ -157,12 +157,14 @@ static void run256(unsigned seed) {
   };
   auto fwd = [&] {
     step([&](float2* s) { F::x1_step<false, true, true>(s, tw.data(), none); });
-    step([&](float2* s) { F::block_step<false>(s, tw.data()); });
+    step([&](float2* s) { F::x2_step<false>(s); });
+    step([&](float2* s) { F::ra_fwd(s, tw.data()); });
     step([&](float2* s) { F::rb_step<true, false, true>(s, nullptr, none); });
   };
   auto inv = [&] {
     step([&](float2* s) { F::rb_step<false, true, true>(s, tw.data(), none); });
-    step([&](float2* s) { F::block_step<true>(s, tw.data()); });
+    step([&](float2* s) { F::ra_inv(s, tw.data()); });
+    step([&](float2* s) { F::x2_step<true>(s); });
     step([&](float2* s) { F::x1_step<true, false, true>(s, tw.data(), none); });
   };
   auto read = [&](bool kspace) {
@@ -186,9 +188,11 @@ static void run256(unsigned seed) {
   const double e_inv = rel(read(false), scaled(x, (double)N * N));
   // fused: forward ending in RB -> RB^-1 (row_fwd_inv), then the rest of the inverse
   step([&](float2* s) { F::x1_step<false, true, true>(s, tw.data(), none); });
-  step([&](float2* s) { F::block_step<false>(s, tw.data()); });
+  step([&](float2* s) { F::x2_step<false>(s); });
+  step([&](float2* s) { F::ra_fwd(s, tw.data()); });
   step([&](float2* s) { F::row_fwd_inv(s, tw.data(), none); });
-  step([&](float2* s) { F::block_step<true>(s, tw.data()); });
+  step([&](float2* s) { F::ra_inv(s, tw.data()); });
+  step([&](float2* s) { F::x2_step<true>(s); });
   step([&](float2* s) { F::x1_step<true, false, true>(s, tw.data(), none); });
   const double e_f1 = rel(read(false), scaled(x, std::pow((double)N, 4)));
   for (auto& c : cta)
@@ -196,9 +200,11 @@ static void run256(unsigned seed) {
   // fused: inverse ending in X1^-1 -> X1 (col_inv_fwd), then the rest of the forward
   fwd();
   step([&](float2* s) { F::rb_step<false, true, true>(s, tw.data(), none); });
-  step([&](float2* s) { F::block_step<true>(s, tw.data()); });
+  step([&](float2* s) { F::ra_inv(s, tw.data()); });
+  step([&](float2* s) { F::x2_step<true>(s); });
   step([&](float2* s) { F::col_inv_fwd<true>(s, tw.data(), none); });
-  step([&](float2* s) { F::block_step<false>(s, tw.data()); });
+  step([&](float2* s) { F::x2_step<false>(s); });
+  step([&](float2* s) { F::ra_fwd(s, tw.data()); });
   step([&](float2* s) { F::rb_step<true, false, true>(s, nullptr, none); });
   const double e_f2 = rel(read(true), scaled(X, (double)N * N));
   std::printf("N %d T %d fwd %.3e inv %.3e fused %.3e\n", N, T, e_fwd, e_inv, std::max(e_f1, e_f2));
