@@ -144,12 +144,15 @@ def gpu_smi_id(torch, dev):
         return str(dev.index or 0)
 
 
-def make_inputs(workload, positions):
+def make_inputs(workload, positions, first=0):
     """The workload, the default flat start and measured patterns for the given scan positions
-    (a dict position -> row of the returned [len(positions)][N][N] float32 array)."""
+    (a dict position -> row of the returned [len(positions)][N][N] float32 array).  first > 0 keeps
+    only the first `first` scan positions (small profiling captures)."""
     from paper_2505_07814_gb300 import synth
 
     w = synth.workload(workload)
+    if first > 0:
+        w.pos, w.tilt = w.pos[:first], w.tilt[:first]
     amp0, phase0 = synth.flat_object(w.Nz, w.H, w.W)  # default start of a reconstruction
     used = sorted(set(positions))
     I_rows = synth.vacuum_patterns(w.probe, len(used))
@@ -579,11 +582,11 @@ class Workload:
 
         from paper_2505_07814_gb300.ptycho import Geometry, Params, Ptycho
         self.name, self.B, self.dev, self.world = name, B, dev, world
-        Ntot = _ntot(name)
+        Ntot = args.positions if args.positions > 0 else _ntot(name)
         # weak scaling: every rank its own blocks of B positions (a global batch of world x B); with
         # more than one rank each step is the data-parallel step (statistics and gradient all-reduce)
         self.idx_h = rank_batches(rank, world, B, Ntot)
-        w, amp0, phase0, I_rows, row_of = make_inputs(name, [p for b in self.idx_h for p in b])
+        w, amp0, phase0, I_rows, row_of = make_inputs(name, [p for b in self.idx_h for p in b], args.positions)
         self.w, self.amp0, self.phase0, self.I_rows, self.row_of = w, amp0, phase0, I_rows, row_of
         f32 = dict(dtype=torch.float32, device=dev)
         self.params = Params(amp=torch.tensor(amp0, **f32), phase=torch.tensor(phase0, **f32),
@@ -843,8 +846,10 @@ def main():
     ap.add_argument("--workload", default="c3", choices=sorted(WORKLOADS))
     ap.add_argument("--also", default="c2",
                     help="comma-separated workloads also timed (device only) in the same run and reported under "
-                         "'also' ('' for none)")
+                         "'also' ('none' for none)")
     ap.add_argument("--batch", type=int, default=0, help="positions per step (0: the workload's default)")
+    ap.add_argument("--positions", type=int, default=0,
+                    help="keep only the first P scan positions (0: all); small profiling captures")
     ap.add_argument("--ckpt-stride", type=int, default=1, help="adjoint memory plan (pty_geom.ckpt_stride)")
     ap.add_argument("--fft", default="fp32", choices=["fp32", "bf16", "fp16", "bf16x3"],
                     help="per-slice DFTs: FP32 shared-memory FFT or split-precision tensor-core GEMMs")
@@ -932,7 +937,7 @@ def main():
     config = config_of(args, wl)
 
     also = {}
-    for name in [a for a in args.also.split(",") if a and a != args.workload]:
+    for name in [a for a in args.also.split(",") if a in WORKLOADS and a != args.workload]:
         del wl
         torch.cuda.empty_cache()
         wl = Workload(args, name, WORKLOADS[name][1], dev, rank, world)
