@@ -17,22 +17,42 @@
 // rows 16 a + b of one column, lanes on consecutive columns), "block" the two local steps in
 // between, "row" the step next to k-space (hook on 16 consecutive positions of one local row, lanes
 // on consecutive rows).  Every cross-CTA step starts and ends with a cluster barrier; all CTAs of a
-// cluster run the same sequence of steps.
+// cluster run the same sequence of steps.  Each thread runs two tasks of every step.
 #pragma once
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "fft_smem.cuh"
 
-// Tasks of the cross-CTA step unrolled together (each thread runs two); unrolling lets the remote
-// loads of both tasks be in flight at once.
-#ifndef PTY_C1_UNROLL
-#define PTY_C1_UNROLL 1
+// 1: every step reads both of a thread's tasks before it transforms either, so the second task's
+// shared-memory (or remote) loads are in flight while the first is transformed; the tasks of a
+// step touch disjoint elements.  0: one task at a time.
+#ifndef PTY_PRELOAD
+#define PTY_PRELOAD 1
 #endif
 
 namespace pty {
 
-constexpr int kC1Unroll = PTY_C1_UNROLL;
+// A step's two tasks per thread: load(i, v) reads task i into v[16], work(i, v) transforms it and
+// writes it back.  PRE: both loads first (steps without a hook; a hook's own registers and loads
+// would not fit beside two tasks at 128 registers per thread).
+template <bool PRE, class Load, class Work>
+__device__ __forceinline__ void two_tasks(Load&& load, Work&& work) {
+  if constexpr (PRE) {
+    float2 v[2][16];
+    load(0, v[0]);
+    load(1, v[1]);
+    work(0, v[0]);
+    work(1, v[1]);
+  } else {
+#pragma unroll 1
+    for (int i = 0; i < 2; ++i) {
+      float2 v[16];
+      load(i, v);
+      work(i, v);
+    }
+  }
+}
 
 template <int T>
 struct Fft2<256, T> {
@@ -67,35 +87,36 @@ struct Fft2<256, T> {
 #pragma unroll
     for (int r = 0; r < 4; ++r) rem[r] = remote(s, r);
     cluster_sync();
-#pragma unroll kC1Unroll
-    for (int i = 0; i < 2; ++i) {
-      const int t = threadIdx.x + i * T;
-      const int c = 64 * q + t % 64, b = t / 64;
-      float2 v[16];
-      if (!(std::remove_reference_t<H>::kReplaces && !INV_IN)) {
+    two_tasks<PTY_PRELOAD && kPlain<H>>(
+        [&](int i, float2* v) {
+          const int t = threadIdx.x + i * T, c = 64 * q + t % 64, b = t / 64;
+          if (!(std::remove_reference_t<H>::kReplaces && !INV_IN)) {
 #pragma unroll
-        for (int a = 0; a < 16; ++a) v[a] = rem[a / 4][(16 * (a % 4) + b) * RS + c];
-      }
-      if (INV_IN) {
-        if (!PTY_TW_SKIP || b != 0) {
+            for (int a = 0; a < 16; ++a) v[a] = rem[a / 4][(16 * (a % 4) + b) * RS + c];
+          }
+        },
+        [&](int i, float2* v) {
+          const int t = threadIdx.x + i * T, c = 64 * q + t % 64, b = t / 64;
+          if (INV_IN) {
+            if (!PTY_TW_SKIP || b != 0) {
 #pragma unroll
-          for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmulc(tw[b * k1], v[k1]);
-        }
-        dft<16, true>(v);
-      }
-      hook<16>(h, b, 16, c, 0, v);
-      if (FWD_OUT) {
-        dft<16, false>(v);
-        if (!PTY_TW_SKIP || b != 0) {
+              for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmulc(tw[b * k1], v[k1]);
+            }
+            dft<16, true>(v);
+          }
+          hook<16>(h, b, 16, c, 0, v);
+          if (FWD_OUT) {
+            dft<16, false>(v);
+            if (!PTY_TW_SKIP || b != 0) {
 #pragma unroll
-          for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
-        }
-      }
-      if (WRITE) {
+              for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
+            }
+          }
+          if (WRITE) {
 #pragma unroll
-        for (int a = 0; a < 16; ++a) rem[a / 4][(16 * (a % 4) + b) * RS + c] = v[a];
-      }
-    }
+            for (int a = 0; a < 16; ++a) rem[a / 4][(16 * (a % 4) + b) * RS + c] = v[a];
+          }
+        });
     cluster_sync();
   }
 
@@ -104,53 +125,56 @@ struct Fft2<256, T> {
   // 16 g + b (b -> k2), no twiddle after it.
   template <bool INV>
   __device__ static void x2_step(float2* s) {
-#pragma unroll 1
-    for (int i = 0; i < 2; ++i) {
-      const int t = threadIdx.x + i * T;
-      const int c = t % N, g = t / N;
-      float2 v[16];
+    two_tasks<PTY_PRELOAD != 0>(
+        [&](int i, float2* v) {
+          const int t = threadIdx.x + i * T, c = t % N, g = t / N;
 #pragma unroll
-      for (int b = 0; b < 16; ++b) v[b] = s[(16 * g + b) * RS + c];
-      dft<16, INV>(v);
+          for (int b = 0; b < 16; ++b) v[b] = s[(16 * g + b) * RS + c];
+        },
+        [&](int i, float2* v) {
+          const int t = threadIdx.x + i * T, c = t % N, g = t / N;
+          dft<16, INV>(v);
 #pragma unroll
-      for (int b = 0; b < 16; ++b) s[(16 * g + b) * RS + c] = v[b];
-    }
+          for (int b = 0; b < 16; ++b) s[(16 * g + b) * RS + c] = v[b];
+        });
     __syncthreads();
   }
   __device__ static void ra_fwd(float2* s, const float2* tw) {
-#pragma unroll 1
-    for (int i = 0; i < 2; ++i) {
-      const int t = threadIdx.x + i * T;
-      const int r = t % L, b = t / L;
-      float2 v[16];
+    two_tasks<PTY_PRELOAD != 0>(
+        [&](int i, float2* v) {
+          const int t = threadIdx.x + i * T, r = t % L, b = t / L;
 #pragma unroll
-      for (int a = 0; a < 16; ++a) v[a] = s[r * RS + 16 * a + b];
-      dft<16, false>(v);
-      if (!PTY_TW_SKIP || b != 0) {
+          for (int a = 0; a < 16; ++a) v[a] = s[r * RS + 16 * a + b];
+        },
+        [&](int i, float2* v) {
+          const int t = threadIdx.x + i * T, r = t % L, b = t / L;
+          dft<16, false>(v);
+          if (!PTY_TW_SKIP || b != 0) {
 #pragma unroll
-        for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
-      }
+            for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmul(v[k1], tw[b * k1]);
+          }
 #pragma unroll
-      for (int k1 = 0; k1 < 16; ++k1) s[r * RS + 16 * k1 + b] = v[k1];
-    }
+          for (int k1 = 0; k1 < 16; ++k1) s[r * RS + 16 * k1 + b] = v[k1];
+        });
     __syncthreads();
   }
   __device__ static void ra_inv(float2* s, const float2* tw) {
-#pragma unroll 1
-    for (int i = 0; i < 2; ++i) {
-      const int t = threadIdx.x + i * T;
-      const int r = t % L, b = t / L;
-      float2 v[16];
+    two_tasks<PTY_PRELOAD != 0>(
+        [&](int i, float2* v) {
+          const int t = threadIdx.x + i * T, r = t % L, b = t / L;
 #pragma unroll
-      for (int k1 = 0; k1 < 16; ++k1) v[k1] = s[r * RS + 16 * k1 + b];
-      if (!PTY_TW_SKIP || b != 0) {
+          for (int k1 = 0; k1 < 16; ++k1) v[k1] = s[r * RS + 16 * k1 + b];
+        },
+        [&](int i, float2* v) {
+          const int t = threadIdx.x + i * T, r = t % L, b = t / L;
+          if (!PTY_TW_SKIP || b != 0) {
 #pragma unroll
-        for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmulc(tw[b * k1], v[k1]);
-      }
-      dft<16, true>(v);
+            for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmulc(tw[b * k1], v[k1]);
+          }
+          dft<16, true>(v);
 #pragma unroll
-      for (int a = 0; a < 16; ++a) s[r * RS + 16 * a + b] = v[a];
-    }
+          for (int a = 0; a < 16; ++a) s[r * RS + 16 * a + b] = v[a];
+        });
     __syncthreads();
   }
   // RB, RB^-1 and the fused RB -> hook -> RB^-1.  k-space elements of task (r, k1): positions
@@ -158,23 +182,24 @@ struct Fft2<256, T> {
   template <bool FWD_IN, bool INV_OUT, bool WRITE, class H>
   __device__ static void rb_step(float2* s, const float2* tw, H& h) {
     const int q = rank();
-#pragma unroll 1
-    for (int i = 0; i < 2; ++i) {
-      const int t = threadIdx.x + i * T;
-      const int r = t % L, k1 = t / L;
-      float2 v[16];
-      if (!(std::remove_reference_t<H>::kReplaces && !FWD_IN)) {
+    two_tasks<PTY_PRELOAD && kPlain<H>>(
+        [&](int i, float2* v) {
+          const int t = threadIdx.x + i * T, r = t % L, k1 = t / L;
+          if (!(std::remove_reference_t<H>::kReplaces && !FWD_IN)) {
 #pragma unroll
-        for (int b = 0; b < 16; ++b) v[b] = s[r * RS + 16 * k1 + b];
-      }
-      if (FWD_IN) dft<16, false>(v);
-      hook<16>(h, 64 * q + r, 0, 16 * k1, 1, v);
-      if (INV_OUT) dft<16, true>(v);
-      if (WRITE) {
+            for (int b = 0; b < 16; ++b) v[b] = s[r * RS + 16 * k1 + b];
+          }
+        },
+        [&](int i, float2* v) {
+          const int t = threadIdx.x + i * T, r = t % L, k1 = t / L;
+          if (FWD_IN) dft<16, false>(v);
+          hook<16>(h, 64 * q + r, 0, 16 * k1, 1, v);
+          if (INV_OUT) dft<16, true>(v);
+          if (WRITE) {
 #pragma unroll
-        for (int b = 0; b < 16; ++b) s[r * RS + 16 * k1 + b] = v[b];
-      }
-    }
+            for (int b = 0; b < 16; ++b) s[r * RS + 16 * k1 + b] = v[b];
+          }
+        });
     __syncthreads();
   }
 

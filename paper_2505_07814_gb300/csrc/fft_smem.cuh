@@ -192,6 +192,11 @@ struct NoHook {
   __device__ __forceinline__ void operator()(int, int, int, int, float2*) {}
 };
 
+// Block-step tasks read together before any is transformed (1: one at a time)
+#ifndef PTY_PRELOAD_BLOCK
+#define PTY_PRELOAD_BLOCK 2
+#endif
+
 // 1: steps whose inter-step twiddles are all W^0 (digit n2 = 0 in the column steps, k1 = 0 in the
 // row steps, warp-uniform for N >= 64) skip the multiplication (exact: it multiplies by 1)
 #ifndef PTY_TW_SKIP
@@ -243,35 +248,52 @@ struct Fft2 {
     }
     __syncthreads();
   }
+  // Block tasks are read PTY_PRELOAD_BLOCK at a time before any is transformed, so the later
+  // tasks' shared-memory loads are in flight while the first is transformed (the tasks of a step
+  // touch disjoint elements).
+  static constexpr int BG = NBLK % PTY_PRELOAD_BLOCK == 0 ? PTY_PRELOAD_BLOCK : 1;
+  __device__ static void block_load(const float2* s, int i, float2 (&b)[4][4]) {
+    const int t = threadIdx.x + i * T;
+    const int n2 = t % A, k1 = t / A;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) b[q][p] = s[(4 * k1 + q) * RS + A * p + n2];
+  }
+  __device__ static void block_store(float2* s, int i, const float2 (&b)[4][4]) {
+    const int t = threadIdx.x + i * T;
+    const int n2 = t % A, k1 = t / A;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int p = 0; p < 4; ++p) s[(4 * k1 + q) * RS + A * p + n2] = b[q][p];
+  }
   __device__ static void block_fwd(float2* s, const float2* tw) {
+#pragma unroll 1
+    for (int i0 = 0; i0 < NBLK; i0 += BG) {
+      float2 b[BG][4][4];  // [task][q: row digit][p: column digit]
 #pragma unroll
-    for (int i = 0; i < NBLK; ++i) {
-      const int t = threadIdx.x + i * T;
-      const int n2 = t % A, k1 = t / A;
-      float2 b[4][4];  // [q: row digit][p: column digit]
+      for (int j = 0; j < BG; ++j) block_load(s, i0 + j, b[j]);
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int j = 0; j < BG; ++j) {
+        const int n2 = (threadIdx.x + (i0 + j) * T) % A;
 #pragma unroll
-        for (int p = 0; p < 4; ++p) b[q][p] = s[(4 * k1 + q) * RS + A * p + n2];
+        for (int p = 0; p < 4; ++p) {
+          float2 col[4] = {b[j][0][p], b[j][1][p], b[j][2][p], b[j][3][p]};
+          dft<4, false>(col);
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        float2 col[4] = {b[0][p], b[1][p], b[2][p], b[3][p]};
-        dft<4, false>(col);
+          for (int q = 0; q < 4; ++q) b[j][q][p] = col[q];
+        }
+        const float2 w1 = tw[n2], w2 = tw[2 * n2], w3 = tw[3 * n2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) b[q][p] = col[q];
+        for (int q = 0; q < 4; ++q) {
+          dft<4, false>(b[j][q]);
+          b[j][q][1] = cmul(b[j][q][1], w1);
+          b[j][q][2] = cmul(b[j][q][2], w2);
+          b[j][q][3] = cmul(b[j][q][3], w3);
+        }
+        block_store(s, i0 + j, b[j]);
       }
-      const float2 w1 = tw[n2], w2 = tw[2 * n2], w3 = tw[3 * n2];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        dft<4, false>(b[q]);
-        b[q][1] = cmul(b[q][1], w1);
-        b[q][2] = cmul(b[q][2], w2);
-        b[q][3] = cmul(b[q][3], w3);
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) s[(4 * k1 + q) * RS + A * p + n2] = b[q][p];
     }
     __syncthreads();
   }
@@ -318,28 +340,24 @@ struct Fft2 {
     __syncthreads();
   }
   __device__ static void block_inv(float2* s, const float2*) {
+#pragma unroll 1
+    for (int i0 = 0; i0 < NBLK; i0 += BG) {
+      float2 b[BG][4][4];
 #pragma unroll
-    for (int i = 0; i < NBLK; ++i) {
-      const int t = threadIdx.x + i * T;
-      const int n2 = t % A, k1 = t / A;
-      float2 b[4][4];
+      for (int j = 0; j < BG; ++j) block_load(s, i0 + j, b[j]);
 #pragma unroll
-      for (int q = 0; q < 4; ++q)
+      for (int j = 0; j < BG; ++j) {
 #pragma unroll
-        for (int p = 0; p < 4; ++p) b[q][p] = s[(4 * k1 + q) * RS + A * p + n2];
+        for (int q = 0; q < 4; ++q) dft<4, true>(b[j][q]);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) dft<4, true>(b[q]);
+        for (int p = 0; p < 4; ++p) {
+          float2 col[4] = {b[j][0][p], b[j][1][p], b[j][2][p], b[j][3][p]};
+          dft<4, true>(col);
 #pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        float2 col[4] = {b[0][p], b[1][p], b[2][p], b[3][p]};
-        dft<4, true>(col);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) b[q][p] = col[q];
+          for (int q = 0; q < 4; ++q) b[j][q][p] = col[q];
+        }
+        block_store(s, i0 + j, b[j]);
       }
-#pragma unroll
-      for (int q = 0; q < 4; ++q)
-#pragma unroll
-        for (int p = 0; p < 4; ++p) s[(4 * k1 + q) * RS + A * p + n2] = b[q][p];
     }
     __syncthreads();
   }
