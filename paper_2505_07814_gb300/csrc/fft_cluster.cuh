@@ -30,6 +30,10 @@
 #ifndef PTY_PRELOAD
 #define PTY_PRELOAD 1
 #endif
+// 1: steps with a hook that declares kPreload read both tasks first too
+#ifndef PTY_PRELOAD_HOOKS
+#define PTY_PRELOAD_HOOKS 1
+#endif
 
 namespace pty {
 
@@ -61,6 +65,13 @@ struct Fft2<256, T> {
   static_assert(T == 512, "task counts below assume 512 threads");
   template <class H>
   static constexpr bool kPlain = std::is_same_v<std::decay_t<H>, NoHook>;
+  // Both tasks of a step may be read first when the step has no hook, or a hook that declares
+  // kPreload (one light enough to run beside two tasks' registers).
+  template <class H>
+  __host__ __device__ static constexpr bool preload_ok() {
+    if constexpr (kPlain<H>) return true;
+    else return PTY_PRELOAD_HOOKS && std::decay_t<H>::kPreload;
+  }
 
   __device__ static int rank() { return (int)cooperative_groups::this_cluster().block_rank(); }
   __device__ static void cluster_sync() { cooperative_groups::this_cluster().sync(); }
@@ -87,7 +98,7 @@ struct Fft2<256, T> {
 #pragma unroll
     for (int r = 0; r < 4; ++r) rem[r] = remote(s, r);
     cluster_sync();
-    two_tasks<PTY_PRELOAD && kPlain<H>>(
+    two_tasks<PTY_PRELOAD && preload_ok<H>()>(
         [&](int i, float2* v) {
           const int t = threadIdx.x + i * T, c = 64 * q + t % 64, b = t / 64;
           if (!(std::remove_reference_t<H>::kReplaces && !INV_IN)) {
@@ -182,7 +193,7 @@ struct Fft2<256, T> {
   template <bool FWD_IN, bool INV_OUT, bool WRITE, class H>
   __device__ static void rb_step(float2* s, const float2* tw, H& h) {
     const int q = rank();
-    two_tasks<PTY_PRELOAD && kPlain<H>>(
+    two_tasks<PTY_PRELOAD && preload_ok<H>()>(
         [&](int i, float2* v) {
           const int t = threadIdx.x + i * T, r = t % L, k1 = t / L;
           if (!(std::remove_reference_t<H>::kReplaces && !FWD_IN)) {

@@ -33,6 +33,10 @@
 #ifndef PTY_ADJ_BATCH
 #define PTY_ADJ_BATCH 8
 #endif
+// the same for the N = 256 adjoint's pointwise passes
+#ifndef PTY_ADJ256_BATCH
+#define PTY_ADJ256_BATCH 8
+#endif
 #ifndef PTY_ADJ_SPLIT_ROW
 #define PTY_ADJ_SPLIT_ROW 1
 #endif
@@ -442,6 +446,7 @@ __device__ void adj_tables(float2* cm0, float2* cm1, float2* cr0, float2* cr1, f
 template <int N>
 struct ShiftLoad {
   static constexpr bool kReplaces = true;
+  static constexpr bool kPreload = false;  // may run in a step that has read two tasks
   static constexpr int kChunk = PTY_KS;
   const float2* Ph;
   const float2 *ra0, *ra1;
@@ -458,6 +463,7 @@ struct ShiftLoad {
 template <int N>
 struct TransLoad {
   static constexpr bool kReplaces = false;
+  static constexpr bool kPreload = true;  // may run in a step that has read two tasks
   static constexpr int kChunk = PTY_KT;
   const float2* Ts;  // patch corner in T
   int W;
@@ -484,6 +490,7 @@ struct TransLoad {
 template <int N>
 struct PropStore {
   static constexpr bool kReplaces = false;
+  static constexpr bool kPreload = true;  // may run in a step that has read two tasks
   static constexpr int kChunk = PTY_KP;
   const float2 *m0, *m1;
   float2* vh;
@@ -501,6 +508,7 @@ struct PropStore {
 template <int N>
 struct FarStore {
   static constexpr bool kReplaces = false;
+  static constexpr bool kPreload = true;  // may run in a step that has read two tasks
   static constexpr int kChunk = PTY_KF;
   float2* Psi;
   float* Im;
@@ -597,7 +605,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
 #if PTY_FWD_SPLIT_COL
     NoHook none;
     F::col_inv(s, tw);
-    F::template pointwise<PTY_ADJ_BATCH>(s, trans);
+    F::template pointwise<(N == 256 ? PTY_ADJ256_BATCH : PTY_ADJ_BATCH)>(s, trans);
     F::col_fwd(s, tw, none);
 #else
     if constexpr (kStage) {
@@ -649,6 +657,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_F) k_forward(FwdArgs a) {
 template <int N>
 struct AnchorLoad {
   static constexpr bool kReplaces = true;
+  static constexpr bool kPreload = false;  // may run in a step that has read two tasks
   static constexpr int kChunk = PTY_KS;
   const float2* an;
   float2* slot0;  // or nullptr
@@ -666,6 +675,7 @@ struct AnchorLoad {
 template <int N>
 struct CkptStore {
   static constexpr bool kReplaces = false;
+  static constexpr bool kPreload = true;  // may run in a step that has read two tasks
   static constexpr int kChunk = 4;
   float2* ck;
   template <int K>
@@ -1150,6 +1160,7 @@ __device__ __forceinline__ float2* adj_stage() {
 template <int N>
 struct FarGradLoad {
   static constexpr bool kReplaces = true;
+  static constexpr bool kPreload = false;  // may run in a step that has read two tasks
   static constexpr int kChunk = PTY_KG;
   const float* u;
   const float2* Psi;
@@ -1172,6 +1183,7 @@ struct FarGradLoad {
 template <int N>
 struct AdjTransLoad {
   static constexpr bool kReplaces = false;
+  static constexpr bool kPreload = false;  // may run in a step that has read two tasks
   static constexpr int kChunk = PTY_KA;
   const float2* Ts;  // patch corner in T
   float2* gTs;       // patch corner in the dL/dT accumulator
@@ -1201,6 +1213,7 @@ struct AdjTransLoad {
 template <int N>
 struct AdjPropStore {
   static constexpr bool kReplaces = false;
+  static constexpr bool kPreload = false;  // may run in a step that has read two tasks
   static constexpr int kChunk = PTY_KQ;
   const float2 *cm0, *cm1;
   const float2* vh;  // stored v^/N^2 of this propagation, or nullptr
@@ -1236,6 +1249,7 @@ struct AdjPropStore {
 template <int N>
 struct ProbeStore {
   static constexpr bool kReplaces = false;
+  static constexpr bool kPreload = false;  // may run in a step that has read two tasks
   static constexpr int kChunk = PTY_KR;
   float2* gP;  // or nullptr
   const float2* Ph;
@@ -1389,7 +1403,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
       if constexpr (kStage) {
         if (want_obj) trans.stg = stage_get();
       }
-      F::template pointwise<PTY_ADJ_BATCH>(s, trans);
+      F::template pointwise<(N == 256 ? PTY_ADJ256_BATCH : PTY_ADJ_BATCH)>(s, trans);
       if constexpr (kStage) {  // the stage is free again: fetch this slice's spectrum
         if (tid == 0 && !(sst >> 31) && want_prop && sl > 0)
           stage_issue(sbar, stg, vh_base + (size_t)(sl - 1) * NN, kStageBytes);
@@ -1413,7 +1427,7 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
         if constexpr (kStage) {
           if (want_prop) prop.stg = stage_get();
         }
-        F::template pointwise_k<PTY_ADJ_BATCH>(s, prop);
+        F::template pointwise_k<(N == 256 ? PTY_ADJ256_BATCH : PTY_ADJ_BATCH)>(s, prop);
         if constexpr (kStage) {  // the stage is free again: fetch the next slice's checkpoint
           if (tid == 0 && !(sst >> 31) && want_obj && sl - 1 >= a.s0)
             stage_issue(sbar, stg, ck_base + (size_t)(sl - 1) * NN, kStageBytes);
