@@ -497,6 +497,16 @@ struct PropStore {
   float2* vh;
   template <int K>
   __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
+    if (rs == 0) {  // a chunk of one k-space row (every caller): its axis-0 factor is read once
+      const float2 f0 = m0[r0];
+#pragma unroll
+      for (int k = 0; k < K; ++k) {
+        const int c = c0 + k * cs;
+        v[k] = cmul(cmul(v[k], f0), m1[c]);
+        if (vh) __stcs(vh + kidx<N>(r0, c), v[k]);
+      }
+      return;
+    }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int r = r0 + k * rs, c = c0 + k * cs;
@@ -1232,14 +1242,37 @@ struct AdjPropStore {
         const int e = kidx<N>(r0 + k * rs, c0 + k * cs);
         x[k] = staged ? st[e] : ld_once(vh + e);
       }
+      if (rs == 0) {
+        // a chunk of one k-space row (every caller): the row's dz and tilt factors multiply the
+        // chunk's sum of w once, sum_k w (e0 + e1_k) = e0 sum_k w + sum_k w e1_k
+        float sw = 0.f, sd = 0.f, s1 = 0.f;
 #pragma unroll
-      for (int k = 0; k < K; ++k) {
-        const int r = r0 + k * rs, c = c0 + k * cs;
-        const float w = v[k].x * x[k].y - v[k].y * x[k].x;
-        dz = fmaf(w, e0[r] + e1[c], dz);
-        t0 = fmaf(w, c0t[r], t0);
-        t1 = fmaf(w, c1t[c], t1);
+        for (int k = 0; k < K; ++k) {
+          const int c = c0 + k * cs;
+          const float w = v[k].x * x[k].y - v[k].y * x[k].x;
+          sw += w;
+          sd = fmaf(w, e1[c], sd);
+          s1 = fmaf(w, c1t[c], s1);
+        }
+        dz = fmaf(sw, e0[r0], dz + sd);
+        t0 = fmaf(sw, c0t[r0], t0);
+        t1 += s1;
+      } else {
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+          const int r = r0 + k * rs, c = c0 + k * cs;
+          const float w = v[k].x * x[k].y - v[k].y * x[k].x;
+          dz = fmaf(w, e0[r] + e1[c], dz);
+          t0 = fmaf(w, c0t[r], t0);
+          t1 = fmaf(w, c1t[c], t1);
+        }
       }
+    }
+    if (rs == 0) {
+      const float2 f0 = cm0[r0];
+#pragma unroll
+      for (int k = 0; k < K; ++k) v[k] = cmul(cmul(v[k], f0), cm1[c0 + k * cs]);
+      return;
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) v[k] = cmul(cmul(v[k], cm0[r0 + k * rs]), cm1[c0 + k * cs]);
