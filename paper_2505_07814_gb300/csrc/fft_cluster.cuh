@@ -1,14 +1,15 @@
-// fft_cluster.cuh -- 2D FFT of one 256 x 256 wavefield spread over a four-CTA thread-block cluster.
+// fft_cluster.cuh -- 2D FFT of one 256 x 256 wavefield spread over a thread-block cluster of C CTAs
+// (C = PTY_N256_CTAS: 4 CTAs of 512 threads, or 8 of 128).
 //
-// The wave (512 KB) does not fit one SM's shared memory, so CTA q of the cluster holds rows
-// [64 q, 64 q + 64) as float2 s[64][257] and the four CTAs exchange data through distributed shared
+// The wave (512 KB) does not fit one SM's shared memory, so CTA q of the cluster holds the L = 256 / C
+// rows [L q, L q + L) as float2 s[L][257] and the CTAs exchange data through distributed shared
 // memory.  Axis 0 (across the CTAs) splits as n = 16 a + b (a, b = 0..15), so row n lives in CTA
-// a / 4 at local row 16 (a % 4) + b, and bin k = k1 + 16 k2:
-//   X1   for every (column c, b): 16-point DFT over a (four rows from each CTA), times
-//        W_256^{b k1}; result k1 goes back to the place of a = k1 (CTA k1 / 4, local row
-//        16 (k1 % 4) + b).  The only step touching other CTAs' shared memory;
+// a / AP at local row 16 (a % AP) + b (AP = 16 / C values of a per CTA), and bin k = k1 + 16 k2:
+//   X1   for every (column c, b): 16-point DFT over a (AP rows from each CTA), times W_256^{b k1};
+//        result k1 goes back to the place of a = k1 (CTA k1 / AP, local row 16 (k1 % AP) + b).
+//        The only step touching other CTAs' shared memory;
 //   X2   for every (column c, k1): 16-point DFT over b (16 consecutive local rows); local row
-//        16 (k1 % 4) + k2 of CTA k1 / 4 then holds bin k1 + 16 k2, i.e. global position 16 k1 + k2.
+//        16 (k1 % AP) + k2 of CTA k1 / AP then holds bin k1 + 16 k2, i.e. global position 16 k1 + k2.
 // Axis 1 (local to each CTA) splits as n = 16 a + b:
 //   RA   16-point DFT over a, times W_256^{b k1};   RB   16-point DFT over b.
 // The forward transform runs X1, X2, RA, RB (natural -> k-space), the inverse the mirror images in
@@ -17,7 +18,7 @@
 // rows 16 a + b of one column, lanes on consecutive columns), "block" the two local steps in
 // between, "row" the step next to k-space (hook on 16 consecutive positions of one local row, lanes
 // on consecutive rows).  Every cross-CTA step starts and ends with a cluster barrier; all CTAs of a
-// cluster run the same sequence of steps.  Each thread runs two tasks of every step.
+// cluster run the same sequence of steps.  Every step has L N / 16 tasks per CTA.
 #pragma once
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -34,6 +35,12 @@
 // against 32.8 ms, from register spills; off)
 #ifndef PTY_PRELOAD_HOOKS
 #define PTY_PRELOAD_HOOKS 0
+#endif
+
+// CTAs per 256 x 256 wave: 4 (one 132 KB CTA of 512 threads per SM) or 8 (66 KB CTAs of 128
+// threads, up to three per SM from different clusters)
+#ifndef PTY_N256_CTAS
+#define PTY_N256_CTAS 4
 #endif
 
 namespace pty {
@@ -59,11 +66,21 @@ __device__ __forceinline__ void two_tasks(Load&& load, Work&& work) {
   }
 }
 
+// NT tasks per thread, two at a time through two_tasks.
+template <int NT, bool PRE, class Load, class Work>
+__device__ __forceinline__ void run_tasks(Load&& load, Work&& work) {
+  static_assert(NT % 2 == 0, "tasks per thread");
+#pragma unroll 1
+  for (int i0 = 0; i0 < NT; i0 += 2)
+    two_tasks<PRE>([&](int i, float2* v) { load(i0 + i, v); }, [&](int i, float2* v) { work(i0 + i, v); });
+}
+
 template <int T>
 struct Fft2<256, T> {
-  static constexpr int N = 256, L = 64, RS = N + 1;
-  static constexpr int C = 4, ROWS = L;
-  static_assert(T == 512, "task counts below assume 512 threads");
+  static constexpr int N = 256, C = PTY_N256_CTAS, L = N / C, RS = N + 1, ROWS = L;
+  static constexpr int AP = 16 / C;                    // values of a (rows 16 a + b) per CTA
+  static constexpr int TASKS = L * N / 16, NT = TASKS / T;  // tasks per step per CTA, per thread
+  static_assert((C == 4 || C == 8) && TASKS % T == 0 && NT % 2 == 0, "cluster shape");
   template <class H>
   static constexpr bool kPlain = std::is_same_v<std::decay_t<H>, NoHook>;
   // Both tasks of a step may be read first when the step has no hook, or a hook that declares
@@ -95,20 +112,21 @@ struct Fft2<256, T> {
   template <bool INV_IN, bool FWD_OUT, bool WRITE, class H>
   __device__ static void x1_step(float2* s, const float2* tw, H& h) {
     const int q = rank();
-    float2* rem[4];
+    float2* rem[C];
 #pragma unroll
-    for (int r = 0; r < 4; ++r) rem[r] = remote(s, r);
+    for (int r = 0; r < C; ++r) rem[r] = remote(s, r);
     cluster_sync();
-    two_tasks<PTY_PRELOAD && preload_ok<H>()>(
+    constexpr int CW = N / C;  // columns of the cross step's tasks in each CTA
+    run_tasks<NT, PTY_PRELOAD && preload_ok<H>()>(
         [&](int i, float2* v) {
-          const int t = threadIdx.x + i * T, c = 64 * q + t % 64, b = t / 64;
+          const int t = threadIdx.x + i * T, c = CW * q + t % CW, b = t / CW;
           if (!(std::remove_reference_t<H>::kReplaces && !INV_IN)) {
 #pragma unroll
-            for (int a = 0; a < 16; ++a) v[a] = rem[a / 4][(16 * (a % 4) + b) * RS + c];
+            for (int a = 0; a < 16; ++a) v[a] = rem[a / AP][(16 * (a % AP) + b) * RS + c];
           }
         },
         [&](int i, float2* v) {
-          const int t = threadIdx.x + i * T, c = 64 * q + t % 64, b = t / 64;
+          const int t = threadIdx.x + i * T, c = CW * q + t % CW, b = t / CW;
           if (INV_IN) {
             if (!PTY_TW_SKIP || b != 0) {
 #pragma unroll
@@ -126,18 +144,18 @@ struct Fft2<256, T> {
           }
           if (WRITE) {
 #pragma unroll
-            for (int a = 0; a < 16; ++a) rem[a / 4][(16 * (a % 4) + b) * RS + c] = v[a];
+            for (int a = 0; a < 16; ++a) rem[a / AP][(16 * (a % AP) + b) * RS + c] = v[a];
           }
         });
     cluster_sync();
   }
 
   // ---- local steps ----
-  // X2: task (c, g) for column c and local row group g (k1 % 4): 16-point DFT over the rows
+  // X2: task (c, g) for column c and local row group g (k1 % AP): 16-point DFT over the rows
   // 16 g + b (b -> k2), no twiddle after it.
   template <bool INV>
   __device__ static void x2_step(float2* s) {
-    two_tasks<PTY_PRELOAD != 0>(
+    run_tasks<NT, PTY_PRELOAD != 0>(
         [&](int i, float2* v) {
           const int t = threadIdx.x + i * T, c = t % N, g = t / N;
 #pragma unroll
@@ -152,7 +170,7 @@ struct Fft2<256, T> {
     __syncthreads();
   }
   __device__ static void ra_fwd(float2* s, const float2* tw) {
-    two_tasks<PTY_PRELOAD != 0>(
+    run_tasks<NT, PTY_PRELOAD != 0>(
         [&](int i, float2* v) {
           const int t = threadIdx.x + i * T, r = t % L, b = t / L;
 #pragma unroll
@@ -171,7 +189,7 @@ struct Fft2<256, T> {
     __syncthreads();
   }
   __device__ static void ra_inv(float2* s, const float2* tw) {
-    two_tasks<PTY_PRELOAD != 0>(
+    run_tasks<NT, PTY_PRELOAD != 0>(
         [&](int i, float2* v) {
           const int t = threadIdx.x + i * T, r = t % L, b = t / L;
 #pragma unroll
@@ -190,11 +208,11 @@ struct Fft2<256, T> {
     __syncthreads();
   }
   // RB, RB^-1 and the fused RB -> hook -> RB^-1.  k-space elements of task (r, k1): positions
-  // 16 k1 + k2 of local row r, global k-space row 64 q + r.
+  // 16 k1 + k2 of local row r, global k-space row L q + r.
   template <bool FWD_IN, bool INV_OUT, bool WRITE, class H>
   __device__ static void rb_step(float2* s, const float2* tw, H& h) {
     const int q = rank();
-    two_tasks<PTY_PRELOAD && preload_ok<H>()>(
+    run_tasks<NT, PTY_PRELOAD && preload_ok<H>()>(
         [&](int i, float2* v) {
           const int t = threadIdx.x + i * T, r = t % L, k1 = t / L;
           if (!(std::remove_reference_t<H>::kReplaces && !FWD_IN)) {
@@ -205,7 +223,7 @@ struct Fft2<256, T> {
         [&](int i, float2* v) {
           const int t = threadIdx.x + i * T, r = t % L, k1 = t / L;
           if (FWD_IN) dft<16, false>(v);
-          hook<16>(h, 64 * q + r, 0, 16 * k1, 1, v);
+          hook<16>(h, L * q + r, 0, 16 * k1, 1, v);
           if (INV_OUT) dft<16, true>(v);
           if (WRITE) {
 #pragma unroll
@@ -261,24 +279,43 @@ struct Fft2<256, T> {
     col_inv(s, tw);
   }
 
-  // Natural-layout pointwise pass: thread t owns column t % 256 and local rows t / 256 + 2 i.
+  // Natural-layout pointwise pass.  T >= N: thread t owns column t % 256 and local rows
+  // t / 256 + (T / N) i; T < N: thread t owns columns t + T h and every local row.
   template <int U, class H>
   __device__ static void pointwise(float2* s, H& h) {
-    constexpr int NE = L * N / T, RPI = T / N;
-    static_assert(NE % U == 0, "batch must divide the elements per thread");
-    const int c = threadIdx.x % N, r0 = threadIdx.x / N, g0 = L * rank();
+    const int g0 = L * rank();
+    if constexpr (T >= N) {
+      constexpr int NE = L * N / T, RPI = T / N;
+      static_assert(NE % U == 0, "batch must divide the elements per thread");
+      const int c = threadIdx.x % N, r0 = threadIdx.x / N;
 #pragma unroll 1
-    for (int i0 = 0; i0 < NE; i0 += U) {
-      float2 v[U];
+      for (int i0 = 0; i0 < NE; i0 += U) {
+        float2 v[U];
 #pragma unroll
-      for (int u = 0; u < U; ++u) v[u] = s[(r0 + (i0 + u) * RPI) * RS + c];
-      h.template operator()<U>(g0 + r0 + i0 * RPI, RPI, c, 0, v);
+        for (int u = 0; u < U; ++u) v[u] = s[(r0 + (i0 + u) * RPI) * RS + c];
+        h.template operator()<U>(g0 + r0 + i0 * RPI, RPI, c, 0, v);
 #pragma unroll
-      for (int u = 0; u < U; ++u) s[(r0 + (i0 + u) * RPI) * RS + c] = v[u];
+        for (int u = 0; u < U; ++u) s[(r0 + (i0 + u) * RPI) * RS + c] = v[u];
+      }
+    } else {
+      static_assert(L % U == 0, "batch must divide the rows");
+#pragma unroll 1
+      for (int hc = 0; hc < N / T; ++hc) {
+        const int c = threadIdx.x + hc * T;
+#pragma unroll 1
+        for (int i0 = 0; i0 < L; i0 += U) {
+          float2 v[U];
+#pragma unroll
+          for (int u = 0; u < U; ++u) v[u] = s[(i0 + u) * RS + c];
+          h.template operator()<U>(g0 + i0, 1, c, 0, v);
+#pragma unroll
+          for (int u = 0; u < U; ++u) s[(i0 + u) * RS + c] = v[u];
+        }
+      }
     }
     __syncthreads();
   }
-  // k-space pointwise pass: thread t owns local row t % 64 and columns t / 64 + 8 i.
+  // k-space pointwise pass: thread t owns local row t % L and columns t / L + (T / L) i.
   template <int U, class H>
   __device__ static void pointwise_k(float2* s, H& h) {
     constexpr int NE = L * N / T, CPI = T / L;

@@ -517,11 +517,11 @@ struct Fft2 {
   }
 };
 
-// tw[t] = exp(-2 pi i t / N) for t < N, written by the first N threads.
+// tw[t] = exp(-2 pi i t / N) for t < N, written by the CTA's threads (a CTA smaller than N writes
+// several each).
 template <int N>
 __device__ __forceinline__ void build_twiddles(float2* tw) {
-  const int t = threadIdx.x;
-  if (t < N) {
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
     float sn, cs;
     sincospif(2.0f * (float)t / (float)N, &sn, &cs);
     tw[t] = make_float2(cs, -sn);

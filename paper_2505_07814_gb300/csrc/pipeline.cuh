@@ -130,16 +130,18 @@ template <>
 struct Launch<128> {
   static constexpr int T = 512, TF = PTY_TF128, TA = PTY_TA128, MINB_F = 1, MINB_A = 1;
 };
-// N = 256: every wave kernel runs as four-CTA clusters (fft_cluster.cuh), 512 threads per CTA.
+// N = 256: every wave kernel runs as clusters of PTY_N256_CTAS CTAs (fft_cluster.cuh): four CTAs
+// of 512 threads (one per SM), or eight of 128 threads (three per SM, from different clusters).
 template <>
 struct Launch<256> {
-  static constexpr int T = 512, TF = 512, TA = 512, MINB_F = 1, MINB_A = 1;
+  static constexpr int T = PTY_N256_CTAS == 8 ? 128 : 512, TF = T, TA = T;
+  static constexpr int MINB_F = PTY_N256_CTAS == 8 ? 3 : 1, MINB_A = MINB_F;
 };
 
-// Rows of a wave one CTA holds in shared memory (a quarter of the wave at N = 256).
+// Rows of a wave one CTA holds in shared memory (1 / PTY_N256_CTAS of the wave at N = 256).
 template <int N>
 __host__ __device__ constexpr int wave_rows() {
-  return N == 256 ? 64 : N;
+  return N == 256 ? 256 / PTY_N256_CTAS : N;
 }
 
 // exp(i pi x); x is reduced modulo 2 in double precision before the float sincospi.
@@ -335,13 +337,13 @@ __device__ __forceinline__ void prefetch_l1(const void* base, int bytes) {
   for (int l = threadIdx.x * 128; l < bytes; l += blockDim.x * 128)
     asm volatile("prefetch.global.L1 [%0];" ::"l"(reinterpret_cast<const char*>(base) + l));
 }
-// Rows [0, N) of an N-wide patch with row stride W (elements), one row per thread tid < N.  With
+// Rows [0, N) of an N-wide patch with row stride W (elements), one row per thread and pass.  With
 // C > 1 CTAs per wave, CTA `rank` takes its own N / C columns of every row (the columns its
 // cross-CTA step reads).
 template <int N, int C = 1>
 __device__ __forceinline__ void prefetch_patch(const float2* base, int W, int rank = 0) {
-  if (threadIdx.x < N)
-    prefetch_l2(base + (size_t)threadIdx.x * W + rank * (N / C), sizeof(float2) * (N / C));
+  for (int r = threadIdx.x; r < N; r += blockDim.x)
+    prefetch_l2(base + (size_t)r * W + rank * (N / C), sizeof(float2) * (N / C));
 }
 // A contiguous N*N block, split over the first 8 threads.
 template <int N>
@@ -399,8 +401,7 @@ __device__ __forceinline__ bool stage_wait(uint32_t bar, uint32_t parity) {
 template <int N>
 __device__ void fwd_tables(float2* ra0, float2* ra1, float2* pm0, float2* pm1, float d0, float d1, float th0, float th1,
                            float dz, float dx, float lam) {
-  const int tid = threadIdx.x;
-  if (tid < N) {
+  for (int tid = threadIdx.x; tid < N; tid += blockDim.x) {
     const int q0 = signed_bin<N>(kbin0<N>(tid)), q1 = signed_bin<N>(kbin1<N>(tid));
     const float inv_nn = 1.0f / (float)(N * N);
     ra0[tid] = cscale(expipi(-2.0 * q0 * (double)d0 / N), inv_nn);
@@ -417,9 +418,8 @@ template <int N>
 __device__ void adj_tables(float2* cm0, float2* cm1, float2* cr0, float2* cr1, float* e0, float* e1, float* c0,
                            float* c1, float* f0, float* f1, float d0, float d1, float th0, float th1, float dz,
                            float dx, float lam) {
-  const int tid = threadIdx.x;
   constexpr int NN = N * N;
-  if (tid < N) {
+  for (int tid = threadIdx.x; tid < N; tid += blockDim.x) {
     // axis-0 tables are indexed by k-space row p0, axis-1 tables by k-space column p1
     const int q0 = signed_bin<N>(kbin0<N>(tid)), q1 = signed_bin<N>(kbin1<N>(tid));
     const float inv_nn = 1.0f / (float)NN;

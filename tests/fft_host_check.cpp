@@ -19,6 +19,7 @@ using cd = std::complex<double>;
 
 template <class F>
 static void each_thread(int T, F&& f) {
+  blockDim.x = T;
   for (int t = 0; t < T; ++t) {
     threadIdx.x = t;
     f();
@@ -112,14 +113,16 @@ static void run(unsigned seed) {
   std::printf("N %d T %d fwd %.3e inv %.3e fused %.3e\n", N, T, e_fwd, e_inv, std::max(e_f1, e_f2));
 }
 
-// N = 256 on four emulated CTAs: CTA q holds rows [64 q, 64 q + 64) as float2 [64][257]; k-space
-// row p0 = 64 q + local row.  The cluster FFT's sub-steps are each one barrier-delimited step.
+// N = 256 on C emulated CTAs (PTY_N256_CTAS: 4 of 512 threads or 8 of 128): CTA q holds rows
+// [L q, L q + L) as float2 [L][257]; k-space row p0 = L q + local row.  The cluster FFT's
+// sub-steps are each one barrier-delimited step.
 static void run256(unsigned seed) {
-  constexpr int N = 256, T = 512, L = 64;
+  constexpr int N = 256, C = PTY_N256_CTAS, T = C == 8 ? 128 : 512, L = N / C;
   using F = pty::Fft2<N, T>;
+  static_assert(F::C == C && F::L == L, "cluster shape");
   constexpr int RS = F::RS;
-  std::vector<float2> cta[4];
-  for (int q = 0; q < 4; ++q) {
+  std::vector<float2> cta[C];
+  for (int q = 0; q < C; ++q) {
     cta[q].assign(L * RS, make_float2(0.f, 0.f));
     host_cta_base[q] = reinterpret_cast<char*>(cta[q].data());
   }
@@ -150,7 +153,7 @@ static void run256(unsigned seed) {
   pty::NoHook none;
   // one barrier-delimited step on every thread of every CTA
   auto step = [&](auto&& f) {
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < C; ++q) {
       host_cluster_rank = q;
       each_thread(T, [&] { f(cta[q].data()); });
     }

@@ -14,6 +14,7 @@ struct HostThreadIdx {
   int x = 0, y = 0, z = 0;
 };
 inline HostThreadIdx threadIdx;  // set by the caller before each emulated thread's call
+inline HostThreadIdx blockDim;   // the emulated CTA's thread count, set by the caller
 inline void __syncthreads() {}
 inline void sincospif(float x, float* s, float* c) {
   const double a = 3.14159265358979323846 * (double)x;
