@@ -309,7 +309,6 @@ __global__ void __launch_bounds__(256) k_stage(StageArgs g) {
   const int sl = g.sl;
   float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   constexpr int U = 8;
-  constexpr bool kNatural = ST == GS_TRANS || ST == GS_ADJTRANS;
   // natural stages: thread owns column tid % N, rows tid / N + STEP i; k-space stages: row p0 = tid % N,
   // columns p1 = tid / N + STEP i (the buffer is stored p1 * N + p0)
   const int lo = tid % N, hi0 = tid / N;

@@ -18,7 +18,9 @@
 // rows 16 a + b of one column, lanes on consecutive columns), "block" the two local steps in
 // between, "row" the step next to k-space (hook on 16 consecutive positions of one local row, lanes
 // on consecutive rows).  Every cross-CTA step starts and ends with a cluster barrier; all CTAs of a
-// cluster run the same sequence of steps.  Every step has L N / 16 tasks per CTA.
+// cluster run the same sequence of steps.  Every step has L N / 16 tasks per CTA.  The local steps
+// (X2, RA, RB, the k-space pass) touch 16-row blocks of one CTA only, so with PTY_GROUPS256 = G > 1
+// each of G thread groups works on its own L / G rows and waits only for its own threads.
 #pragma once
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
@@ -41,6 +43,14 @@
 // threads, up to three per SM from different clusters)
 #ifndef PTY_N256_CTAS
 #define PTY_N256_CTAS 4
+#endif
+
+// Thread groups of the local steps (1, 2 or 4): group g of the CTA's threads owns local rows
+// [g L / G, (g + 1) L / G), and every step between two cross-CTA steps touches one group's rows
+// only, so such a step ends on the group's own named barrier instead of the CTA's.  Large-window
+// workload: forward 32.39 / 32.82 / 31.25 ms and adjoint 42.40 / 42.15 / 42.21 ms at 1 / 2 / 4.
+#ifndef PTY_GROUPS256
+#define PTY_GROUPS256 4
 #endif
 
 namespace pty {
@@ -81,6 +91,8 @@ struct Fft2<256, T> {
   static constexpr int AP = 16 / C;                    // values of a (rows 16 a + b) per CTA
   static constexpr int TASKS = L * N / 16, NT = TASKS / T;  // tasks per step per CTA, per thread
   static_assert((C == 4 || C == 8) && TASKS % T == 0 && NT % 2 == 0, "cluster shape");
+  static constexpr int G = PTY_GROUPS256, TG = T / G, RG = L / G;  // groups, their threads and rows
+  static_assert(T % G == 0 && (L / 16) % G == 0 && TG % 32 == 0, "thread groups");
   template <class H>
   static constexpr bool kPlain = std::is_same_v<std::decay_t<H>, NoHook>;
   // Both tasks of a step may be read first when the step has no hook, or a hook that declares
@@ -92,6 +104,30 @@ struct Fft2<256, T> {
   }
 
   __device__ static int rank() { return (int)cooperative_groups::this_cluster().block_rank(); }
+  __device__ static int grp() { return G == 1 ? 0 : (int)threadIdx.x / TG; }
+  __device__ static int gtid() { return G == 1 ? (int)threadIdx.x : (int)threadIdx.x % TG; }
+  // end of a local step: the group's barrier (named barrier 1 + g; 0 is the CTA's)
+  __device__ static void group_sync() {
+#ifdef __CUDA_ARCH__
+    if constexpr (G > 1) {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / TG), "r"(TG) : "memory");
+      return;
+    }
+#endif
+    __syncthreads();
+  }
+  // task i of this thread in X2: column c, 16-row block blk (the group's blocks only)
+  __device__ static void x2_task(int i, int& c, int& blk) {
+    const int t = gtid() + i * TG;
+    c = t % N;
+    blk = grp() * (L / 16 / G) + t / N;
+  }
+  // task i of this thread in RA / RB: local row r (the group's rows only) and digit d
+  __device__ static void row_task(int i, int& r, int& d) {
+    const int t = gtid() + i * TG;
+    r = grp() * RG + t % RG;
+    d = t / RG;
+  }
   __device__ static void cluster_sync() { cooperative_groups::this_cluster().sync(); }
   __device__ static float2* remote(float2* s, int q) { return cooperative_groups::this_cluster().map_shared_rank(s, q); }
 
@@ -157,27 +193,31 @@ struct Fft2<256, T> {
   __device__ static void x2_step(float2* s) {
     run_tasks<NT, PTY_PRELOAD != 0>(
         [&](int i, float2* v) {
-          const int t = threadIdx.x + i * T, c = t % N, g = t / N;
+          int c, g;
+          x2_task(i, c, g);
 #pragma unroll
           for (int b = 0; b < 16; ++b) v[b] = s[(16 * g + b) * RS + c];
         },
         [&](int i, float2* v) {
-          const int t = threadIdx.x + i * T, c = t % N, g = t / N;
+          int c, g;
+          x2_task(i, c, g);
           dft<16, INV>(v);
 #pragma unroll
           for (int b = 0; b < 16; ++b) s[(16 * g + b) * RS + c] = v[b];
         });
-    __syncthreads();
+    group_sync();
   }
   __device__ static void ra_fwd(float2* s, const float2* tw) {
     run_tasks<NT, PTY_PRELOAD != 0>(
         [&](int i, float2* v) {
-          const int t = threadIdx.x + i * T, r = t % L, b = t / L;
+          int r, b;
+          row_task(i, r, b);
 #pragma unroll
           for (int a = 0; a < 16; ++a) v[a] = s[r * RS + 16 * a + b];
         },
         [&](int i, float2* v) {
-          const int t = threadIdx.x + i * T, r = t % L, b = t / L;
+          int r, b;
+          row_task(i, r, b);
           dft<16, false>(v);
           if (!PTY_TW_SKIP || b != 0) {
 #pragma unroll
@@ -186,17 +226,19 @@ struct Fft2<256, T> {
 #pragma unroll
           for (int k1 = 0; k1 < 16; ++k1) s[r * RS + 16 * k1 + b] = v[k1];
         });
-    __syncthreads();
+    group_sync();
   }
   __device__ static void ra_inv(float2* s, const float2* tw) {
     run_tasks<NT, PTY_PRELOAD != 0>(
         [&](int i, float2* v) {
-          const int t = threadIdx.x + i * T, r = t % L, b = t / L;
+          int r, b;
+          row_task(i, r, b);
 #pragma unroll
           for (int k1 = 0; k1 < 16; ++k1) v[k1] = s[r * RS + 16 * k1 + b];
         },
         [&](int i, float2* v) {
-          const int t = threadIdx.x + i * T, r = t % L, b = t / L;
+          int r, b;
+          row_task(i, r, b);
           if (!PTY_TW_SKIP || b != 0) {
 #pragma unroll
             for (int k1 = 1; k1 < 16; ++k1) v[k1] = cmulc(tw[b * k1], v[k1]);
@@ -205,7 +247,7 @@ struct Fft2<256, T> {
 #pragma unroll
           for (int a = 0; a < 16; ++a) s[r * RS + 16 * a + b] = v[a];
         });
-    __syncthreads();
+    group_sync();
   }
   // RB, RB^-1 and the fused RB -> hook -> RB^-1.  k-space elements of task (r, k1): positions
   // 16 k1 + k2 of local row r, global k-space row L q + r.
@@ -214,14 +256,16 @@ struct Fft2<256, T> {
     const int q = rank();
     run_tasks<NT, PTY_PRELOAD && preload_ok<H>()>(
         [&](int i, float2* v) {
-          const int t = threadIdx.x + i * T, r = t % L, k1 = t / L;
+          int r, k1;
+          row_task(i, r, k1);
           if (!(std::remove_reference_t<H>::kReplaces && !FWD_IN)) {
 #pragma unroll
             for (int b = 0; b < 16; ++b) v[b] = s[r * RS + 16 * k1 + b];
           }
         },
         [&](int i, float2* v) {
-          const int t = threadIdx.x + i * T, r = t % L, k1 = t / L;
+          int r, k1;
+          row_task(i, r, k1);
           if (FWD_IN) dft<16, false>(v);
           hook<16>(h, L * q + r, 0, 16 * k1, 1, v);
           if (INV_OUT) dft<16, true>(v);
@@ -230,7 +274,7 @@ struct Fft2<256, T> {
             for (int b = 0; b < 16; ++b) s[r * RS + 16 * k1 + b] = v[b];
           }
         });
-    __syncthreads();
+    group_sync();
   }
 
   // ---- the step API shared with the single-CTA FFT ----
@@ -271,6 +315,7 @@ struct Fft2<256, T> {
     col_fwd(s, tw, load);
     block_fwd(s, tw);
     row_fwd<WRITE>(s, store);
+    if constexpr (G > 1) __syncthreads();  // the caller may read any row
   }
   template <class LH = NoHook>
   __device__ static void inverse(float2* s, const float2* tw, LH&& load = LH()) {
@@ -283,6 +328,7 @@ struct Fft2<256, T> {
   // t / 256 + (T / N) i; T < N: thread t owns columns t + T h and every local row.
   template <int U, class H>
   __device__ static void pointwise(float2* s, H& h) {
+    if constexpr (G > 1) __syncthreads();  // reads every group's rows
     const int g0 = L * rank();
     if constexpr (T >= N) {
       constexpr int NE = L * N / T, RPI = T / N;
@@ -315,12 +361,13 @@ struct Fft2<256, T> {
     }
     __syncthreads();
   }
-  // k-space pointwise pass: thread t owns local row t % L and columns t / L + (T / L) i.
+  // k-space pointwise pass: thread j of group g owns local row g RG + j % RG and columns
+  // j / RG + (T / L) i.
   template <int U, class H>
   __device__ static void pointwise_k(float2* s, H& h) {
     constexpr int NE = L * N / T, CPI = T / L;
-    static_assert(NE % U == 0, "batch must divide the elements per thread");
-    const int r = threadIdx.x % L, c0 = threadIdx.x / L, g = L * rank() + r;
+    static_assert(NE % U == 0 && TG / RG == CPI, "batch must divide the elements per thread");
+    const int r = grp() * RG + gtid() % RG, c0 = gtid() / RG, g = L * rank() + r;
 #pragma unroll 1
     for (int i0 = 0; i0 < NE; i0 += U) {
       float2 v[U];
@@ -330,7 +377,7 @@ struct Fft2<256, T> {
 #pragma unroll
       for (int u = 0; u < U; ++u) s[r * RS + c0 + (i0 + u) * CPI] = v[u];
     }
-    __syncthreads();
+    group_sync();
   }
 };
 

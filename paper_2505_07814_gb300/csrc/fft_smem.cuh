@@ -206,6 +206,15 @@ struct NoHook {
 #define PTY_TW_SKIP 1
 #endif
 
+// Thread groups of the row-local steps (1, 2 or 4).  The block and row steps and the k-space pass
+// touch groups of four rows only, so with G > 1 group g of the CTA's threads takes rows
+// [g N / G, (g + 1) N / G) in those steps and they end on the group's own named barrier; the column
+// steps, which mix all rows, start with the CTA's barrier.  Multislice workload: forward 2.204 /
+// 2.286 / 2.281 ms and adjoint 3.453 / 3.599 / 3.551 ms at 1 / 2 / 4, so one group stays.
+#ifndef PTY_GROUPS
+#define PTY_GROUPS 1
+#endif
+
 template <int N, int T>
 struct Fft2 {
   static constexpr int A = N / 4, RS = N + 1;
@@ -216,6 +225,24 @@ struct Fft2 {
   static constexpr int NBLK = A * A / T;    // block-step tasks per thread: (k1, n2)
   static constexpr int NROW = 4 * N / T;    // row-step tasks per thread: (r, k1)
   static_assert(NCOL * T == 4 * N && NBLK * T == A * A, "tasks must divide the CTA");
+  static constexpr int G = PTY_GROUPS, TG = T / G, RG = N / G;  // groups, their threads and rows
+  static_assert(T % G == 0 && TG % 32 == 0 && A % G == 0 && TG % RG == 0 || G == 1, "thread groups");
+  __device__ static int grp() { return G == 1 ? 0 : (int)threadIdx.x / TG; }
+  __device__ static int gtid() { return G == 1 ? (int)threadIdx.x : (int)threadIdx.x % TG; }
+  // end of a row-local step: the group's barrier (named barrier 1 + g; 0 is the CTA's)
+  __device__ static void group_sync() {
+#ifdef __CUDA_ARCH__
+    if constexpr (G > 1) {
+      asm volatile("bar.sync %0, %1;" ::"r"(1 + (int)threadIdx.x / TG), "r"(TG) : "memory");
+      return;
+    }
+#endif
+    __syncthreads();
+  }
+  // start of a step that reads every group's rows
+  __device__ static void all_sync() {
+    if constexpr (G > 1) __syncthreads();
+  }
   template <class H>
   static constexpr bool kPlain = std::is_same_v<std::decay_t<H>, NoHook>;
 
@@ -231,6 +258,7 @@ struct Fft2 {
   // ---- forward steps ----
   template <class LH>
   __device__ static void col_fwd(float2* s, const float2* tw, LH& lh) {
+    all_sync();
 #pragma unroll 1
     for (int i = 0; i < NCOL; ++i) {
       const int t = threadIdx.x + i * T;
@@ -257,16 +285,16 @@ struct Fft2 {
   static constexpr int BG = (PTY_PRELOAD_BLOCK >= 4 && NBLK % 4 == 0) ? 4
                             : (PTY_PRELOAD_BLOCK >= 2 && NBLK % 2 == 0) ? 2 : 1;
   __device__ static void block_load(const float2* s, int i, float2 (&b)[4][4]) {
-    const int t = threadIdx.x + i * T;
-    const int n2 = t % A, k1 = t / A;
+    const int t = gtid() + i * TG;
+    const int n2 = t % A, k1 = grp() * (A / G) + t / A;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
       for (int p = 0; p < 4; ++p) b[q][p] = s[(4 * k1 + q) * RS + A * p + n2];
   }
   __device__ static void block_store(float2* s, int i, const float2 (&b)[4][4]) {
-    const int t = threadIdx.x + i * T;
-    const int n2 = t % A, k1 = t / A;
+    const int t = gtid() + i * TG;
+    const int n2 = t % A, k1 = grp() * (A / G) + t / A;
 #pragma unroll
     for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -280,7 +308,7 @@ struct Fft2 {
       for (int j = 0; j < BG; ++j) block_load(s, i0 + j, b[j]);
 #pragma unroll
       for (int j = 0; j < BG; ++j) {
-        const int n2 = (threadIdx.x + (i0 + j) * T) % A;
+        const int n2 = (gtid() + (i0 + j) * TG) % A;
 #pragma unroll
         for (int p = 0; p < 4; ++p) {
           float2 col[4] = {b[j][0][p], b[j][1][p], b[j][2][p], b[j][3][p]};
@@ -299,14 +327,14 @@ struct Fft2 {
         block_store(s, i0 + j, b[j]);
       }
     }
-    __syncthreads();
+    group_sync();
   }
   template <bool WRITE, class SH>
   __device__ static void row_fwd(float2* s, SH& sh) {
 #pragma unroll 1
     for (int i = 0; i < NROW; ++i) {
-      const int t = threadIdx.x + i * T;
-      const int r = t % N, k1 = t / N;
+      const int t = gtid() + i * TG;
+      const int r = grp() * RG + t % RG, k1 = t / RG;
       float2 v[A];
 #pragma unroll
       for (int n2 = 0; n2 < A; ++n2) v[n2] = s[r * RS + A * k1 + n2];
@@ -317,7 +345,7 @@ struct Fft2 {
         for (int k2 = 0; k2 < A; ++k2) s[r * RS + A * k1 + k2] = v[k2];
       }
     }
-    __syncthreads();
+    group_sync();
   }
 
   // ---- inverse steps (mirror images) ----
@@ -325,8 +353,8 @@ struct Fft2 {
   __device__ static void row_inv(float2* s, const float2* tw, LH& lh) {
 #pragma unroll 1
     for (int i = 0; i < NROW; ++i) {
-      const int t = threadIdx.x + i * T;
-      const int r = t % N, k1 = t / N;
+      const int t = gtid() + i * TG;
+      const int r = grp() * RG + t % RG, k1 = t / RG;
       float2 v[A];
       if (!std::remove_reference_t<LH>::kReplaces) {
 #pragma unroll
@@ -341,7 +369,7 @@ struct Fft2 {
 #pragma unroll
       for (int n2 = 0; n2 < A; ++n2) s[r * RS + A * k1 + n2] = v[n2];
     }
-    __syncthreads();
+    group_sync();
   }
   __device__ static void block_inv(float2* s, const float2*) {
 #pragma unroll 1
@@ -363,9 +391,10 @@ struct Fft2 {
         block_store(s, i0 + j, b[j]);
       }
     }
-    __syncthreads();
+    group_sync();
   }
   __device__ static void col_inv(float2* s, const float2* tw) {
+    all_sync();
 #pragma unroll 1
     for (int i = 0; i < NCOL; ++i) {
       const int t = threadIdx.x + i * T;
@@ -389,6 +418,7 @@ struct Fft2 {
   // (starting the next forward FFT).  FWD = false: stop after the hook (nothing written back).
   template <bool FWD, class H>
   __device__ static void col_inv_fwd(float2* s, const float2* tw, H& h) {
+    all_sync();
 #pragma unroll 1
     for (int i = 0; i < NCOL; ++i) {
       const int t = threadIdx.x + i * T;
@@ -419,8 +449,8 @@ struct Fft2 {
   __device__ static void row_fwd_inv(float2* s, const float2* tw, H& h) {
 #pragma unroll 1
     for (int i = 0; i < NROW; ++i) {
-      const int t = threadIdx.x + i * T;
-      const int r = t % N, k1 = t / N;
+      const int t = gtid() + i * TG;
+      const int r = grp() * RG + t % RG, k1 = t / RG;
       float2 v[A];
 #pragma unroll
       for (int n2 = 0; n2 < A; ++n2) v[n2] = s[r * RS + A * k1 + n2];
@@ -434,7 +464,7 @@ struct Fft2 {
 #pragma unroll
       for (int n2 = 0; n2 < A; ++n2) s[r * RS + A * k1 + n2] = v[n2];
     }
-    __syncthreads();
+    group_sync();
   }
 
   // natural s[r][c] -> k-space s[p0][p1] (unnormalised forward DFT).  `load` sees natural (r, c);
@@ -444,6 +474,7 @@ struct Fft2 {
     col_fwd(s, tw, load);
     block_fwd(s, tw);
     row_fwd<WRITE>(s, store);
+    all_sync();  // the caller may read any row
   }
   // k-space s[p0][p1] -> natural s[r][c] (unnormalised inverse DFT); `load` sees k-space (p0, p1).
   template <class LH = NoHook>
@@ -460,6 +491,7 @@ struct Fft2 {
   __device__ static void pointwise(float2* s, H& h) {
     constexpr int NE = N * N / T, RPI = T / N;
     static_assert(NE % U == 0, "batch must divide the elements per thread");
+    all_sync();
     const int c = threadIdx.x % N, r0 = threadIdx.x / N;
 #pragma unroll 1
     for (int i0 = 0; i0 < NE; i0 += U) {
@@ -480,7 +512,7 @@ struct Fft2 {
   __device__ static void pointwise_rows(float2* s, H& h) {
     constexpr int NE = N * N / T, CPI = T / N;
     static_assert(NE % U == 0, "batch must divide the elements per thread");
-    const int r = threadIdx.x % N, c0 = threadIdx.x / N;
+    const int r = grp() * RG + gtid() % RG, c0 = gtid() / RG;
 #pragma unroll 1
     for (int i0 = 0; i0 < NE; i0 += U) {
       float2 v[U];
@@ -490,7 +522,7 @@ struct Fft2 {
 #pragma unroll
       for (int u = 0; u < U; ++u) s[r * RS + c0 + (i0 + u) * CPI] = v[u];
     }
-    __syncthreads();
+    group_sync();
   }
 
   // k-space pointwise pass (lanes on consecutive rows, matching the transposed global buffers)
@@ -502,6 +534,7 @@ struct Fft2 {
   // Apply a hook to every element of the natural-layout array (same task shape as the col step).
   template <class H>
   __device__ static void elementwise(float2* s, H&& h) {
+    all_sync();
 #pragma unroll 1
     for (int i = 0; i < NCOL; ++i) {
       const int t = threadIdx.x + i * T;
