@@ -135,6 +135,7 @@ struct Fft2<256, T> {
   __device__ static __forceinline__ void hook(H& h, int row0, int rs, int col0, int cs, float2* v) {
     if constexpr (!kPlain<H>) {
       constexpr int KC = std::decay_t<H>::kChunk < K ? std::decay_t<H>::kChunk : K;
+      static_assert(K % KC == 0, "a chunk must divide the task");
 #pragma unroll
       for (int q = 0; q < K; q += KC) h.template operator()<KC>(row0 + q * rs, rs, col0 + q * cs, cs, v + q);
     }

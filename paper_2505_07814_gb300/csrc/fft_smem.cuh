@@ -249,7 +249,9 @@ struct Fft2 {
   template <class H>
   __device__ static __forceinline__ void hook(H& h, int row0, int rs, int col0, int cs, float2* v) {
     if constexpr (!kPlain<H>) {
-      constexpr int KC = std::decay_t<H>::kChunk;
+      // chunks of kChunk elements, at most the task's A
+      constexpr int KC = std::decay_t<H>::kChunk < A ? std::decay_t<H>::kChunk : A;
+      static_assert(A % KC == 0, "a chunk must divide the task");
 #pragma unroll
       for (int q = 0; q < A; q += KC) h.template operator()<KC>(row0 + q * rs, rs, col0 + q * cs, cs, v + q);
     }

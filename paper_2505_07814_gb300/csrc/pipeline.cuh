@@ -45,18 +45,21 @@
 #ifndef PTY_ADJ_GROUP
 #define PTY_ADJ_GROUP 32
 #endif
+// The propagation step inside the row transform (0) reads each task's 32 spectrum values in one
+// batch (PTY_KQ = 32): multislice adjoint 3.274 ms against 3.455 as its own pass (1)
 #ifndef PTY_ADJ_SPLIT_ROW
-#define PTY_ADJ_SPLIT_ROW 1
+#define PTY_ADJ_SPLIT_ROW 0
 #endif
 // The same two choices for the N = 256 cluster adjoint.  Its column step is the cross-CTA step, so
 // a separate transmission pass costs a second pass through distributed shared memory per slice
-// (large-window workload: adjoint 63.5 ms split, 46.8 ms fused); the propagation pass measured
-// slightly faster split (45.0 against 45.9 ms).
+// (large-window workload: adjoint 63.5 ms split, 46.8 ms fused).  The propagation step fused into
+// the row transform with each task's 16 spectrum loads in one batch: 39.98 ms against 42.41 as its
+// own pass (with batches of 4 the fused form was the slower one, 44.17 ms).
 #ifndef PTY_ADJ256_SPLIT_COL
 #define PTY_ADJ256_SPLIT_COL 0
 #endif
 #ifndef PTY_ADJ256_SPLIT_ROW
-#define PTY_ADJ256_SPLIT_ROW 1
+#define PTY_ADJ256_SPLIT_ROW 0
 #endif
 #ifndef PTY_FWD_SPLIT_COL
 #define PTY_FWD_SPLIT_COL 0
@@ -114,8 +117,9 @@
 #ifndef PTY_KA
 #define PTY_KA 4
 #endif
+// (the adjoint's spectrum reads in the fused propagation step; capped at a task's elements)
 #ifndef PTY_KQ
-#define PTY_KQ 4
+#define PTY_KQ 32
 #endif
 #ifndef PTY_KR
 #define PTY_KR 4
