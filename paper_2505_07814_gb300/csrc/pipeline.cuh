@@ -1166,6 +1166,17 @@ template <int N, int T>
 __host__ __device__ constexpr bool adj_staged() {
   return PTY_ADJ_STAGE && N == 128 && PTY_ADJ_SPLIT_COL && PTY_ADJ_SPLIT_ROW;
 }
+// Large-window adjoint: the cross-CTA column step of CTA q reads the entering wave at every row and
+// at q's column slab [N/C q, N/C (q + 1)).  With PTY_ADJ256_STAGE = 1 warp 0 copies rows 0..N/2-1 of
+// that slab of the next slice's checkpoint (N/2 row pieces of N/C float2, 64 KB) into the free
+// shared memory right after the current column step, five passes before the next one reads it.
+#ifndef PTY_ADJ256_STAGE
+#define PTY_ADJ256_STAGE 0
+#endif
+template <int N>
+__host__ __device__ constexpr bool adj256_staged() {
+  return PTY_ADJ256_STAGE && N == 256 && !PTY_ADJ256_SPLIT_COL;
+}
 // Whether the adjoint's transmission (COL) and propagation (ROW) steps run as their own pointwise
 // passes (true) or inside the neighbouring transform steps (false), per window size.
 template <int N>
@@ -1187,7 +1198,7 @@ __host__ __device__ constexpr size_t adj_stage_offset() {
 template <int N, int T>
 __host__ __device__ constexpr size_t adj_smem_bytes() {
   static_assert(T <= 1024, "reduction slots");
-  return adj_staged<N, T>() ? adj_stage_offset<N>() + kStageBytes + 16
+  return adj_staged<N, T>() || adj256_staged<N>() ? adj_stage_offset<N>() + kStageBytes + 16
                             : sizeof(float2) * ((size_t)wave_rows<N>() * (N + 1) + 5 * N) + sizeof(float) * 6 * N +
                                   sizeof(double) * 5 * (T / 32);
 }
@@ -1233,7 +1244,8 @@ struct AdjTransLoad {
   float2* gTs;       // patch corner in the dL/dT accumulator
   const float2* ck;  // checkpoint of the wave entering slice s, or nullptr (no object gradient)
   int W;
-  bool stg = false;  // rows 0..N/2-1 of ck are in the stage (adj_stage)
+  bool stg = false;  // rows 0..N/2-1 of ck are in the stage (adj_stage): (r, c) at r * st_ld + c - st_c0
+  int st_ld = N, st_c0 = 0;
   template <int K>
   __device__ __forceinline__ void operator()(int r0, int rs, int c0, int cs, float2* v) {
     float2 t[K], ps[K];
@@ -1243,7 +1255,7 @@ struct AdjTransLoad {
     for (int k = 0; k < K; ++k) {
       const int r = r0 + k * rs, c = c0 + k * cs;
       t[k] = ld_ro(Ts + (size_t)r * W + c);
-      if (ck) ps[k] = staged ? st[r * N + c] : ld_once(ck + r * N + c);
+      if (ck) ps[k] = staged ? st[r * st_ld + c - st_c0] : ld_once(ck + r * N + c);
     }
 #pragma unroll
     for (int k = 0; k < K; ++k) {
@@ -1420,6 +1432,30 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
       if (want_obj) stage_issue(sbar, stg, ck_base + (size_t)(a.s1 - 1) * NN, kStageBytes);
     }
   }
+  // Large-window stage (adj256_staged): one copy batch per slice, issued by warp 0 after the column
+  // step that read the previous batch and waited for by every thread before the next column step,
+  // so the k-th wait is again on parity k & 1.  Warp 0 stops issuing once its lane 0 gave up.
+  constexpr bool kSlab = adj256_staged<N>();
+  constexpr int SW = N / F::C;  // columns of the slab
+  auto stage_slab = [&](int sl) {
+    if (tid < 32 && !(__shfl_sync(0xffffffffu, sst, 0) >> 31)) {
+      constexpr uint32_t piece = SW * sizeof(float2);
+      static_assert(!kSlab || (N / 2) * piece == kStageBytes, "the slab half fills the stage");
+      const uint64_t pol = evict_first_policy();
+      if (tid == 0) stage_expect(sbar, (N / 2) * piece);
+      __syncwarp();
+      const float2* src = ck_base + (size_t)sl * NN + SW * F::rank();
+      for (int r = tid; r < N / 2; r += 32) stage_copy(sbar, stg + r * SW, src + (size_t)r * N, piece, pol);
+    }
+  };
+  if constexpr (kSlab) {
+    if (tid == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sbar) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (tid < 32) __syncwarp();
+    if (want_obj) stage_slab(a.s1 - 1);
+  }
 
   build_twiddles<N>(tw);
   adj_tables<N>(cm0, cm1, cr0, cr1, e0, e1, c0, c1, f0, f1, d0, d1, th0, th1, dz, a.dx, a.lam);
@@ -1481,7 +1517,17 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
 #endif
       F::col_fwd(s, tw, none);
       } else {
+        if constexpr (kSlab) {
+          if (want_obj) {
+            trans.stg = stage_get();
+            trans.st_ld = SW;
+            trans.st_c0 = SW * F::rank();
+          }
+        }
         F::template col_inv_fwd<true>(s, tw, trans);
+        if constexpr (kSlab) {  // every thread is past the column step: fetch the next slice's slab
+          if (want_obj && sl - 1 >= a.s0) stage_slab(sl - 1);
+        }
       }
 #if PTY_ADJ_PF == 1
       if (sl - 1 >= a.s0 && want_obj) prefetch_block<N>(ck_base + (size_t)(sl - 1) * NN);
@@ -1515,10 +1561,15 @@ __global__ void __launch_bounds__(T, Launch<N>::MINB_A) k_adjoint(AdjArgs a) {
       }
     } else if (want_obj) {
       if constexpr (kStage) trans.stg = stage_get();
+      if constexpr (kSlab) {
+        trans.stg = stage_get();
+        trans.st_ld = SW;
+        trans.st_c0 = SW * F::rank();
+      }
       F::template col_inv_fwd<false>(s, tw, trans);
     }
   }
-  if constexpr (kStage) {  // a copy whose wait gave up may still be in flight: give it time to land
+  if constexpr (kStage || kSlab) {  // a copy whose wait gave up may still be in flight: give it time to land
     if (tid == 0 && (sst >> 31)) stage_wait(sbar, sst & 1);
   }
 
