@@ -1154,7 +1154,7 @@ struct AdjArgs {
 };
 
 // Bulk-copy staging of the adjoint's once-read blocks (N = 128, split transmission and propagation
-// passes).  The checkpoint a slice's transmission pass reads and the spectrum its propagation pass
+// passes, so it also needs PTY_ADJ_SPLIT_ROW = 1).  The checkpoint a slice's transmission pass reads and the spectrum its propagation pass
 // reads are contiguous 128 KB blocks; the first half of each (natural rows 0..63, k-space columns
 // 0..63: the first two load batches of those passes) is copied by one thread with cp.async.bulk into
 // the 64 KB of shared memory the wave leaves free, three transform steps before it is read.  The
