@@ -143,9 +143,19 @@ struct Launch<128> {
 };
 // N = 256: every wave kernel runs as clusters of PTY_N256_CTAS CTAs (fft_cluster.cuh): four CTAs
 // of 512 threads (one per SM), or eight of 128 threads (three per SM, from different clusters).
+// PTY_TF256 / PTY_TA256 (0: the CTA size) give the forward / adjoint other thread counts with four
+// CTAs per wave.  Large-window workload at 256 threads (up to 255 registers): forward 33.86 ms
+// against 31.28, adjoint 49.79 against 39.97 (42.79 with checkpoint loads in batches of 16).
+#ifndef PTY_TF256
+#define PTY_TF256 0
+#endif
+#ifndef PTY_TA256
+#define PTY_TA256 0
+#endif
 template <>
 struct Launch<256> {
-  static constexpr int T = PTY_N256_CTAS == 8 ? 128 : 512, TF = T, TA = T;
+  static constexpr int T = PTY_N256_CTAS == 8 ? 128 : 512;
+  static constexpr int TF = PTY_TF256 ? PTY_TF256 : T, TA = PTY_TA256 ? PTY_TA256 : T;
   static constexpr int MINB_F = PTY_N256_CTAS == 8 ? 3 : 1, MINB_A = MINB_F;
 };
 
