@@ -90,6 +90,16 @@ def test_single_slice_single_mode_n64():
     _check_all(case, list(range(16)))
 
 
+def test_adjoint_wave_order_full_and_ragged_groups():
+    """40 positions: the adjoint takes its waves in groups of 32 positions (modes outermost inside a
+    group), so this batch has one full group and a ragged group of 8; every gradient must still be
+    the oracle's."""
+    case = make_case(N=64, M=3, Nz=2, scan=(5, 8), seed=21, step=4)
+    idx = list(range(40))
+    idx = idx[7:] + idx[:7]
+    _check_all(case, idx)
+
+
 def test_global_tilt_and_ragged_batch():
     case = make_case(N=64, M=2, Nz=4, scan=(3, 3), global_tilt=True, seed=3)
     _check_all(case, [8, 2, 5, 0, 7])  # B = 5: partial batch of a 9-position scan
