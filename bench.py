@@ -364,7 +364,9 @@ def run_nmse(args):
     initialiser's predictions (network trained on 65536 pairs from 16 other random volumes).  Adam
     on the object phase only (probe, positions, tilt, dz at the truth), batch 64, each start at the
     better of two phase learning rates.  Times are GPU seconds of reconstruction (and of inference +
-    stitching for the learned start), NMSE evaluation excluded."""
+    stitching for the learned start), NMSE evaluation excluded.  With --nmse-probe-defocus the same
+    comparison is repeated from a probe with the wrong defocus that Adam refines with the object
+    ("wrong_probe" in the line)."""
     import torch
 
     from paper_2505_07814_gb300 import _lib, build
@@ -416,6 +418,36 @@ def run_nmse(args):
     infer_s = ev0.elapsed_time(ev1) / 1e3
     learned, learned_runs = best(amp_c, ph_c)
     value = learned["seconds"] + infer_s if learned else None
+    wrong = None
+    if args.nmse_probe_defocus:
+        # Both starts begin from a probe with the wrong defocus and refine it with the object; the
+        # learned start is stitched with that probe too.
+        P0 = L.probe_estimate(prob, args.nmse_probe_defocus)
+        lr_p = args.nmse_probe_lr
+
+        def best_p(amp0, ph0):
+            runs = []
+            for lr in lrs:
+                hist, _ = L.reconstruct(prob, amp0, ph0, iters=args.nmse_probe_iters, batch=batch,
+                                        lr={"phase": lr, "probe": lr_p}, target=target, probe0=P0)
+                it, e, t = hist[-1]
+                runs.append({"lr_phase": lr, "reached": e <= target, "iterations": it, "nmse": e, "seconds": t,
+                             "nmse_start": hist[0][1]})
+            ok = [r for r in runs if r["reached"]]
+            return (min(ok, key=lambda r: r["seconds"]) if ok else None), runs
+
+        ev0.record()
+        amp_w, ph_w = L.initial_object(net_inf, prob, batch=1024, probe=P0)
+        ev1.record()
+        ev1.synchronize()
+        infer_w = ev0.elapsed_time(ev1) / 1e3
+        flat_w, flat_w_runs = best_p(amp_f, ph_f)
+        learned_w, learned_w_runs = best_p(amp_w, ph_w)
+        value_w = learned_w["seconds"] + infer_w if learned_w else None
+        wrong = {"probe_start": "the workload's probe model with defocus %g A (truth 50 A)" % args.nmse_probe_defocus,
+                 "lr_probe": lr_p, "max_iterations": args.nmse_probe_iters, "flat": flat_w, "flat_runs": flat_w_runs,
+                 "learned": dict(learned_w or {}, inference_stitch_seconds=infer_w), "learned_runs": learned_w_runs,
+                 "speedup_vs_flat": (flat_w["seconds"] / value_w) if (flat_w and value_w) else None}
     line = {"metric": "time to object NMSE <= %g (learned start vs flat start, 1 GB300)" % target, "value": value,
             "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic",
             "config": {"workload": WORKLOADS["c2"][0] + ", measured counts from the forward model (dose 1e5)",
@@ -426,6 +458,8 @@ def run_nmse(args):
             "training": {"pairs": 65536, "objects": 16, "epochs": args.nmse_epochs, "batch": 256,
                          "generation_seconds": gen_s, "training_seconds": train_s, "epoch_losses": losses},
             "speedup_vs_flat": (flat["seconds"] / value) if (flat and value) else None}
+    if wrong is not None:
+        line["wrong_probe"] = wrong
     print(json.dumps(line), flush=True)
 
 
@@ -865,6 +899,11 @@ def main():
     ap.add_argument("--nmse", action="store_true",
                     help="time to object NMSE: flat start vs learned initialiser (and split precision)")
     ap.add_argument("--nmse-target", type=float, default=0.05)
+    ap.add_argument("--nmse-probe-defocus", type=float, default=80.0,
+                    help="also time both starts from a probe with this defocus (A; the truth has 50), refined "
+                         "with the object (0: off)")
+    ap.add_argument("--nmse-probe-lr", type=float, default=1e-2)
+    ap.add_argument("--nmse-probe-iters", type=int, default=20)
     ap.add_argument("--nmse-epochs", type=int, default=8)
     ap.add_argument("--nmse-split", default="bf16,fp16", help="split-precision forms to time from the flat start")
     ap.add_argument("--cnn", action="store_true", help="learned-initialiser training / inference throughput")

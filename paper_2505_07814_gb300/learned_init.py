@@ -128,10 +128,20 @@ def probe_weight(probe: torch.Tensor) -> torch.Tensor:
     return (w / w.max())[q:q + N // 2, q:q + N // 2].float().contiguous()
 
 
-def initial_object(net: Cnn, prob: Problem, batch: int = 256):
-    """CNN predictions for every measured pattern, stitched into amp, phase [Nz, H, W]."""
+def probe_estimate(prob: Problem, defocus_A: float, dose: float = 1e5) -> torch.Tensor:
+    """A starting probe from nominal settings: the workload's probe model (synth.make_probe: same
+    aperture, modes, mode powers and dose) with defocus `defocus_A` instead of the true value."""
     g = prob.geom
-    st = Stitcher(g.N, g.Nz, g.H, g.W, probe_weight(prob.truth.probe), device=prob.I_meas.device)
+    p = synth.make_probe(g.N, g.M, g.dx, defocus_A=defocus_A, dose=dose)
+    return torch.tensor(p, dtype=torch.complex64, device=prob.I_meas.device)
+
+
+def initial_object(net: Cnn, prob: Problem, batch: int = 256, probe: torch.Tensor | None = None):
+    """CNN predictions for every measured pattern, stitched into amp, phase [Nz, H, W].  The
+    stitching weight comes from `probe` (default: the true probe)."""
+    g = prob.geom
+    w = probe_weight(prob.truth.probe if probe is None else probe)
+    st = Stitcher(g.N, g.Nz, g.H, g.W, w, device=prob.I_meas.device)
     for s in range(0, g.Ntot, batch):
         idx = torch.arange(s, min(s + batch, g.Ntot), dtype=torch.int32, device=prob.I_meas.device)
         pred = net.predict(prob.I_meas[s:s + idx.numel()].contiguous())
@@ -148,15 +158,19 @@ def flat_object(prob: Problem, seed: int = 1234):
 
 
 def reconstruct(prob: Problem, amp0: torch.Tensor, phase0: torch.Tensor, iters: int, batch: int, lr: dict,
-                target: float = 0.05, seed: int = 7, fft: str = "fp32", eval_every: int = 8):
-    """Adam on the object (probe, positions, tilt and dz frozen at the truth) from (amp0, phase0); one
+                target: float = 0.05, seed: int = 7, fft: str = "fp32", eval_every: int = 8,
+                probe0: torch.Tensor | None = None):
+    """Adam on the object from (amp0, phase0), with positions, tilt and dz frozen at the truth; the
+    probe is the truth, or starts at `probe0` and is refined too when `lr` has a "probe" rate.  One
     iteration = one pass over all positions in shuffled batches.  The NMSE is evaluated every
     `eval_every` batches (outside the timed work).  Returns the list of (iterations done, NMSE, GPU
     seconds of reconstruction so far), stopping once NMSE <= target."""
-    g = dataclasses.replace(prob.geom, grads=("amp", "phase"), fft=fft)
+    names = ("amp", "phase") + (("probe",) if lr.get("probe") else ())
+    g = dataclasses.replace(prob.geom, grads=names, fft=fft)
     dev = prob.I_meas.device
     pt = Ptycho(g, batch, device=dev)
-    params = Params(amp=amp0.clone(), phase=phase0.clone(), probe=prob.truth.probe, pos=prob.truth.pos,
+    probe = prob.truth.probe if probe0 is None else probe0.clone()
+    params = Params(amp=amp0.clone(), phase=phase0.clone(), probe=probe, pos=prob.truth.pos,
                     tilt=prob.truth.tilt, dz=prob.truth.dz)
     grads = params.zeros_like()
     adam = Adam(params, lr)
